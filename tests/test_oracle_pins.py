@@ -1,0 +1,401 @@
+"""Pins for the CPU oracle: each test ties an oracle function to something other than itself
+(a value the paper prints, a closed form, an invariant, brute force on tiny inputs)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import morlet as M
+from oracle import sft_dd as D
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+def _gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+# ------------------------------------------------------------------------------------------------
+# RMSE evaluator and fits
+# ------------------------------------------------------------------------------------------------
+
+def test_truncated_gaussian_rmse_matches_paper():
+    """Sec. II-E: truncating a Gaussian to +-3 sigma leaves a relative RMSE of 0.46 %.
+    Continuous closed form: sqrt(erfc(3)) = 0.470 %."""
+    g = _gold("truncation_3sigma.json")["relative_rmse_percent"]
+    sigma = 100.0
+    k = np.arange(-30 * 100, 30 * 100 + 1)
+    G = M.gaussian(k, sigma)
+    Gt = np.where(np.abs(k) <= 3 * sigma, G, 0.0)
+    e = 100 * M.relative_rmse(Gt, G)
+    assert abs(e - g) < 0.005
+    assert abs(e / 100 - math.sqrt(math.erfc(3.0))) < 0.02 * math.sqrt(math.erfc(3.0))
+
+
+def test_gaussian_derivatives_by_finite_difference():
+    """G_D and G_DD are the first and second derivatives of G (Sec. II definitions)."""
+    s, h = 7.3, 1e-4
+    k = np.linspace(-20, 20, 41)
+    d1 = (M.gaussian(k + h, s) - M.gaussian(k - h, s)) / (2 * h)
+    d2 = (M.gaussian(k + h, s) - 2 * M.gaussian(k, s) + M.gaussian(k - h, s)) / (h * h)
+    assert np.abs(d1 - M.gaussian_d(k, s)).max() < 1e-8
+    assert np.abs(d2 - M.gaussian_dd(k, s)).max() < 1e-5 * np.abs(d2).max()
+    assert abs(M.gaussian(np.arange(-2000, 2001), s).sum() - 1.0) < 1e-12
+
+
+def test_morlet_normalised_has_unit_energy():
+    """norm=1 reading of the discrete Morlet: C_xi pi^{-1/4} sigma^{-1/2} makes sum |psi|^2 = 1
+    (the continuous psi_xi has unit L2 norm; the sampled sum approximates the integral)."""
+    for xi in (2.0, 6.0):
+        for sigma in (16.0, 64.0):
+            k = np.arange(-int(12 * sigma), int(12 * sigma) + 1)
+            e = np.sum(np.abs(M.morlet(k, sigma, xi, 1)) ** 2)
+            assert abs(e - 1.0) < 1e-9
+    # kappa_xi makes the wavelet admissible (zero mean)
+    k = np.arange(-2000, 2001)
+    assert abs(M.morlet(k, 40.0, 3.0, 1).sum()) < 1e-9
+
+
+def test_fit_recovers_exact_series():
+    """If the target is exactly a series in the basis, the least-squares fit returns its coefficients."""
+    L, p0 = 50, 3
+    cm = np.array([0.3, -1.2, 0.7, 0.05])
+    cl = np.array([1.1, 0.2, -0.4, 0.9])
+    fit = dict(p0=p0, m=cm, l=cl, L=L)
+    k = np.arange(-L, L + 1)
+    target = M.kernel_direct(fit, k)
+    m, r1 = M._ls_fit(np.cos, lambda kk: target[kk + L].real, L, range(p0, p0 + 4))
+    l, r2 = M._ls_fit(np.sin, lambda kk: target[kk + L].imag, L, range(p0, p0 + 4))
+    assert np.abs(m - cm).max() < 1e-12 and np.abs(l - cl).max() < 1e-12
+    assert r1 < 1e-10 and r2 < 1e-10      # rss is formed by cancellation of O(L) terms
+
+
+def test_fit_matches_closed_form_gram():
+    """On k in [-L, L] the cosine Gram matrix has a closed form: sum_k cos(beta m k) = (-1)^m for
+    m != 0 mod 2L and 2L+1 for m = 0. Solving with that Gram must give the oracle's m_p."""
+    sigma, xi, K = 12.0, 6.0, 5
+    fit = M.fit_direct(sigma, xi, K)
+    L, p0 = fit["L"], fit["p0"]
+    k = np.arange(-L, L + 1)
+    ps = np.arange(p0, p0 + K)
+
+    def S(mm):
+        mm = int(mm)
+        return 2 * L + 1 if mm % (2 * L) == 0 else (-1) ** (mm % 2)
+
+    Gc = np.array([[0.5 * (S(p - q) + S(p + q)) for q in ps] for p in ps])
+    Gs = np.array([[0.5 * (S(p - q) - S(p + q)) for q in ps] for p in ps])
+    psi = M.morlet(k, sigma, xi, 0)
+    bc = np.array([np.sum(psi.real * np.cos(np.pi * p * k / L)) for p in ps])
+    bs = np.array([np.sum(psi.imag * np.sin(np.pi * p * k / L)) for p in ps])
+    assert np.abs(np.linalg.solve(Gc, bc) - fit["m"]).max() < 1e-11
+    assert np.abs(np.linalg.solve(Gs, bs) - fit["l"]).max() < 1e-11
+
+
+def test_fit_residual_orthogonal_and_pstart_global():
+    """Least-squares residuals are orthogonal to the basis; the chosen P_S is the global argmin
+    over all starts 0 .. 3*round(omega0/beta)."""
+    for sigma, K in ((8.0, 3), (64.0, 4), (30.0, 6)):
+        fit = M.fit_direct(sigma, 6.0, K)
+        L = fit["L"]
+        k = np.arange(-L, L + 1)
+        r = M.morlet(k, sigma, 6.0) - M.kernel_direct(fit, k)
+        for j in range(K):
+            a = M.harmonic_angle(fit["p0"] + j, k, L)
+            scale = np.sqrt(np.sum(np.abs(M.morlet(k, sigma, 6.0)) ** 2) * (2 * L + 1))
+            assert abs(np.dot(r.real, np.cos(a))) < 1e-10 * scale
+            assert abs(np.dot(r.imag, np.sin(a))) < 1e-10 * scale
+        pc = int(math.floor(6.0 / sigma * L / math.pi + 0.5))
+        allr = [M.fit_direct(sigma, 6.0, K, L, 0, p)["rss"] for p in range(0, 3 * pc + 1)]
+        assert fit["p0"] == int(np.argmin(allr))
+
+
+def test_table1_sft_soft_pin():
+    """Table I, SFT rows (soft pin: sigma and the optimised beta are not printed). With L = 256 and
+    beta optimised per P, some sigma in [L/5, L/3] reproduces all three printed errors of each row
+    to within 25 %."""
+    g = _gold("table1_relative_rmse.json")
+    L = g["L"]
+    for P in (3, 4, 5, 6):
+        want = np.array(g["SFT"][str(P)])
+        best = None
+        for ratio in np.linspace(3.0, 5.0, 21):
+            sig = L / ratio
+            b = M.table1_best_beta(P, L, sig, iters=40)
+            got = np.array([100 * M.table1_sft_rmse(P, d, L, sig, b) for d in range(3)])
+            err = np.abs(np.log(got / want)).max()
+            best = err if best is None else min(best, err)
+        assert best < math.log(1.25), (P, best)
+
+
+# ------------------------------------------------------------------------------------------------
+# Kernel integral (O-SFT) against brute force, Algorithm 1 and the definition
+# ------------------------------------------------------------------------------------------------
+
+def _brute_sft(x, L, p):
+    """Literal eqs. cp, sp: c_p[n] = sum_k x[n-k] cos(beta p k), s_p[n] = sum_k x[n-k] sin(beta p k)."""
+    N = len(x)
+    c = np.zeros(N)
+    s = np.zeros(N)
+    for n in range(N):
+        for k in range(-L, L + 1):
+            if 0 <= n - k < N:
+                c[n] += x[n - k] * math.cos(math.pi * p * k / L)
+                s[n] += x[n - k] * math.sin(math.pi * p * k / L)
+    return c, s
+
+
+@pytest.mark.parametrize("N,L,p0,K", [(1, 1, 0, 2), (7, 3, 1, 3), (40, 8, 2, 4), (64, 5, 0, 3), (13, 20, 4, 2)])
+def test_sft_dd_vs_brute_force(N, L, p0, K):
+    rng = np.random.default_rng(N * 100 + L)
+    x = rng.standard_normal(N)
+    m = rng.standard_normal(K)
+    l = rng.standard_normal(K)
+    fit = dict(p0=p0, m=m, l=l, L=L)
+    W = D.sft_direct_method(x, fit)
+    ref = np.zeros(N, complex)
+    for j in range(K):
+        c, s = _brute_sft(x, L, p0 + j)
+        ref += m[j] * c + 1j * l[j] * s
+    assert np.abs(W - ref).max() <= 1e-14 * max(1.0, np.abs(ref).max())
+
+
+def test_algorithm1_doubling_sliding_sum():
+    """Algorithm 1 (restated on the CPU) gives the same window sums as a literal sum, for odd and
+    even lengths including the 2L+1 windows of the SFT."""
+    rng = np.random.default_rng(11)
+    f = rng.standard_normal(300)
+    for length in (1, 2, 3, 8, 17, 33, 64, 129):
+        h = M.sliding_sum_doubling(f, length)
+        ref = np.array([f[n:n + length].sum() for n in range(len(f) - length + 1)])
+        assert np.abs(h - ref).max() < 1e-12
+
+
+def test_sft_window_sums_match_algorithm1():
+    """The kernel-integral window sum u_(2L+1)[t] (eq. kernelInter) equals the doubling sliding sum
+    of the modulated signal; checked through c_p - i s_p = e^{-i beta p n} u_(2L+1)[n+L]."""
+    rng = np.random.default_rng(5)
+    N, L, p = 200, 9, 3
+    x = rng.standard_normal(N)
+    t = np.arange(N)
+    f = x * np.exp(1j * np.pi * ((p * t) % (2 * L)) / L)
+    fpad = np.concatenate([np.zeros(2 * L), f, np.zeros(2 * L)])
+    h = M.sliding_sum_doubling(fpad, 2 * L + 1)           # h[i] = sum fpad[i .. i+2L]
+    # u_W[n + L] = sum_{s=n-L}^{n+L} f[s] = h[n - L + 2L] = h[n + L]
+    z = np.exp(-1j * np.pi * ((p * t) % (2 * L)) / L) * h[t + L]
+    W = D.sft_direct_method(x, dict(p0=p, m=np.array([1.0]), l=np.array([1.0]), L=L))
+    assert np.abs(W.real - z.real).max() < 1e-12
+    assert np.abs(W.imag + z.imag).max() < 1e-12
+
+
+def test_sft_dd_vs_direct_definition_c1():
+    """O-SFT (kernel integral, double-double) equals sum_k psi_hat[k] x[n-k] on config 1."""
+    import workloads as WL
+    w = WL.c1_fp64_single()
+    x = w.signals[0]
+    fit = M.fit_direct(64.0, 6.0, 4)
+    a = D.sft_direct_method(x, fit)
+    b = M.morlet_sft_direct(x, fit)
+    assert np.abs(a - b).max() < 1e-13 * np.abs(b).max()
+    # sampled direct sums agree with the full convolution
+    idx = np.array([0, 1, 255, 256, 2048, 4095])
+    assert np.abs(M.morlet_sft_direct(x, fit, idx) - b[idx]).max() < 1e-13 * np.abs(b).max()
+
+
+def test_sft_dd_long_signal_stays_exact():
+    """Double-double prefixes keep the window difference exact far into a long signal: sampled
+    outputs of a 2^20-sample signal agree with the direct sum to 1e-13."""
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(1 << 20) + 3.0      # a DC offset makes the raw prefix grow linearly
+    fit = M.fit_direct(16.0, 6.0, 4)
+    W = D.sft_direct_method(x, fit)
+    idx = np.array([5, 1000, 500000, (1 << 20) - 70, (1 << 20) - 1])
+    ref = M.morlet_sft_direct(x, fit, idx)
+    assert np.abs(W[idx] - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+# ------------------------------------------------------------------------------------------------
+# Closed forms and invariants of the direct convolutions
+# ------------------------------------------------------------------------------------------------
+
+def test_true_morlet_closed_form_for_complex_sinusoid():
+    """x = e^{i nu n} gives W[n] = e^{i nu n} sqrt(2 pi) sigma e^{-sigma^2 (nu - omega0)^2 / 2}
+    (norm 0; Poisson summation, truncation at 8 sigma below 1e-13). Real and imaginary inputs are
+    transformed separately since the oracle takes real signals."""
+    sigma, xi, N = 40.0, 6.0, 3000
+    n = np.arange(N)
+    for nu in (0.05, 0.15, 0.3):
+        W = M.morlet_true_direct(np.cos(nu * n), sigma, xi) + 1j * M.morlet_true_direct(np.sin(nu * n), sigma, xi)
+        want = np.exp(1j * nu * n) * math.sqrt(2 * math.pi) * sigma * math.exp(-sigma ** 2 * (nu - xi / sigma) ** 2 / 2)
+        mid = slice(int(8 * sigma) + 1, N - int(8 * sigma) - 1)
+        assert np.abs(W[mid] - want[mid]).max() < 1e-12 * math.sqrt(2 * math.pi) * sigma
+
+
+def test_fitted_transform_closed_form_and_error_by_K():
+    """The fitted kernel's response to a tone at the carrier approaches the closed form as K grows
+    (L = ceil(4 sigma)); the approximation error is reported per K, not gated tightly."""
+    sigma, xi, N = 32.0, 6.0, 2000
+    n = np.arange(N)
+    nu = xi / sigma
+    want = math.sqrt(2 * math.pi) * sigma
+    errs = []
+    for K in (3, 4, 6, 8):
+        fit = M.fit_direct(sigma, xi, K)
+        W = M.morlet_sft_direct(np.cos(nu * n), fit) + 1j * M.morlet_sft_direct(np.sin(nu * n), fit)
+        mid = slice(fit["L"] + 1, N - fit["L"] - 1)
+        errs.append(np.abs(W[mid] * np.exp(-1j * nu * n[mid]) - want).max() / want)
+    assert errs[-1] < errs[0]
+    assert errs[-1] < 0.05
+
+
+def test_invariants_linearity_shift_dc_hermitian():
+    rng = np.random.default_rng(3)
+    sigma = 10.0
+    fit = M.fit_direct(sigma, 6.0, 4)
+    L = fit["L"]
+    N = 400
+    x, y = rng.standard_normal(N), rng.standard_normal(N)
+    a, b = 1.7, -0.4
+    Wx, Wy = D.sft_direct_method(x, fit), D.sft_direct_method(y, fit)
+    assert np.abs(D.sft_direct_method(a * x + b * y, fit) - (a * Wx + b * Wy)).max() < 1e-12
+    s = 13   # shift-equivariance away from the ends
+    xs = np.concatenate([np.zeros(s), x[:-s]])
+    Ws = D.sft_direct_method(xs, fit)
+    assert np.abs(Ws[L + s:N - L] - Wx[L:N - L - s]).max() < 1e-12
+    # DC response: x = 1 gives sum_k psi_hat[k] in the interior
+    W1 = D.sft_direct_method(np.ones(N), fit)
+    assert np.abs(W1[L:N - L] - M.kernel_direct(fit).sum()).max() < 1e-11
+    # omega0 = 0: real cosine-only kernel, the transform of real x is real
+    f0 = M.fit_direct(sigma, 0.0, 4)
+    assert np.abs(D.sft_direct_method(x, f0).imag).max() < 1e-14 * np.abs(D.sft_direct_method(x, f0)).max() + 1e-15
+
+
+# ------------------------------------------------------------------------------------------------
+# ASFT
+# ------------------------------------------------------------------------------------------------
+
+def test_asft_shift_identity():
+    """eq. siftGauss: e^{-alpha k} G[k] = e^{alpha^2/(4 gamma)} G[k + n0], n0 = alpha / (2 gamma)."""
+    sigma, n0 = 37.0, 5
+    a = M.asft_alpha(sigma, n0)
+    g = 1 / (2 * sigma ** 2)
+    k = np.arange(-300, 301)
+    lhs = np.exp(-a * k) * M.gaussian(k, sigma)
+    rhs = math.exp(a * a / (4 * g)) * M.gaussian(k + n0, sigma)
+    assert np.abs(lhs - rhs).max() < 1e-15 * np.abs(lhs).max() * 10
+
+
+def test_asft_recursion_vs_brute_damped_sums():
+    """The double-double attenuated recursion equals literal damped sums
+    sum_k x[n-k] e^{-alpha k} (cos, sin)(beta p k) over k in [-L, L] (eqs. acp, asp, decaying reading)."""
+    rng = np.random.default_rng(9)
+    N, L, p0, K, sigma, xi, n0 = 50, 6, 1, 2, 3.0, 2.0, 2
+    x = rng.standard_normal(N)
+    m, l = rng.standard_normal(K), rng.standard_normal(K)
+    fit = dict(p0=p0, m=m, l=l, L=L)
+    W = D.asft_direct_method(x, fit, sigma, xi, n0)
+    alpha = n0 / sigma ** 2
+    g = 1 / (2 * sigma ** 2)
+    E = math.exp(-alpha ** 2 / (4 * g)) * np.exp(1j * xi / sigma * n0)
+    ref = np.zeros(N, complex)
+    for n in range(N):
+        acc = 0j
+        nn = n - n0
+        for j in range(K):
+            p = p0 + j
+            ct = st = 0.0
+            for k in range(-L, L + 1):
+                if 0 <= nn - k < N:
+                    w = math.exp(-alpha * k)
+                    ct += x[nn - k] * w * math.cos(math.pi * p * k / L)
+                    st += x[nn - k] * w * math.sin(math.pi * p * k / L)
+            acc += m[j] * ct + 1j * l[j] * st
+        ref[n] = E * acc
+    assert np.abs(W - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+def test_asft_approximates_morlet_and_sign_of_alpha():
+    """ASFT with the decaying reading tracks the true Morlet to within the SFT fit error times the
+    edge gain e^{4 n0/sigma}; flipping the sign of alpha would move the output by 2 n0 and fail."""
+    import workloads as WL
+    sigma, xi, K = 48.0, 6.0, 6
+    x = WL.white(21, 3000, np.float64)
+    fit = M.fit_direct(sigma, xi, K)
+    n0 = M.default_n0(sigma)
+    Wa = D.asft_direct_method(x, fit, sigma, xi, n0)
+    Ws = M.morlet_sft_direct(x, fit)
+    Wt = M.morlet_true_direct(x, sigma, xi)
+    L = fit["L"]
+    mid = slice(2 * L, 3000 - 2 * L)
+    e_sft = np.abs(Ws[mid] - Wt[mid]).max() / np.abs(Wt[mid]).max()
+    e_asft = np.abs(Wa[mid] - Wt[mid]).max() / np.abs(Wt[mid]).max()
+    assert e_asft < 3.0 * e_sft * math.exp(4 * n0 / sigma) + 1e-3
+    # the definition (direct sum with the ASFT kernel) and the recursion agree
+    Wd = M.morlet_asft_direct(x, fit, sigma, xi, n0)
+    assert np.abs(Wd - Wa).max() < 1e-12 * np.abs(Wd).max()
+    # a 2 n0 shift (what the opposite sign of alpha produces) is far off
+    shifted = np.roll(Wa, 2 * n0)
+    assert np.abs(shifted[mid] - Wt[mid]).max() / np.abs(Wt[mid]).max() > 5 * e_asft
+
+
+# ------------------------------------------------------------------------------------------------
+# Gaussian smoothing and adjoint
+# ------------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("deriv", [0, 1, 2])
+def test_gauss_kernel_integral_vs_direct(deriv):
+    rng = np.random.default_rng(deriv)
+    x = rng.standard_normal(3000)
+    sigma = 20.0
+    gf = M.fit_gauss(sigma, 6, deriv)
+    a = D.sft_gauss(x, gf)
+    b = M.gauss_sft_direct(x, gf)
+    assert np.abs(a - b).max() < 1e-13 * np.abs(b).max()
+    # against the true (differentiated) Gaussian smoothing in the interior
+    L = gf["L"]
+    k = np.arange(-L, L + 1)
+    true = M.conv_direct(x, [M.gaussian, M.gaussian_d, M.gaussian_dd][deriv](k, sigma), -L)
+    mid = slice(L, 3000 - L)
+    assert np.abs(b[mid] - true[mid]).max() < 0.02 * np.abs(true[mid]).max()
+
+
+def test_adjoint_inner_product_identity():
+    rng = np.random.default_rng(17)
+    N, sigma = 700, 9.0
+    fit = M.fit_direct(sigma, 6.0, 4)
+    x = rng.standard_normal(N)
+    g = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    W = M.morlet_sft_direct(x, fit)
+    dx = M.adjoint_direct(g, fit)
+    lhs = float(np.sum((np.conj(g) * W).real))
+    rhs = float(np.dot(x, dx))
+    assert abs(lhs - rhs) < 1e-11 * (abs(lhs) + 1)
+    idx = np.array([0, 3, 350, N - 1])
+    assert np.abs(M.adjoint_direct(g, fit, idx) - dx[idx]).max() < 1e-12 * np.abs(dx).max()
+
+
+def test_adjoint_finite_differences_log_power_loss():
+    """Loss sum_n w[n] log(1e-6 + |W[n]|^2) (the differentiation workload's loss). Its gradient
+    dLoss/dx through adjoint_direct matches central differences (eps = 1e-6) at random coordinates."""
+    rng = np.random.default_rng(23)
+    N, sigma = 300, 6.0
+    fit = M.fit_direct(sigma, 6.0, 4)
+    x = rng.standard_normal(N)
+    w = rng.standard_normal(N)
+
+    def loss(v):
+        W = M.morlet_sft_direct(v, fit)
+        return float(np.sum(w * np.log(1e-6 + np.abs(W) ** 2)))
+
+    W = M.morlet_sft_direct(x, fit)
+    g = w * 2 * W / (1e-6 + np.abs(W) ** 2)          # dLoss/dRe W + i dLoss/dIm W
+    dx = M.adjoint_direct(g, fit)
+    for t in rng.choice(N, 8, replace=False):
+        e = np.zeros(N)
+        e[t] = 1e-6
+        fd = (loss(x + e) - loss(x - e)) / 2e-6
+        assert abs(fd - dx[t]) < 1e-5 * (abs(dx[t]) + 1e-3)
