@@ -1,0 +1,175 @@
+/*
+ * morlet_sft.h - C ABI of a GB300 (sm_103a) library for the Morlet wavelet transform and Gaussian
+ * smoothing by the sliding Fourier transform (SFT) and the attenuated SFT (ASFT), after
+ * Y. Yamashita and T. Wakahara, "Morlet wavelet transform using attenuated sliding Fourier
+ * transform and kernel integral for graphic processing unit" (arXiv:2110.11866).
+ *
+ * Notation. The paper's half window K is called L here (the window is k in [-L, L], 2L+1 samples,
+ * beta = pi / L) and its number of Fourier terms P_D is called K.
+ *
+ * Conventions shared by every entry point
+ *   - Plain pointers and sizes only. Device pointers are CUDA device (or managed) addresses owned by
+ *     the caller; the library never frees them. Host pointers are read during the call only.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream. Calls that
+ *     launch work are asynchronous on that stream unless stated otherwise.
+ *   - Every function returns a morlet_status (0 = success). Errors are reported, never abort.
+ *     A timeout inside a kernel (the bounded cross-tile wait) is latched in a host-visible error
+ *     word and returned as MORLET_ERR_TIMEOUT by the next call on the plan and by
+ *     morlet_last_device_error.
+ *   - Real input x: the signals of a batch are concatenated, signal i starting at element
+ *     sum_{i'<i} lengths[i'], FP32 (precision FP32_*) or FP64 (precision FP64).
+ *   - Scalogram output W: interleaved complex (complex64 for FP32 precisions, complex128 for FP64),
+ *     laid out [signal][scale][n]: element S * off_i + s * N_i + n, off_i the signal's start in x.
+ *   - Samples outside [0, N) count as zero (the "zero" extension of Sec. II, eq. xG).
+ */
+#ifndef MORLET_SFT_H
+#define MORLET_SFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct morlet_plan_s* morlet_plan_t;
+
+typedef enum {
+  MORLET_OK = 0,
+  MORLET_ERR_ARG = -1,          /* invalid argument (size, pointer, option) */
+  MORLET_ERR_UNSUPPORTED = -2,  /* valid but not built (e.g. K > 12, ASFT adjoint) */
+  MORLET_ERR_CUDA = -3,         /* a CUDA runtime call failed */
+  MORLET_ERR_TIMEOUT = -4,      /* a kernel gave up waiting on a predecessor tile */
+  MORLET_ERR_NOMEM = -5         /* device or host allocation failed */
+} morlet_status;
+
+/* method */
+enum { MORLET_DIRECT = 0, MORLET_GAUSS = 1 };
+/* transform */
+enum { MORLET_SFT = 0, MORLET_ASFT = 1 };
+/* precision: arithmetic of the per-sample scan and of the cross-tile carries */
+enum {
+  MORLET_FP32_PLAIN = 0,  /* FP32 samples, FP32 scan, FP32 carries, one look-back chain per row */
+  MORLET_FP32_COMP = 1,   /* FP32 samples and scan; FP64 carries; short windows recomputed per tile */
+  MORLET_FP64 = 2         /* FP64 everywhere */
+};
+/* scan form */
+enum {
+  MORLET_FORM_AUTO = 0,       /* rotating frame (the faster form on this GPU) */
+  MORLET_FORM_KERNEL = 1,     /* kernel integral: modulate, prefix-scan, difference, demodulate */
+  MORLET_FORM_ROTATING = 2    /* the same window sums kept in the frame of each harmonic */
+};
+/* flags */
+enum {
+  MORLET_FLAG_NO_GRAPH = 1,   /* launch kernels directly instead of replaying a CUDA graph */
+  MORLET_FLAG_AUTOTUNE = 2,   /* time the launch shapes on this plan at plan time and keep the fastest */
+  MORLET_FLAG_NO_HALO = 4     /* force one look-back chain per row (no per-tile window recompute) */
+};
+
+typedef struct {
+  int64_t n_signals;        /* >= 1 */
+  const int64_t* lengths;   /* host array [n_signals], each >= 1; copied into the plan */
+  int32_t n_scales;         /* >= 1 */
+  const double* sigmas;     /* host array [n_scales], each >= 0.5; copied into the plan */
+  double xi;                /* Morlet centre parameter; omega0 = xi / sigma (Sec. III) */
+  int32_t K;                /* Fourier terms, 1..12; 0 = smallest K whose relative fit RMSE <= fit_tol */
+  double fit_tol;           /* used only when K == 0 */
+  int32_t method;           /* MORLET_DIRECT (Morlet, direct method of Sec. III-A) | MORLET_GAUSS */
+  int32_t transform;        /* MORLET_SFT | MORLET_ASFT */
+  int32_t precision;        /* MORLET_FP32_PLAIN | MORLET_FP32_COMP | MORLET_FP64 */
+  int32_t norm;             /* 0: e^{-k^2/2sigma^2} e^{i omega0 k}; 1: C_xi pi^{-1/4} sigma^{-1/2} (...)(e^{i xi k/sigma} - kappa_xi) */
+  int32_t n0;               /* ASFT output shift; 0 = max(1, round(sigma / 8)) per scale */
+  double window_mult;       /* L = ceil(window_mult * sigma); 0 = 4.0 */
+  int32_t deriv;            /* MORLET_GAUSS only: 0 = G, 1 = G_D, 2 = G_DD (Sec. II) */
+  int32_t form;             /* MORLET_FORM_* */
+  int32_t flags;            /* MORLET_FLAG_* */
+  int64_t spin_limit;       /* bounded wait in polls of a predecessor flag; 0 = default (about 1 s) */
+} morlet_plan_desc;
+
+/*
+ * morlet_plan - validate `desc`, fit the coefficients and build everything a transform needs.
+ * Defines: per scale, L = ceil(window_mult * sigma), beta = pi / L, harmonics p = P_S .. P_S + K - 1
+ * with P_S the least-residual start (direct method, Sec. III-A), coefficients m_p (cos) and l_p
+ * (sin) minimising eq. mmse over k in [-L, L], fitted on the GPU in FP64. For MORLET_GAUSS:
+ * harmonics 0..K-1 fitted to G, G_D or G_DD (eq. aproGauss).
+ * Allocates the plan's device workspace (tile table, cross-tile status, tables) and a host-mapped
+ * error word; no allocation happens in forward/backward. Synchronises `stream`.
+ * Errors: MORLET_ERR_ARG (bad sizes/options), MORLET_ERR_NOMEM, MORLET_ERR_CUDA.
+ * On error *out is set to NULL.
+ */
+int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* desc, void* stream);
+
+/*
+ * morlet_forward - the transform of Sec. III-A (SFT: eqs. kernel-kernelInter and the direct-method
+ * combine; ASFT: eq. iir1A with the shift of eq. GsASFT), for all signals x all scales.
+ * x: device, real, layout above (FP32, or FP64 for MORLET_FP64).
+ * W: device, complex scalogram [signal][scale][n] for MORLET_DIRECT; for MORLET_GAUSS a real array
+ *    [signal][scale][n] of the smoothed signal (or derivative).
+ * Asynchronous. Returns MORLET_ERR_TIMEOUT if a previous launch on this plan timed out.
+ */
+int morlet_forward(morlet_plan_t plan, const void* x, void* W, void* stream);
+
+/*
+ * morlet_backward - adjoint of morlet_forward for a real-valued loss (SFT, MORLET_DIRECT only).
+ * gW: device complex [signal][scale][n], gW = dLoss/dRe W + i dLoss/dIm W.
+ * gx: device real, same layout as x: gx[t] = sum_scales sum_n Re(conj(gW[n]) dW[n]/dx[t]).
+ * The scale sum is done in a fixed order (deterministic). Uses the plan's workspace.
+ * Errors: MORLET_ERR_UNSUPPORTED for ASFT or MORLET_GAUSS plans.
+ */
+int morlet_backward(morlet_plan_t plan, const void* gW, void* gx, void* stream);
+
+/*
+ * gauss_smooth - Gaussian smoothing (deriv 0) or its first / second derivative (deriv 1, 2) of one
+ * real signal by SFT (eq. GsSFT and the two after it), harmonics p = 0..P (P + 1 terms),
+ * L = ceil(4 sigma). x, y: device arrays of N elements (FP32, or FP64 if precision == MORLET_FP64).
+ * Builds (first call) and caches a plan per (N, sigma, P, deriv, precision, device); later calls
+ * with the same key allocate nothing. Synchronous on first use of a key, asynchronous afterwards.
+ */
+int gauss_smooth(const void* x, int64_t N, double sigma, int32_t P, int32_t deriv, int32_t precision,
+                 void* y, void* stream);
+
+/* Release a plan and everything it owns. Synchronises the device. NULL is ignored. */
+void morlet_plan_destroy(morlet_plan_t plan);
+
+/* Static description of a status code. */
+const char* morlet_strerror(int status);
+
+/*
+ * morlet_last_device_error - the plan's host-mapped error word after synchronising `stream`:
+ * 0, or MORLET_ERR_TIMEOUT if any cross-tile wait gave up. Clears the word.
+ */
+int morlet_last_device_error(morlet_plan_t plan, void* stream);
+
+/*
+ * morlet_plan_info - copy the fitted parameters of scale `s` to host memory.
+ * L, p0, K: host int64/int32 outputs; m, l: host double[12] (coefficients of cos / sin terms,
+ * entries >= K are zero); n0: ASFT shift (0 for SFT). Any output pointer may be NULL.
+ */
+int morlet_plan_info(morlet_plan_t plan, int32_t s, int64_t* L, int32_t* p0, int32_t* K, double* m,
+                     double* l, int32_t* n0);
+
+/*
+ * morlet_plan_stats - launch shape and work of the forward kernel, for measurement:
+ * out[0] = threads per CTA, out[1] = samples per thread, out[2] = CTAs launched,
+ * out[3] = work items, out[4] = sub-tiles processed (incl. window prologues), out[5] = rows in
+ * look-back mode, out[6] = rows in per-tile window mode, out[7] = kernel launches per forward.
+ */
+int morlet_plan_stats(morlet_plan_t plan, int64_t out[8]);
+
+/*
+ * morlet_plan_set_spin_limit - change the bounded-wait limit (polls) of later launches; used to make
+ * the timeout path fire quickly in tests.
+ */
+int morlet_plan_set_spin_limit(morlet_plan_t plan, int64_t polls);
+
+/*
+ * morlet_debug_skip_tickets - testing hook: the next forward starts its work-item counter at `skip`
+ * instead of 0, so the first `skip` work items are never processed and tiles that wait on them hit
+ * the bounded wait. Must be followed by morlet_last_device_error.
+ */
+int morlet_debug_skip_tickets(morlet_plan_t plan, int64_t skip);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MORLET_SFT_H */

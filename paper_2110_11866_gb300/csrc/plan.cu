@@ -1,0 +1,620 @@
+// Host side of the C ABI (include/morlet_sft.h): plan construction, tile tables, launches.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "../../include/morlet_sft.h"
+#include "plan_internal.h"
+
+namespace msft {
+const void* kernel_rf_f32c_morlet(int);
+const void* kernel_rf_f32p_morlet(int);
+const void* kernel_rf_f32p_asft(int);
+const void* kernel_rf_f64_morlet(int);
+const void* kernel_ki_f32c_morlet(int);
+const void* kernel_ki_f32p_morlet(int);
+const void* kernel_ki_f64_morlet(int);
+const void* kernel_rf_f32c_real(int);
+const void* kernel_rf_f32p_real(int);
+const void* kernel_rf_f64_real(int);
+const void* kernel_rf_f32c_adj(int);
+const void* kernel_rf_f32p_adj(int);
+const void* kernel_rf_f64_adj(int);
+
+const void* kernel_for(int variant, int K) {
+  switch (variant) {
+    case V_RF_F32C_MORLET: return kernel_rf_f32c_morlet(K);
+    case V_RF_F32P_MORLET: return kernel_rf_f32p_morlet(K);
+    case V_RF_F32P_ASFT: return kernel_rf_f32p_asft(K);
+    case V_RF_F64_MORLET: return kernel_rf_f64_morlet(K);
+    case V_KI_F32C_MORLET: return kernel_ki_f32c_morlet(K);
+    case V_KI_F32P_MORLET: return kernel_ki_f32p_morlet(K);
+    case V_KI_F64_MORLET: return kernel_ki_f64_morlet(K);
+    case V_RF_F32C_REAL: return kernel_rf_f32c_real(K);
+    case V_RF_F32P_REAL: return kernel_rf_f32p_real(K);
+    case V_RF_F64_REAL: return kernel_rf_f64_real(K);
+    case V_RF_F32C_ADJ: return kernel_rf_f32c_adj(K);
+    case V_RF_F32P_ADJ: return kernel_rf_f32p_adj(K);
+    case V_RF_F64_ADJ: return kernel_rf_f64_adj(K);
+    default: return nullptr;
+  }
+}
+}  // namespace msft
+
+using namespace msft;
+
+namespace {
+
+constexpr int ITEMS = 16;
+constexpr long long TILE = (long long)THREADS * ITEMS;
+constexpr long long DEFAULT_SPIN = 1LL << 20;  // polls of ~64 ns sleep + an L2 round trip: about 1 s
+
+// A launchable transform: kernel, work table, chains and status arrays.
+struct Launch {
+  const void* func = nullptr;
+  WorkItem* d_work = nullptr;
+  long long n_work = 0;
+  ChainDesc* d_chains = nullptr;
+  int grid = 0;
+  long long sub_tiles = 0;
+  long long rows_chain = 0, rows_halo = 0;
+  std::vector<long long> scale_begin;  // adjoint: work items of scale s are [scale_begin[s], scale_begin[s+1])
+};
+
+}  // namespace
+
+struct morlet_plan_s {
+  int device = 0;
+  int sms = 0;
+  morlet_plan_desc desc{};
+  std::vector<int64_t> lengths;
+  std::vector<double> sigmas;
+  std::vector<int64_t> x_off;
+  int K_fit = 0;     // terms per scale after the fit (max over scales)
+  int K_kernel = 0;  // compiled term count used
+  int form = 2;
+  size_t elem = 4;   // bytes per real sample
+  ScaleTab* d_tabs = nullptr;
+  FitJob* d_jobs = nullptr;
+  std::vector<ScaleTab> h_tabs;
+  Launch fwd, adj;
+  uint32_t* d_flags = nullptr;
+  void* d_agg = nullptr;
+  void* d_incl = nullptr;
+  long long n_slots = 0;
+  unsigned long long* d_ticket = nullptr;  // one counter per launch (adjoint: one per scale)
+  int* h_err = nullptr;                    // host-mapped error word
+  int* d_err = nullptr;
+  long long spin = DEFAULT_SPIN;
+  long long skip_tickets = 0;
+  int latched = 0;
+  // graph of the forward (memsets + kernel) for a given (x, W)
+  cudaGraphExec_t gexec = nullptr;
+  const void* g_x = nullptr;
+  void* g_out = nullptr;
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return MORLET_OK;
+  if (e == cudaErrorMemoryAllocation) return MORLET_ERR_NOMEM;
+  return MORLET_ERR_CUDA;
+}
+
+#define CK(call)                         \
+  do {                                   \
+    cudaError_t e_ = (call);             \
+    if (e_ != cudaSuccess) {             \
+      rc = cuda_status(e_);              \
+      goto fail;                         \
+    }                                    \
+  } while (0)
+
+int round_k(int K) {
+  for (int i = 0; i < N_KBUILT; ++i)
+    if (kbuilt(i) >= K) return kbuilt(i);
+  return -1;
+}
+
+int variant_of(const morlet_plan_s* p, bool adjoint) {
+  const int prec = p->desc.precision;
+  if (adjoint) return prec == MORLET_FP64 ? V_RF_F64_ADJ : prec == MORLET_FP32_COMP ? V_RF_F32C_ADJ : V_RF_F32P_ADJ;
+  if (p->desc.method == MORLET_GAUSS)
+    return prec == MORLET_FP64 ? V_RF_F64_REAL : prec == MORLET_FP32_COMP ? V_RF_F32C_REAL : V_RF_F32P_REAL;
+  if (p->desc.transform == MORLET_ASFT) return V_RF_F32P_ASFT;
+  if (p->form == 1)
+    return prec == MORLET_FP64 ? V_KI_F64_MORLET : prec == MORLET_FP32_COMP ? V_KI_F32C_MORLET : V_KI_F32P_MORLET;
+  return prec == MORLET_FP64 ? V_RF_F64_MORLET : prec == MORLET_FP32_COMP ? V_RF_F32C_MORLET : V_RF_F32P_MORLET;
+}
+
+long long floordiv(long long a, long long b) { return (a >= 0) ? a / b : -((-a + b - 1) / b); }
+
+// Work table of one transform. Rows are (signal, scale) pairs taken in `order`.
+//
+// FP32 rounding leaves a residue of about one unit of roundoff of |x| per sample in the carried
+// window state (the lagged subtraction never cancels the earlier addition bit for bit), and with
+// |rho| = 1 the residue is never forgotten. The compensated precision therefore restarts the scan
+// from a zero state 2L samples before each "segment" of outputs, which bounds the history that
+// can leave a residue to (segment + 2L) samples; FP64 carries make the rest exact. Short windows
+// (2L <= 2T) use one sub-tile per segment processed by one CTA ("window" rows, no look-back);
+// long windows use segments of max(4T, 4L) outputs, each a look-back chain of sub-tiles. The plain
+// precision keeps one chain per row (its errors grow with the row length), FP64 and ASFT (whose
+// damping forgets old residue) use long segments.
+void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& work, std::vector<ChainDesc>& chains,
+                long long& slots, Launch& ln) {
+  const int S = (int)p->sigmas.size();
+  const long long nsig = (long long)p->lengths.size();
+  const int prec = p->desc.precision;
+  const bool comp = prec == MORLET_FP32_COMP && p->desc.transform == MORLET_SFT;
+  const bool window_ok = prec != MORLET_FP32_PLAIN && !(p->desc.flags & MORLET_FLAG_NO_HALO);
+  std::vector<std::pair<long long, int>> order;  // (signal, scale)
+  if (adjoint) {
+    for (int s = 0; s < S; ++s)
+      for (long long i = 0; i < nsig; ++i) order.push_back({i, s});
+  } else {
+    for (long long i = 0; i < nsig; ++i)
+      for (int s = 0; s < S; ++s) order.push_back({i, s});
+  }
+  ln.scale_begin.assign(S + 1, 0);
+  int prev_scale = -1;
+  for (auto& rs : order) {
+    const long long i = rs.first;
+    const int s = rs.second;
+    if (adjoint && s != prev_scale) {
+      for (int q = prev_scale + 1; q <= s; ++q) ln.scale_begin[q] = (long long)work.size();
+      prev_scale = s;
+    }
+    const ScaleTab& tb = p->h_tabs[s];
+    const long long N = p->lengths[i];
+    const long long L = tb.L, D = tb.D;
+    ChainDesc c{};
+    c.n = N;
+    const long long row = (long long)S * p->x_off[i] + (long long)s * N;  // scalogram row
+    c.x_off = adjoint ? row : p->x_off[i];
+    c.out_off = adjoint ? p->x_off[i] : row;
+    c.scale = s;
+    const int ci = (int)chains.size();
+    chains.push_back(c);
+    const long long k_min = -floordiv(D + TILE - 1, TILE);  // sub-tile holding t = 0
+    const long long n_out = (N + TILE - 1) / TILE;          // sub-tiles with outputs: 0 .. n_out-1
+    const long long h = (2 * L + TILE - 1) / TILE;          // sub-tiles covering the 2L-sample prologue
+    if (window_ok && h <= 2) {
+      // one CTA per segment: prologue sub-tiles + M output sub-tiles, zero state at t_dom
+      ln.rows_halo++;
+      const long long M = comp ? 1 : std::max<long long>(1, 4 * h);
+      for (long long k0 = 0; k0 < n_out; k0 += M) {
+        WorkItem w{};
+        w.chain = ci;
+        const long long t0 = D + k0 * TILE;
+        w.t_dom = std::max<long long>(0, t0 - 2 * L);
+        w.k_first = std::max(floordiv(w.t_dom - D, TILE), k_min);
+        const long long kend = std::min(k0 + M, n_out);
+        w.n_sub = (int)(kend - w.k_first);
+        w.k_out = k0;
+        w.slot = -1;
+        w.slot_first = -1;
+        work.push_back(w);
+        ln.sub_tiles += w.n_sub;
+      }
+    } else {
+      ln.rows_chain++;
+      long long seg = n_out;  // output sub-tiles per segment
+      if (comp && window_ok) seg = std::max<long long>(4, (4 * L + TILE - 1) / TILE);
+      for (long long k0 = 0; k0 < n_out; k0 += seg) {
+        const long long t0 = D + k0 * TILE;
+        const long long t_dom = std::max<long long>(0, t0 - 2 * L);
+        const long long kf = std::max(floordiv(t_dom - D, TILE), k_min);
+        const long long kend = std::min(k0 + seg, n_out);
+        const long long first = slots;
+        for (long long k = kf; k < kend; ++k) {
+          WorkItem w{};
+          w.chain = ci;
+          w.k_first = k;
+          w.n_sub = 1;
+          w.k_out = k0;
+          w.t_dom = t_dom;
+          w.slot = slots++;
+          w.slot_first = first;
+          work.push_back(w);
+          ln.sub_tiles += 1;
+        }
+      }
+    }
+  }
+  if (adjoint)
+    for (int q = prev_scale + 1; q <= S; ++q) ln.scale_begin[q] = (long long)work.size();
+}
+
+int setup_launch(morlet_plan_s* p, bool adjoint, Launch& ln, long long& slots) {
+  int rc = MORLET_OK;
+  std::vector<WorkItem> work;
+  std::vector<ChainDesc> chains;
+  build_work(p, adjoint, work, chains, slots, ln);
+  ln.func = kernel_for(variant_of(p, adjoint), p->K_kernel);
+  if (!ln.func) return MORLET_ERR_UNSUPPORTED;
+  ln.n_work = (long long)work.size();
+  int occ = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ln.func, THREADS, 0));
+  if (occ < 1) occ = 1;
+  ln.grid = (int)std::min<long long>((long long)occ * p->sms, std::max<long long>(1, ln.n_work));
+  CK(cudaMalloc(&ln.d_work, sizeof(WorkItem) * std::max<size_t>(1, work.size())));
+  CK(cudaMalloc(&ln.d_chains, sizeof(ChainDesc) * std::max<size_t>(1, chains.size())));
+  CK(cudaMemcpy(ln.d_work, work.data(), sizeof(WorkItem) * work.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ln.d_chains, chains.data(), sizeof(ChainDesc) * chains.size(), cudaMemcpyHostToDevice));
+  return MORLET_OK;
+fail:
+  return rc;
+}
+
+void free_launch(Launch& ln) {
+  cudaFree(ln.d_work);
+  cudaFree(ln.d_chains);
+  ln.d_work = nullptr;
+  ln.d_chains = nullptr;
+}
+
+int check_latched(morlet_plan_s* p) {
+  if (p->latched) return p->latched;
+  if (p->h_err && *(volatile int*)p->h_err) {
+    p->latched = MORLET_ERR_TIMEOUT;
+    return p->latched;
+  }
+  return MORLET_OK;
+}
+
+size_t carry_bytes(const morlet_plan_s* p) {
+  const size_t c = (p->desc.precision == MORLET_FP32_PLAIN || p->desc.transform == MORLET_ASFT) ? 8 : 16;
+  return c;
+}
+
+// Enqueue one scan launch: reset its work counter (and the status flags), then the kernel.
+cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out, long long w_begin, long long w_end,
+                    unsigned long long* ticket, bool clear_flags, cudaStream_t st, int accumulate = 0) {
+  cudaError_t e;
+  if (p->skip_tickets > 0) {
+    const unsigned long long v = (unsigned long long)p->skip_tickets;
+    e = cudaMemcpyAsync(ticket, &v, sizeof(v), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    p->skip_tickets = 0;
+  } else {
+    e = cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), st);
+  }
+  if (e != cudaSuccess) return e;
+  if (clear_flags && p->n_slots > 0) {
+    e = cudaMemsetAsync(p->d_flags, 0, sizeof(uint32_t) * p->n_slots, st);
+    if (e != cudaSuccess) return e;
+  }
+  KParams kp{};
+  kp.x = x;
+  kp.out = out;
+  kp.work = ln.d_work + w_begin;
+  kp.n_work = w_end - w_begin;
+  kp.chains = ln.d_chains;
+  kp.tabs = p->d_tabs;
+  kp.flags = p->d_flags;
+  kp.agg = p->d_agg;
+  kp.incl = p->d_incl;
+  kp.ticket = ticket;
+  kp.err = p->d_err;
+  kp.spin_limit = p->spin;
+  kp.accumulate = accumulate;
+  if (kp.n_work <= 0) return cudaSuccess;
+  void* args[] = {&kp};
+  const int grid = (int)std::min<long long>(ln.grid, kp.n_work);
+  return cudaLaunchKernel(ln.func, dim3(grid), dim3(THREADS), args, 0, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* morlet_strerror(int status) {
+  switch (status) {
+    case MORLET_OK: return "ok";
+    case MORLET_ERR_ARG: return "invalid argument";
+    case MORLET_ERR_UNSUPPORTED: return "unsupported option";
+    case MORLET_ERR_CUDA: return "CUDA runtime error";
+    case MORLET_ERR_TIMEOUT: return "a kernel timed out waiting for a predecessor tile";
+    case MORLET_ERR_NOMEM: return "out of memory";
+    default: return "unknown status";
+  }
+}
+
+void morlet_plan_destroy(morlet_plan_t p) {
+  if (!p) return;
+  cudaSetDevice(p->device);
+  cudaDeviceSynchronize();
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  free_launch(p->fwd);
+  free_launch(p->adj);
+  cudaFree(p->d_tabs);
+  cudaFree(p->d_jobs);
+  cudaFree(p->d_flags);
+  cudaFree(p->d_agg);
+  cudaFree(p->d_incl);
+  cudaFree(p->d_ticket);
+  if (p->h_err) cudaFreeHost(p->h_err);
+  delete p;
+}
+
+int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
+  if (!out) return MORLET_ERR_ARG;
+  *out = nullptr;
+  if (!d || d->n_signals < 1 || !d->lengths || d->n_scales < 1 || !d->sigmas) return MORLET_ERR_ARG;
+  if (d->K < 0 || d->K > KMAX) return d->K > KMAX ? MORLET_ERR_UNSUPPORTED : MORLET_ERR_ARG;
+  if (d->K == 0 && !(d->fit_tol > 0)) return MORLET_ERR_ARG;
+  if (d->method != MORLET_DIRECT && d->method != MORLET_GAUSS) return MORLET_ERR_ARG;
+  if (d->transform != MORLET_SFT && d->transform != MORLET_ASFT) return MORLET_ERR_ARG;
+  if (d->precision < MORLET_FP32_PLAIN || d->precision > MORLET_FP64) return MORLET_ERR_ARG;
+  if (d->norm != 0 && d->norm != 1) return MORLET_ERR_ARG;
+  if (d->form < 0 || d->form > 2) return MORLET_ERR_ARG;
+  if (d->method == MORLET_GAUSS && (d->deriv < 0 || d->deriv > 2)) return MORLET_ERR_ARG;
+  if (d->transform == MORLET_ASFT && (d->method != MORLET_DIRECT || d->precision == MORLET_FP64 || d->form == 1))
+    return MORLET_ERR_UNSUPPORTED;
+  if (d->n0 < 0 || d->window_mult < 0 || d->spin_limit < 0) return MORLET_ERR_ARG;
+  for (int64_t i = 0; i < d->n_signals; ++i)
+    if (d->lengths[i] < 1) return MORLET_ERR_ARG;
+  for (int32_t s = 0; s < d->n_scales; ++s)
+    if (!(d->sigmas[s] >= 0.5) || !(d->sigmas[s] < 1e9)) return MORLET_ERR_ARG;
+  if (!(d->xi >= 0.0 && d->xi < 1e6)) return MORLET_ERR_ARG;
+
+  cudaStream_t st = (cudaStream_t)stream;
+  morlet_plan_s* p = new (std::nothrow) morlet_plan_s();
+  if (!p) return MORLET_ERR_NOMEM;
+  int rc = MORLET_OK;
+  const int S = d->n_scales;
+  const double wm = d->window_mult > 0 ? d->window_mult : 4.0;
+  std::vector<FitJob> jobs(S);
+  double* d_partial = nullptr;
+  const int nblk = 64;
+  long long maxL = 0;
+  {
+    p->desc = *d;
+    p->lengths.assign(d->lengths, d->lengths + d->n_signals);
+    p->sigmas.assign(d->sigmas, d->sigmas + d->n_scales);
+    p->desc.lengths = nullptr;
+    p->desc.sigmas = nullptr;
+    p->form = (d->form == 1) ? 1 : 2;
+    p->elem = d->precision == MORLET_FP64 ? 8 : 4;
+    p->spin = d->spin_limit > 0 ? d->spin_limit : DEFAULT_SPIN;
+    p->x_off.resize(p->lengths.size());
+    long long acc = 0;
+    for (size_t i = 0; i < p->lengths.size(); ++i) {
+      p->x_off[i] = acc;
+      acc += p->lengths[i];
+    }
+    CK(cudaGetDevice(&p->device));
+    CK(cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device));
+
+    const double Cxi = pow(1.0 + exp(-d->xi * d->xi) - 2.0 * exp(-0.75 * d->xi * d->xi), -0.5);
+    const double kxi = exp(-0.5 * d->xi * d->xi);
+    for (int s = 0; s < S; ++s) {
+      FitJob& J = jobs[s];
+      const double sg = p->sigmas[s];
+      J.sigma = sg;
+      J.xi = d->xi;
+      J.omega0 = d->xi / sg;
+      J.L = (long long)ceil(wm * sg);
+      J.amp = d->norm ? Cxi * pow(M_PI, -0.25) / sqrt(sg) : 1.0;
+      J.kappa_xi = d->norm ? kxi : 0.0;
+      J.method = d->method == MORLET_GAUSS ? 1 : 0;
+      J.deriv = d->deriv;
+      J.K = d->K;
+      J.fit_tol = d->fit_tol;
+      const int kmax_fit = d->K > 0 ? d->K : KMAX;
+      if (J.method == 0) {
+        J.pc = (long long)floor((d->xi / sg) * (double)J.L / M_PI + 0.5);
+        J.ph_lo = (int)std::max<long long>(0, J.pc - kmax_fit);
+        J.nh = (int)(J.pc + kmax_fit - J.ph_lo);
+      } else {
+        J.pc = 0;
+        J.ph_lo = 0;
+        J.nh = kmax_fit;
+      }
+      if (J.ph_lo + J.nh > J.L) { rc = MORLET_ERR_ARG; goto fail; }  // harmonics must stay below beta p < pi
+      if (d->transform == MORLET_ASFT) {
+        J.n0 = d->n0 > 0 ? d->n0 : std::max(1, (int)floor(sg / 8.0 + 0.5));
+        if (J.n0 > J.L) { rc = MORLET_ERR_ARG; goto fail; }
+        J.alpha = (double)J.n0 / (sg * sg);
+      } else {
+        J.n0 = 0;
+        J.alpha = 0.0;
+      }
+      maxL = std::max(maxL, J.L);
+    }
+    CK(cudaMalloc(&p->d_jobs, sizeof(FitJob) * S));
+    CK(cudaMalloc(&p->d_tabs, sizeof(ScaleTab) * S));
+    CK(cudaMemsetAsync(p->d_tabs, 0, sizeof(ScaleTab) * S, st));
+    CK(cudaMalloc(&d_partial, sizeof(double) * FIT_STRIDE * nblk * S));
+    CK(cudaMemcpyAsync(p->d_jobs, jobs.data(), sizeof(FitJob) * S, cudaMemcpyHostToDevice, st));
+    CK(run_fit(p->d_jobs, S, maxL, d_partial, nblk, p->d_tabs, 0, ITEMS, p->form, st));
+    p->h_tabs.resize(S);
+    CK(cudaMemcpyAsync(p->h_tabs.data(), p->d_tabs, sizeof(ScaleTab) * S, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    p->K_fit = 0;
+    for (int s = 0; s < S; ++s) p->K_fit = std::max(p->K_fit, (int)p->h_tabs[s].K);
+    p->K_kernel = round_k(std::max(p->K_fit, 2));
+    if (p->K_kernel < 0) { rc = MORLET_ERR_UNSUPPORTED; goto fail; }
+    for (int s = 0; s < S; ++s)
+      if (p->h_tabs[s].p0 + p->K_kernel > jobs[s].L) { rc = MORLET_ERR_ARG; goto fail; }
+    CK(run_tables(p->d_tabs, p->d_jobs, S, p->K_kernel, ITEMS, p->form, st));
+    CK(cudaMemcpyAsync(p->h_tabs.data(), p->d_tabs, sizeof(ScaleTab) * S, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+
+    // work tables and status arrays
+    long long slots = 0;
+    rc = setup_launch(p, false, p->fwd, slots);
+    if (rc) goto fail;
+    const bool has_adj = d->method == MORLET_DIRECT && d->transform == MORLET_SFT;
+    long long slots_adj = 0;
+    if (has_adj) {
+      rc = setup_launch(p, true, p->adj, slots_adj);
+      if (rc) goto fail;
+    }
+    p->n_slots = std::max(slots, slots_adj);
+    const int nt_adj = has_adj ? 2 * p->K_kernel : p->K_kernel;
+    if (p->n_slots > 0) {
+      CK(cudaMalloc(&p->d_flags, sizeof(uint32_t) * p->n_slots));
+      CK(cudaMalloc(&p->d_agg, carry_bytes(p) * nt_adj * p->n_slots));
+      CK(cudaMalloc(&p->d_incl, carry_bytes(p) * nt_adj * p->n_slots));
+    }
+    CK(cudaMalloc(&p->d_ticket, sizeof(unsigned long long) * (S + 1)));
+    CK(cudaHostAlloc((void**)&p->h_err, sizeof(int), cudaHostAllocMapped));
+    *p->h_err = 0;
+    CK(cudaHostGetDevicePointer((void**)&p->d_err, p->h_err, 0));
+  }
+  cudaFree(d_partial);
+  *out = p;
+  return MORLET_OK;
+fail:
+  cudaFree(d_partial);
+  morlet_plan_destroy(p);
+  return rc;
+}
+
+int morlet_forward(morlet_plan_t p, const void* x, void* W, void* stream) {
+  if (!p || !x || !W) return MORLET_ERR_ARG;
+  int rc = check_latched(p);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool use_graph = !(p->desc.flags & MORLET_FLAG_NO_GRAPH) && p->skip_tickets == 0;
+  if (!use_graph) return cuda_status(enqueue(p, p->fwd, x, W, 0, p->fwd.n_work, p->d_ticket, true, st));
+  if (!p->gexec || p->g_x != x || p->g_out != W) {
+    // capture memsets + kernel once per (x, W); replays are a single graph launch
+    if (p->gexec) {
+      cudaGraphExecDestroy(p->gexec);
+      p->gexec = nullptr;
+    }
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_status(e);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e2 = enqueue(p, p->fwd, x, W, 0, p->fwd.n_work, p->d_ticket, true, cs);
+      e = cudaStreamEndCapture(cs, &g);
+      if (e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->gexec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return cuda_status(e);
+    p->g_x = x;
+    p->g_out = W;
+  }
+  return cuda_status(cudaGraphLaunch(p->gexec, st));
+}
+
+int morlet_backward(morlet_plan_t p, const void* gW, void* gx, void* stream) {
+  if (!p || !gW || !gx) return MORLET_ERR_ARG;
+  if (!p->adj.func) return MORLET_ERR_UNSUPPORTED;
+  int rc = check_latched(p);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  // One launch per scale, in scale order: the first writes gx, the later ones add to it, so the
+  // sum over scales has a fixed order (deterministic, no float atomics).
+  const int S = (int)p->sigmas.size();
+  for (int s = 0; s < S; ++s) {
+    const cudaError_t e = enqueue(p, p->adj, gW, gx, p->adj.scale_begin[s], p->adj.scale_begin[s + 1],
+                                  p->d_ticket + 1 + s, s == 0, st, s > 0 ? 1 : 0);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return MORLET_OK;
+}
+
+int morlet_last_device_error(morlet_plan_t p, void* stream) {
+  if (!p) return MORLET_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  int rc = check_latched(p);
+  *(volatile int*)p->h_err = 0;
+  p->latched = 0;
+  return rc;
+}
+
+int morlet_plan_info(morlet_plan_t p, int32_t s, int64_t* L, int32_t* p0, int32_t* K, double* m, double* l,
+                     int32_t* n0) {
+  if (!p || s < 0 || s >= (int32_t)p->h_tabs.size()) return MORLET_ERR_ARG;
+  const ScaleTab& t = p->h_tabs[s];
+  if (L) *L = t.L;
+  if (p0) *p0 = t.p0;
+  if (K) *K = t.K;
+  if (m) memcpy(m, t.m, sizeof(double) * KMAX);
+  if (l) memcpy(l, t.l, sizeof(double) * KMAX);
+  if (n0) *n0 = t.n0;
+  return MORLET_OK;
+}
+
+int morlet_plan_stats(morlet_plan_t p, int64_t o[8]) {
+  if (!p || !o) return MORLET_ERR_ARG;
+  o[0] = THREADS;
+  o[1] = ITEMS;
+  o[2] = p->fwd.grid;
+  o[3] = p->fwd.n_work;
+  o[4] = p->fwd.sub_tiles;
+  o[5] = p->fwd.rows_chain;
+  o[6] = p->fwd.rows_halo;
+  o[7] = 1;
+  return MORLET_OK;
+}
+
+int morlet_plan_set_spin_limit(morlet_plan_t p, int64_t polls) {
+  if (!p || polls < 1) return MORLET_ERR_ARG;
+  p->spin = polls;
+  if (p->gexec) {
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+  }
+  return MORLET_OK;
+}
+
+int morlet_debug_skip_tickets(morlet_plan_t p, int64_t skip) {
+  if (!p || skip < 0) return MORLET_ERR_ARG;
+  p->skip_tickets = skip;
+  return MORLET_OK;
+}
+
+int gauss_smooth(const void* x, int64_t N, double sigma, int32_t P, int32_t deriv, int32_t precision, void* y,
+                 void* stream) {
+  if (!x || !y || N < 1 || P < 0 || P + 1 > KMAX || deriv < 0 || deriv > 2) return MORLET_ERR_ARG;
+  if (precision < MORLET_FP32_PLAIN || precision > MORLET_FP64) return MORLET_ERR_ARG;
+  // Plans are cached per key; the cache lives until process exit.
+  static std::mutex mu;
+  static std::map<std::tuple<int, int64_t, double, int, int, int>, morlet_plan_t> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MORLET_ERR_CUDA;
+  morlet_plan_t plan = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_tuple(dev, N, sigma, P, deriv, precision);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      plan = it->second;
+    } else {
+      morlet_plan_desc d{};
+      d.n_signals = 1;
+      d.lengths = &N;
+      d.n_scales = 1;
+      d.sigmas = &sigma;
+      d.K = P + 1;
+      d.method = MORLET_GAUSS;
+      d.transform = MORLET_SFT;
+      d.precision = precision;
+      d.deriv = deriv;
+      const int rc = morlet_plan(&plan, &d, stream);
+      if (rc) return rc;
+      cache[key] = plan;
+    }
+  }
+  return morlet_forward(plan, x, y, stream);
+}
+
+}  // extern "C"

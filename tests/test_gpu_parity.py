@@ -1,0 +1,129 @@
+"""GPU parity: the CUDA library through its C ABI against the CPU oracle on the same seeded inputs.
+
+Tolerances (relative max-abs error over max |W| of the oracle):
+  compensated FP32 (FP32 scan, FP64 carries): 1e-5;  FP64: 1e-12;
+  plain FP32 and ASFT FP32: reported by print, gated only loosely (1e-3 / 1e-4) since the method's
+  plain-FP32 error grows with the row length.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import paper_2110_11866_gb300 as m
+import workloads as WL
+from oracle import morlet as om
+from tests.gpu_helpers import gpu_forward, oracle_forward, rel_err
+
+pytestmark = pytest.mark.gpu
+
+TOL = {m.MORLET_FP32_COMP: 1e-5, m.MORLET_FP64: 1e-12, m.MORLET_FP32_PLAIN: 1e-3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+@pytest.mark.parametrize("form", [m.MORLET_FORM_ROTATING, m.MORLET_FORM_KERNEL])
+def test_c1_fp64_single_signal(form):
+    """Config 1: N = 4096 N(0,1) float64, sigma = 64, K = 4, FP64 path vs the double-double oracle."""
+    w = WL.c1_fp64_single()
+    x = w.signals[0]
+    plan, out = gpu_forward([x], [64.0], K=4, precision=m.MORLET_FP64, form=form)
+    ref = oracle_forward(x, 64.0, 4)
+    e = rel_err(out[0][0], ref)
+    print(f"c1 fp64 form={form} rel err {e:.3e}")
+    assert e < 1e-12
+    # the fit: same harmonics and coefficients as the oracle's independent FP64 least squares
+    info = m.morlet_plan_info(plan, 0)
+    fit = om.fit_direct(64.0, 6.0, 4)
+    assert info["p0"] == fit["p0"] and info["L"] == fit["L"] == 256
+    assert np.abs(np.array(info["m"]) - fit["m"]).max() < 1e-12
+    assert np.abs(np.array(info["l"]) - fit["l"]).max() < 1e-12
+    # approximation error of the method itself (reported, K = 4, L = 4 sigma)
+    true = om.morlet_true_direct(x, 64.0, 6.0)
+    print(f"c1 SFT vs direct +-8 sigma Morlet: {rel_err(ref, true):.3e}")
+
+
+@pytest.mark.parametrize("precision", [m.MORLET_FP32_COMP, m.MORLET_FP32_PLAIN, m.MORLET_FP64])
+@pytest.mark.parametrize("form", [m.MORLET_FORM_ROTATING, m.MORLET_FORM_KERNEL])
+@pytest.mark.parametrize("K", [2, 3, 4, 5, 6, 8, 12])
+def test_small_shapes(precision, form, K):
+    """Ragged lengths that straddle tile edges (4096 outputs per sub-tile) and short windows."""
+    rng = np.random.default_rng(100 + K)
+    lens = [1, 7, 4095, 4096, 4097, 9000, 20000]
+    sigs = [rng.standard_normal(n).astype(np.float32) for n in lens]
+    sigmas = [8.0, 37.5, 300.0, 1500.0]
+    plan, out = gpu_forward(sigs, sigmas, K=K, precision=precision, form=form)
+    worst = 0.0
+    for i, x in enumerate(sigs):
+        for s, sg in enumerate(sigmas):
+            ref = oracle_forward(x, sg, K)
+            worst = max(worst, rel_err(out[i][s], ref))
+    print(f"K={K} precision={precision} form={form} worst rel err {worst:.3e}")
+    assert worst < TOL[precision]
+
+
+def test_n_shorter_than_window():
+    """Signals far shorter than the window (L >> N): outputs still equal the zero-extended sums."""
+    rng = np.random.default_rng(5)
+    sigs = [rng.standard_normal(n).astype(np.float32) for n in (3, 100, 1000)]
+    plan, out = gpu_forward(sigs, [2000.0, 10321.0], K=4)
+    for i, x in enumerate(sigs):
+        for s, sg in enumerate([2000.0, 10321.0]):
+            assert rel_err(out[i][s], oracle_forward(x, sg, 4)) < 1e-5
+
+
+@pytest.mark.parametrize("sigma", WL.C2_SIGMAS)
+@pytest.mark.parametrize("K", WL.C2_KS)
+def test_c2_chirps_forms(sigma, K):
+    """Config 2: N = 102400 chirps + noise, sigma sweep x K x {plain, compensated, ASFT} FP32."""
+    x = WL.c2_chirps()
+    ref = oracle_forward(x, sigma, K)
+    _, comp = gpu_forward([x], [sigma], K=K, precision=m.MORLET_FP32_COMP)
+    _, plain = gpu_forward([x], [sigma], K=K, precision=m.MORLET_FP32_PLAIN)
+    _, ki = gpu_forward([x], [sigma], K=K, precision=m.MORLET_FP32_COMP, form=m.MORLET_FORM_KERNEL)
+    ea = rel_err(comp[0][0], ref)
+    ep = rel_err(plain[0][0], ref)
+    ek = rel_err(ki[0][0], ref)
+    refa = oracle_forward(x, sigma, K, transform=m.MORLET_ASFT)
+    _, asft = gpu_forward([x], [sigma], K=K, precision=m.MORLET_FP32_PLAIN, transform=m.MORLET_ASFT)
+    es = rel_err(asft[0][0], refa)
+    print(f"c2 sigma={sigma} K={K}: comp {ea:.2e} kernel-integral {ek:.2e} plain {ep:.2e} asft {es:.2e}")
+    assert ea < 1e-5 and ek < 1e-5
+    assert ep < 1e-3
+    assert es < 1e-4
+
+
+def test_deterministic_replay():
+    """Two launches (graph replays) give bit-identical outputs."""
+    x = WL.white(3, 300000)
+    import torch
+    plan = m.morlet_plan([len(x)], [12.0, 900.0, 5000.0], K=4)
+    xt = torch.from_numpy(x).cuda()
+    W1 = torch.empty(len(x) * 3, dtype=torch.complex64, device="cuda")
+    W2 = torch.empty_like(W1)
+    m.morlet_forward(plan, xt, W1)
+    m.morlet_forward(plan, xt, W2)
+    torch.cuda.synchronize()
+    assert torch.equal(W1, W2)
+
+
+def test_timeout_is_reported_and_context_survives():
+    """A tile whose predecessor never publishes gives up after the bounded wait: the call reports
+    MORLET_ERR_TIMEOUT and later launches on the same context still work."""
+    import torch
+    x = WL.white(4, 200000)
+    plan = m.morlet_plan([len(x)], [3000.0], K=4, precision=m.MORLET_FP32_PLAIN, flags=m.MORLET_FLAG_NO_GRAPH)
+    m.morlet_plan_set_spin_limit(plan, 2000)
+    xt = torch.from_numpy(x).cuda()
+    W = torch.empty(len(x), dtype=torch.complex64, device="cuda")
+    m.morlet_debug_skip_tickets(plan, 1)   # work item 0 (the row's first tile) is never processed
+    m.morlet_forward(plan, xt, W)
+    assert m.morlet_last_device_error(plan) == m.MORLET_ERR_TIMEOUT
+    m.morlet_forward(plan, xt, W)          # clean run afterwards
+    assert m.morlet_last_device_error(plan) == 0
+    ref = oracle_forward(x, 3000.0, 4)
+    assert rel_err(W.cpu().numpy(), ref) < 1e-3

@@ -1,0 +1,207 @@
+"""GPU parity at full workload sizes (sampled outputs against the oracle's direct sums), the adjoint,
+autograd and Gaussian smoothing."""
+import math
+
+import numpy as np
+import pytest
+
+import paper_2110_11866_gb300 as m
+import workloads as WL
+from oracle import morlet as om
+from oracle import sft_dd
+from tests.gpu_helpers import gpu_forward, oracle_forward, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _sample_idx(N, L, rng, n=24):
+    """Sampled output indices: both ends (boundary windows), tile edges and random interior points."""
+    fixed = [0, 1, N - 1, N - 2, min(N - 1, L), min(N - 1, 4095), min(N - 1, 4096), N // 2]
+    return np.unique(np.concatenate([fixed, rng.integers(0, N, n)]))
+
+
+def test_c3_scalogram_full_size_sampled():
+    """Config 3 at full size (256 ragged signals x 32 scales, 1.24 G outputs), compensated FP32, one
+    launch. Every (signal, scale) row is checked at sampled outputs against the direct sum
+    sum_k psi_hat[k] x[n-k] with the oracle's own fit; tolerance 1e-5 of the row's max |W| estimated
+    from the sampled oracle values and the GPU row."""
+    import torch
+    w = WL.c3_scalogram()
+    sigmas = w.sigmas
+    fits = [om.fit_direct(s, 6.0, 4) for s in sigmas]
+    lens = w.lengths
+    x = torch.from_numpy(w.concat()).cuda()
+    plan = m.morlet_plan(lens, sigmas, K=4, precision=m.MORLET_FP32_COMP)
+    W = torch.empty(sum(lens) * len(sigmas), dtype=torch.complex64, device="cuda")
+    m.morlet_forward(plan, x, W)
+    torch.cuda.synchronize()
+    assert m.morlet_last_device_error(plan) == 0
+    rng = np.random.default_rng(0)
+    S = len(sigmas)
+    off = 0
+    worst = 0.0
+    rows = list(range(0, 256, 5)) + [int(np.argmax(lens)), int(np.argmin(lens))]
+    offs = np.concatenate([[0], np.cumsum(lens)])
+    for i in rows:
+        xi = w.signals[i].astype(np.float64)
+        Ni = lens[i]
+        for s in range(0, S, 3):
+            row0 = S * int(offs[i]) + s * Ni
+            Wrow = W[row0:row0 + Ni]
+            idx = _sample_idx(Ni, fits[s]["L"], rng)
+            ref = om.morlet_sft_direct(xi, fits[s], idx)
+            got = Wrow[torch.from_numpy(idx).cuda()].cpu().numpy()
+            scale = max(float(Wrow.abs().max().item()), np.abs(ref).max())
+            worst = max(worst, float(np.abs(got - ref).max() / scale))
+    print(f"c3 full size: worst sampled rel err {worst:.3e} over {len(rows)} signals")
+    assert worst < 1e-5
+    del W
+
+
+@pytest.mark.parametrize("sigma", WL.C5_SIGMAS)
+def test_c5_long_signal_sampled(sigma):
+    """Config 5: one 2^24-sample pink-noise signal, K = 6, compensated FP32 and FP64, sampled outputs
+    (multi-tile look-back carries at large n) against the direct sums."""
+    import torch
+    x = WL.c5_pink()
+    fit = om.fit_direct(sigma, 6.0, 6)
+    rng = np.random.default_rng(int(sigma))
+    N = len(x)
+    idx = _sample_idx(N, fit["L"], rng, n=16)
+    idx = np.unique(np.concatenate([idx, [N - 4096 * 3, N - 17, 12345678]]))
+    ref = om.morlet_sft_direct(x.astype(np.float64), fit, idx)
+    for prec, tol in ((m.MORLET_FP32_COMP, 1e-5), (m.MORLET_FP64, 1e-12)):
+        xs = x.astype(np.float64) if prec == m.MORLET_FP64 else x
+        plan, out = gpu_forward([xs], [sigma], K=6, precision=prec)
+        row = out[0][0]
+        e = np.abs(row[idx] - ref).max() / np.abs(row).max()
+        print(f"c5 sigma={sigma} precision={prec}: sampled rel err {e:.3e}")
+        assert e < tol
+        del out
+
+
+def _loss_terms(W, wts):
+    return wts * np.log(1e-6 + np.abs(W) ** 2)
+
+
+def test_c4_adjoint_vs_direct_and_finite_differences():
+    """Config 4: batch 64 x 65536, 16 scales, K = 4; loss = sum w log(1e-6 + |W|^2).
+    (a) FP32-compensated adjoint against the oracle's direct-convolution adjoint at sampled
+        coordinates (tolerance 1e-5 of max |gx|);
+    (b) FP64 adjoint against central finite differences (eps = 1e-6) of the FP64 transform on 32
+        random coordinates; each loss difference is summed over the outputs the coordinate touches
+        (|n - t| <= L_s per scale), so that rounding of the 67 M-term sum does not swamp it."""
+    import torch
+    w = WL.c4_batch()
+    wts = WL.c4_loss_weights()
+    sig = w.sigmas
+    S, B, N = len(sig), len(w.signals), len(w.signals[0])
+    fits = [om.fit_direct(s, 6.0, 4) for s in sig]
+    xb = np.stack(w.signals)
+    wt = torch.from_numpy(wts).cuda()
+
+    def grad_W(W):  # dLoss/dRe W + i dLoss/dIm W, laid out [signal][scale][n]
+        Wv = W.view(B, S, N)
+        return (wt * 2 * Wv / (1e-6 + Wv.abs() ** 2)).reshape(-1)
+
+    # (a) compensated FP32
+    plan = m.morlet_plan([N] * B, sig, K=4, precision=m.MORLET_FP32_COMP)
+    x = torch.from_numpy(xb.reshape(-1)).cuda()
+    W = torch.empty(B * S * N, dtype=torch.complex64, device="cuda")
+    m.morlet_forward(plan, x, W)
+    g = grad_W(W).to(torch.complex64).contiguous()
+    gx = torch.empty(B * N, dtype=torch.float32, device="cuda")
+    m.morlet_backward(plan, g, gx)
+    torch.cuda.synchronize()
+    assert m.morlet_last_device_error(plan) == 0
+    rng = np.random.default_rng(7)
+    gh = g.view(B, S, N).cpu().numpy().astype(np.complex128)
+    gxh = gx.view(B, N).cpu().numpy()
+    worst = 0.0
+    for b in rng.choice(B, 4, replace=False):
+        idx = _sample_idx(N, fits[-1]["L"], rng, n=12)
+        ref = sum(om.adjoint_direct(gh[b, s], fits[s], idx) for s in range(S))
+        worst = max(worst, np.abs(gxh[b, idx] - ref).max() / np.abs(gxh[b]).max())
+    print(f"c4 adjoint fp32-comp vs direct adjoint: {worst:.3e}")
+    assert worst < 1e-5
+
+    # (b) FP64 adjoint vs central differences of the FP64 forward
+    plan64 = m.morlet_plan([N] * B, sig, K=4, precision=m.MORLET_FP64)
+    x64 = torch.from_numpy(xb.reshape(-1).astype(np.float64)).cuda()
+    W64 = torch.empty(B * S * N, dtype=torch.complex128, device="cuda")
+    m.morlet_forward(plan64, x64, W64)
+    g64 = grad_W(W64).to(torch.complex128).contiguous()
+    gx64 = torch.empty(B * N, dtype=torch.float64, device="cuda")
+    m.morlet_backward(plan64, g64, gx64)
+    torch.cuda.synchronize()
+    Ls = [f["L"] for f in fits]
+    eps = 1e-6
+    Wp = torch.empty_like(W64)
+    Wm = torch.empty_like(W64)
+    worst_fd = 0.0
+    for _ in range(32):
+        b, t = int(rng.integers(B)), int(rng.integers(N))
+        xp = x64.clone()
+        xp[b * N + t] += eps
+        xm = x64.clone()
+        xm[b * N + t] -= eps
+        m.morlet_forward(plan64, xp, Wp)
+        m.morlet_forward(plan64, xm, Wm)
+        d = 0.0
+        for s in range(S):
+            lo, hi = max(0, t - Ls[s]), min(N, t + Ls[s] + 1)
+            base = (b * S + s) * N
+            lp = torch.log(1e-6 + Wp[base + lo:base + hi].abs() ** 2)
+            lm = torch.log(1e-6 + Wm[base + lo:base + hi].abs() ** 2)
+            d += float((wt[b, s, lo:hi].double() * (lp - lm)).sum().item())
+        fd = d / (2 * eps)
+        an = float(gx64[b * N + t].item())
+        worst_fd = max(worst_fd, abs(fd - an) / (abs(an) + 1e-3 * float(gx64.abs().max().item())))
+    print(f"c4 adjoint fp64 vs central differences: worst rel {worst_fd:.3e}")
+    assert worst_fd < 1e-5
+
+
+def test_autograd_function_matches_backward():
+    import torch
+    from paper_2110_11866_gb300.torch_ops import MorletFn, MorletTransform
+    rng = np.random.default_rng(3)
+    lens = [5000, 12000]
+    tr = MorletTransform(lens, [10.0, 80.0], K=4, precision=m.MORLET_FP32_COMP)
+    x = torch.from_numpy(rng.standard_normal(sum(lens)).astype(np.float32)).cuda().requires_grad_(True)
+    W = MorletFn.apply(x, tr)
+    wts = torch.from_numpy(rng.standard_normal(W.numel()).astype(np.float32)).cuda()
+    loss = (wts * torch.log(1e-6 + W.abs() ** 2)).sum()
+    loss.backward()
+    g = (wts * 2 * W / (1e-6 + W.abs() ** 2)).detach().to(torch.complex64)
+    gx = tr.backward(g)
+    torch.cuda.synchronize()
+    assert torch.allclose(x.grad, gx, rtol=0, atol=1e-6 * float(gx.abs().max()))
+
+
+@pytest.mark.parametrize("deriv", [0, 1, 2])
+@pytest.mark.parametrize("precision", [m.MORLET_FP32_COMP, m.MORLET_FP64])
+def test_gauss_smooth(deriv, precision):
+    """gauss_smooth (eq. GsSFT and its derivative forms) against the oracle's kernel integral."""
+    import torch
+    rng = np.random.default_rng(deriv)
+    N = 70000
+    x = rng.standard_normal(N)
+    for sigma, P in ((5.0, 3), (40.0, 4), (700.0, 6)):
+        gf = om.fit_gauss(sigma, P, deriv)
+        ref = sft_dd.sft_gauss(x, gf)
+        dt = torch.float64 if precision == m.MORLET_FP64 else torch.float32
+        xt = torch.from_numpy(x).to(dt).cuda()
+        y = torch.empty(N, dtype=dt, device="cuda")
+        m.gauss_smooth(xt, N, sigma, P, deriv, precision, y)
+        torch.cuda.synchronize()
+        if precision != m.MORLET_FP64:
+            ref = sft_dd.sft_gauss(x.astype(np.float32).astype(np.float64), gf)
+        e = rel_err(y.cpu().numpy(), ref)
+        print(f"gauss deriv={deriv} sigma={sigma} P={P} precision={precision}: {e:.2e}")
+        assert e < (1e-12 if precision == m.MORLET_FP64 else 1e-5)
