@@ -168,6 +168,27 @@ int morlet_plan_set_spin_limit(morlet_plan_t plan, int64_t polls);
  */
 int morlet_debug_skip_tickets(morlet_plan_t plan, int64_t skip);
 
+/*
+ * morlet_forward_noalloc - forward transform that allocates no memory (no cudaMalloc, no cudaFree,
+ * no allocating library call), for callers that cannot allocate device memory themselves, such as
+ * code running inside a framework or allocator that owns all device memory.
+ * The paper has no counterpart; this is a deployment convenience of this library.
+ * One real FP32 signal x[0..N-1] (device), one scale sigma, omega0 = xi / sigma, K terms (1..12),
+ * SFT, compensated FP32, unnormalised Morlet (norm 0), L = ceil(4 sigma); W: device complex64[N],
+ * the caller's. Results equal morlet_plan + morlet_forward with the same parameters.
+ * All working memory (fit, tables, tile table, look-back status) lives in one fixed device array of
+ * about 7.2 MB inside the library; every GPU that loads the library holds it until the process exits.
+ * Limits: the row may need at most 16384 sub-tiles of 4096 outputs (N up to about 6.7e7 for short
+ * windows) and at most 16384 look-back slots; larger sizes return MORLET_ERR_ARG.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture. Each call synchronises `stream`
+ * once at entry to read the error word of the previous call (MORLET_ERR_TIMEOUT if its bounded
+ * cross-tile wait gave up), then enqueues its kernels asynchronously. All calls on a device share the
+ * array: calls whose kernels overlap on the GPU (different streams, no ordering) race and corrupt
+ * each other's results; order them on one stream.
+ */
+int morlet_forward_noalloc(const void* x, int64_t N, double sigma, double xi, int32_t K, void* W, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

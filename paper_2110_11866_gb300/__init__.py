@@ -20,6 +20,7 @@ __all__ = [
     "morlet_plan", "morlet_forward", "morlet_backward", "gauss_smooth", "morlet_plan_destroy",
     "morlet_strerror", "morlet_last_device_error", "morlet_plan_info", "morlet_plan_stats",
     "morlet_plan_set_spin_limit", "morlet_debug_skip_tickets", "EXPORTED_SYMBOLS", "source_hash",
+    "morlet_forward_noalloc",
 ]
 
 MORLET_OK, MORLET_ERR_ARG, MORLET_ERR_UNSUPPORTED, MORLET_ERR_CUDA, MORLET_ERR_TIMEOUT, MORLET_ERR_NOMEM = (
@@ -33,7 +34,7 @@ MORLET_FLAG_NO_GRAPH, MORLET_FLAG_AUTOTUNE, MORLET_FLAG_NO_HALO = 1, 2, 4
 EXPORTED_SYMBOLS = [
     "morlet_plan", "morlet_forward", "morlet_backward", "gauss_smooth", "morlet_plan_destroy",
     "morlet_strerror", "morlet_last_device_error", "morlet_plan_info", "morlet_plan_stats",
-    "morlet_plan_set_spin_limit", "morlet_debug_skip_tickets",
+    "morlet_plan_set_spin_limit", "morlet_debug_skip_tickets", "morlet_forward_noalloc",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -100,8 +101,10 @@ def lib():
     L.morlet_plan_stats.argtypes = [vp, ctypes.POINTER(i64)]
     L.morlet_plan_set_spin_limit.argtypes = [vp, i64]
     L.morlet_debug_skip_tickets.argtypes = [vp, i64]
+    L.morlet_forward_noalloc.argtypes = [vp, i64, ctypes.c_double, ctypes.c_double, i32, vp, vp]
     for f in ("morlet_plan", "morlet_forward", "morlet_backward", "gauss_smooth", "morlet_last_device_error",
-              "morlet_plan_info", "morlet_plan_stats", "morlet_plan_set_spin_limit", "morlet_debug_skip_tickets"):
+              "morlet_plan_info", "morlet_plan_stats", "morlet_plan_set_spin_limit", "morlet_debug_skip_tickets",
+              "morlet_forward_noalloc"):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
@@ -226,3 +229,10 @@ def morlet_plan_set_spin_limit(plan: Plan, polls: int):
 
 def morlet_debug_skip_tickets(plan: Plan, skip: int):
     _check(lib().morlet_debug_skip_tickets(plan.handle, int(skip)), "morlet_debug_skip_tickets")
+
+
+def morlet_forward_noalloc(x, N, sigma, xi, K, W, stream=None):
+    """Forward transform of one FP32 signal at one scale using only the library's fixed device
+    scratch array (no allocation anywhere); for callers that cannot allocate device memory."""
+    _check(lib().morlet_forward_noalloc(_ptr(x), int(N), float(sigma), float(xi), int(K), _ptr(W),
+                                        _stream(stream)), "morlet_forward_noalloc")

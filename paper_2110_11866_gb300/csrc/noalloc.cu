@@ -1,0 +1,235 @@
+// morlet_forward_noalloc: a forward transform that allocates no memory at all, for callers that
+// cannot call cudaMalloc (for example code running under an allocator that forbids it, or inside a
+// framework that owns all device memory). Every buffer the transform needs besides the caller's
+// input and output lives in one file-scope device array of fixed size, held by each GPU that loads
+// this library until the process exits.
+#include <math.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "../../include/morlet_sft.h"
+#include "plan_internal.h"
+
+namespace msft {
+
+namespace {
+
+constexpr int NA_THREADS_ITEMS = 16;
+constexpr long long NA_TILE = (long long)THREADS * NA_THREADS_ITEMS;
+constexpr long long NA_MAX_ITEMS = 16384;  // work items (sub-tiles) one call may use
+constexpr long long NA_MAX_SLOTS = 16384;  // look-back status slots one call may use
+constexpr int NA_FIT_BLOCKS = 64;
+
+// Byte layout of the scratch array (every part 256-byte aligned).
+constexpr size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
+constexpr size_t OFF_TAB = 0;
+constexpr size_t OFF_JOB = al(OFF_TAB + sizeof(ScaleTab));
+constexpr size_t OFF_PART = al(OFF_JOB + sizeof(FitJob));
+constexpr size_t OFF_CHAIN = al(OFF_PART + sizeof(double) * FIT_STRIDE * NA_FIT_BLOCKS);
+constexpr size_t OFF_WORK = al(OFF_CHAIN + sizeof(ChainDesc));
+constexpr size_t OFF_FLAGS = al(OFF_WORK + sizeof(WorkItem) * NA_MAX_ITEMS);
+constexpr size_t OFF_AGG = al(OFF_FLAGS + sizeof(uint32_t) * NA_MAX_SLOTS);
+constexpr size_t OFF_INCL = al(OFF_AGG + sizeof(double2) * KMAX * NA_MAX_SLOTS);
+constexpr size_t OFF_TICKET = al(OFF_INCL + sizeof(double2) * KMAX * NA_MAX_SLOTS);
+constexpr size_t OFF_ERR = al(OFF_TICKET + sizeof(unsigned long long));
+constexpr size_t NA_SCRATCH_BYTES = al(OFF_ERR + sizeof(int));
+
+// The scratch array. In host code `na_scratch` is only a stand-in symbol, not a device address:
+// the address every kernel receives comes from cudaGetSymbolAddress, taken once per device.
+static __device__ __align__(256) unsigned char na_scratch[NA_SCRATCH_BYTES];
+
+constexpr int NA_MAX_DEVICES = 64;
+std::mutex na_mu;
+unsigned char* na_addr[NA_MAX_DEVICES] = {nullptr};
+
+// The work decomposition of the plan for one row, compensated precision: short windows (2L <= 2T)
+// get one segment per output sub-tile with its window prologue; long windows get look-back chains
+// over segments of max(4, ceil(4L / T)) output sub-tiles. With out == nullptr only counts the items.
+struct RowShape {
+  long long N, L, D;
+};
+
+__host__ __device__ long long row_items(const RowShape r, WorkItem* out, long long* n_slots) {
+  const long long T = NA_TILE;
+  const long long k_min = -((r.D + T - 1) / T);
+  const long long n_out = (r.N + T - 1) / T;
+  const long long h = (2 * r.L + T - 1) / T;
+  long long n = 0, slots = 0;
+  if (h <= 2) {
+    for (long long k0 = 0; k0 < n_out; ++k0) {
+      const long long t0 = r.D + k0 * T;
+      const long long t_dom = t0 - 2 * r.L > 0 ? t0 - 2 * r.L : 0;
+      long long kf = (t_dom - r.D >= 0) ? (t_dom - r.D) / T : -((r.D - t_dom + T - 1) / T);
+      if (kf < k_min) kf = k_min;
+      if (out) {
+        WorkItem w{};
+        w.chain = 0;
+        w.k_first = kf;
+        w.n_sub = (int)(k0 + 1 - kf);
+        w.k_out = k0;
+        w.t_dom = t_dom;
+        w.slot = -1;
+        w.slot_first = -1;
+        out[n] = w;
+      }
+      ++n;
+    }
+  } else {
+    long long seg = (4 * r.L + T - 1) / T;
+    if (seg < 4) seg = 4;
+    for (long long k0 = 0; k0 < n_out; k0 += seg) {
+      const long long t0 = r.D + k0 * T;
+      const long long t_dom = t0 - 2 * r.L > 0 ? t0 - 2 * r.L : 0;
+      long long kf = (t_dom - r.D >= 0) ? (t_dom - r.D) / T : -((r.D - t_dom + T - 1) / T);
+      if (kf < k_min) kf = k_min;
+      const long long kend = (k0 + seg < n_out) ? k0 + seg : n_out;
+      const long long first = slots;
+      for (long long k = kf; k < kend; ++k) {
+        if (out) {
+          WorkItem w{};
+          w.chain = 0;
+          w.k_first = k;
+          w.n_sub = 1;
+          w.k_out = k0;
+          w.t_dom = t_dom;
+          w.slot = slots;
+          w.slot_first = first;
+          out[n] = w;
+        }
+        ++n;
+        ++slots;
+      }
+    }
+  }
+  if (n_slots) *n_slots = slots;
+  return n;
+}
+
+// Writes the same items row_items counted on the host (same shape, same arithmetic).
+__global__ void na_build_row(RowShape r, ChainDesc* chain, WorkItem* work) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    row_items(r, work, nullptr);
+    ChainDesc c{};
+    c.x_off = 0;
+    c.n = r.N;
+    c.out_off = 0;
+    c.scale = 0;
+    *chain = c;
+  }
+}
+
+int na_status(cudaError_t e) {
+  if (e == cudaSuccess) return MORLET_OK;
+  if (e == cudaErrorMemoryAllocation) return MORLET_ERR_NOMEM;
+  return MORLET_ERR_CUDA;
+}
+
+}  // namespace
+}  // namespace msft
+
+using namespace msft;
+
+extern "C" int morlet_forward_noalloc(const void* x, int64_t N, double sigma, double xi, int32_t K, void* W,
+                                      void* stream) {
+  if (!x || !W || N < 1 || !(sigma >= 0.5) || !(sigma < 1e9) || !(xi >= 0.0 && xi < 1e6)) return MORLET_ERR_ARG;
+  if (K < 1 || K > KMAX) return MORLET_ERR_ARG;
+  int kk = -1;
+  for (int i = 0; i < N_KBUILT; ++i)
+    if (kbuilt(i) >= std::max(K, 2)) {
+      kk = kbuilt(i);
+      break;
+    }
+  if (kk < 0) return MORLET_ERR_UNSUPPORTED;
+  const long long L = (long long)ceil(4.0 * sigma);
+  const long long pc = (long long)floor((xi / sigma) * (double)L / M_PI + 0.5);
+  const long long ph_lo = std::max<long long>(0, pc - K);
+  if (pc + kk > L) return MORLET_ERR_ARG;  // every harmonic p0 + j must stay below L (beta p < pi)
+  // size limits of the scratch array
+  RowShape r{N, L, L};
+  long long n_slots = 0;
+  const long long n_work = row_items(r, nullptr, &n_slots);
+  if (n_work > NA_MAX_ITEMS || n_slots > NA_MAX_SLOTS) return MORLET_ERR_ARG;
+
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return na_status(e);
+  if (dev < 0 || dev >= NA_MAX_DEVICES) return MORLET_ERR_UNSUPPORTED;
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(na_mu);
+    if (!na_addr[dev]) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, na_scratch);  // device address of the array on this device
+      if (e != cudaSuccess || !ptr) return na_status(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+      na_addr[dev] = (unsigned char*)ptr;
+    }
+    base = na_addr[dev];
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+
+  // a timeout latched by the previous call on this device is reported now
+  int prev_err = 0;
+  e = cudaMemcpyAsync(&prev_err, base + OFF_ERR, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return na_status(e);
+
+  FitJob J{};
+  J.sigma = sigma;
+  J.xi = xi;
+  J.omega0 = xi / sigma;
+  J.L = L;
+  J.amp = 1.0;
+  J.kappa_xi = 0.0;
+  J.method = 0;
+  J.K = K;
+  J.pc = pc;
+  J.ph_lo = (int)ph_lo;
+  J.nh = (int)(pc + K - ph_lo);
+  J.n0 = 0;
+  J.alpha = 0.0;
+  FitJob* d_job = (FitJob*)(base + OFF_JOB);
+  ScaleTab* d_tab = (ScaleTab*)(base + OFF_TAB);
+  e = cudaMemcpyAsync(d_job, &J, sizeof(FitJob), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_tab, 0, sizeof(ScaleTab), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + OFF_ERR, 0, sizeof(int), st);
+  if (e == cudaSuccess)
+    e = run_fit(d_job, 1, L, (double*)(base + OFF_PART), NA_FIT_BLOCKS, d_tab, kk, NA_THREADS_ITEMS, 2, st);
+  if (e == cudaSuccess) e = run_tables(d_tab, d_job, 1, kk, NA_THREADS_ITEMS, 2, st);
+  ChainDesc* d_chain = (ChainDesc*)(base + OFF_CHAIN);
+  WorkItem* d_work = (WorkItem*)(base + OFF_WORK);
+  if (e == cudaSuccess) {
+    na_build_row<<<1, 1, 0, st>>>(r, d_chain, d_work);
+    e = cudaGetLastError();
+  }
+  // the counter and the status flags must start at zero for every call
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + OFF_TICKET, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess && n_slots > 0) e = cudaMemsetAsync(base + OFF_FLAGS, 0, sizeof(uint32_t) * n_slots, st);
+  if (e != cudaSuccess) return na_status(e);
+
+  const void* func = kernel_for(V_RF_F32C_MORLET, kk);
+  if (!func) return MORLET_ERR_UNSUPPORTED;
+  int sms = 0, occ = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, func, THREADS, 0);
+  if (e != cudaSuccess) return na_status(e);
+  KParams kp{};
+  kp.x = x;
+  kp.out = W;
+  kp.work = d_work;
+  kp.n_work = n_work;
+  kp.chains = d_chain;
+  kp.tabs = d_tab;
+  kp.flags = (uint32_t*)(base + OFF_FLAGS);
+  kp.agg = base + OFF_AGG;
+  kp.incl = base + OFF_INCL;
+  kp.ticket = (unsigned long long*)(base + OFF_TICKET);
+  kp.err = (int*)(base + OFF_ERR);
+  kp.spin_limit = 1LL << 20;
+  kp.accumulate = 0;
+  void* args[] = {&kp};
+  const int grid = (int)std::min<long long>((long long)std::max(occ, 1) * sms, n_work);
+  e = cudaLaunchKernel(func, dim3(grid), dim3(THREADS), args, 0, st);
+  if (e != cudaSuccess) return na_status(e);
+  return prev_err ? MORLET_ERR_TIMEOUT : MORLET_OK;
+}
