@@ -30,18 +30,25 @@ struct ChainDesc {
   int32_t pad;
 };
 
-// One unit of work: `n_sub` consecutive sub-tiles of one row. Sub-tile k covers scan positions
-// t in [D + k*T, D + (k+1)*T) whose outputs are n = t - D. Samples before t_dom count as zero
-// (window recomputed from t_dom, no look-back) when slot < 0; otherwise the state entering the
-// first sub-tile comes from the look-back over status slots [slot_first, slot).
+// One unit of work: `n_sub` consecutive sub-tiles of one row, sub-tile s covering scan positions
+// t in [t_a + s*T, t_a + (s+1)*T) (the output of position t is n = t - D). Samples before t_dom
+// count as zero; outputs are stored for positions in [t_out, t_end). When slot < 0 the scan starts
+// from a zero state at t_a (the window is recomputed from t_dom); otherwise the state entering the
+// work item comes from the look-back over status slots [slot_first, slot).
 struct WorkItem {
+  int64_t x_off;       // the row: first input element, length, first output element, scale
+  int64_t n;
+  int64_t out_off;
+  int32_t scale;
   int32_t chain;
   int32_t n_sub;
-  int64_t k_first;
-  int64_t k_out;       // sub-tiles k >= k_out store outputs
+  int32_t pad;
+  int64_t t_a;
   int64_t t_dom;
-  int64_t slot;        // status slot of sub-tile k_first, or -1
-  int64_t slot_first;  // status slot of the row's first sub-tile
+  int64_t t_out;
+  int64_t t_end;
+  int64_t slot;        // status slot of this work item, or -1
+  int64_t slot_first;  // status slot of the first work item of the segment
 };
 
 // Per-scale constants, all computed on the GPU in FP64 from the fit (tables.cu).
@@ -63,6 +70,12 @@ struct ScaleTab {
   double2 pw_wofs[8][KMAX];   // rho^{items * 32 * w}
   double2 pw_lane[32][KMAX];  // rho^{items * lane}
   double2 pw_tile[33][KMAX];  // rho^{THREADS * items * q}
+  const float2* ph_hi;        // kernel-integral form: e^{i pi 1024 a / L}, a = 0 .. 2L/1024
+  const float2* ph_lo;        // kernel-integral form: e^{i pi b / L}, b = 0 .. 1023
+  // FP32 copies for the warp-independent kernel
+  float2 f_pw_thr[5][KMAX];   // rho^{items * 2^l}
+  float2 f_pw_lane[32][KMAX]; // rho^{items * lane}
+  float2 f_pwt[2][KMAX];      // rho^{items * 32} as hi + lo
 };
 
 struct KParams {
@@ -78,6 +91,7 @@ struct KParams {
   unsigned long long* ticket;
   int* err;                  // host-mapped error word (device view)
   long long spin_limit;
+  int64_t n_chain;           // work items [0, n_chain) use the look-back; later ones are independent
   int accumulate;            // adjoint: add to the output instead of overwriting it
 };
 
@@ -157,8 +171,107 @@ __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// ------------------------------------------------------------------------------------------------
+// Two-float ("double-single") arithmetic for the cross-tile carries of the compensated precision:
+// a value is hi + lo with |lo| <= ulp(hi)/2, kept exact by error-free transformations on the FP32
+// pipe (GB300's FP64 rate is a small fraction of its FP32 rate). Knuth's TwoSum, Dekker's
+// Fast2Sum and an FMA-based TwoProduct.
+// ------------------------------------------------------------------------------------------------
+
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return DF{s, b - (s - a)};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb);
+  return fast_two_sum(s, e + a.lo + b.lo);
+}
+
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+
+// complex two-float
+struct DFC {
+  DF re, im;
+};
+
+__device__ __forceinline__ DFC dfc_add(DFC a, DFC b) { return DFC{df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ DFC dfc_mul(DFC a, DFC b) {
+  return DFC{df_add(df_mul(a.re, b.re), df_neg(df_mul(a.im, b.im))), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+__device__ __forceinline__ DFC dfc_from_d2(double2 v) {
+  const float rh = (float)v.x, ih = (float)v.y;
+  return DFC{DF{rh, (float)(v.x - (double)rh)}, DF{ih, (float)(v.y - (double)ih)}};
+}
+
+// Carry arithmetic selected by the carry type: float2 (plain), DFC (compensated), double2 (FP64).
+template <typename CV> struct CarryOps;
+template <> struct CarryOps<float2> {
+  using T = float2;
+  __device__ static T zero() { return make_float2(0.f, 0.f); }
+  __device__ static T one() { return make_float2(1.f, 0.f); }
+  __device__ static T from(float2 a) { return a; }
+  __device__ static T from_d2(double2 a) { return make_float2((float)a.x, (float)a.y); }
+  __device__ static T add(T a, T b) { return make_float2(a.x + b.x, a.y + b.y); }
+  __device__ static T mul(T a, T b) { return cmul(a, b); }
+  __device__ static float2 narrow(T a) { return a; }
+  __device__ static T shfl_xor(T a, int o) { return shfl_xor2(a, o); }
+};
+template <> struct CarryOps<double2> {
+  using T = double2;
+  __device__ static T zero() { return make_double2(0.0, 0.0); }
+  __device__ static T one() { return make_double2(1.0, 0.0); }
+  __device__ static T from(double2 a) { return a; }
+  __device__ static T from_d2(double2 a) { return a; }
+  __device__ static T add(T a, T b) { return make_double2(a.x + b.x, a.y + b.y); }
+  __device__ static T mul(T a, T b) { return cmul(a, b); }
+  __device__ static double2 narrow(T a) { return a; }
+  __device__ static T shfl_xor(T a, int o) { return shfl_xor2(a, o); }
+};
+template <> struct CarryOps<DFC> {
+  using T = DFC;
+  __device__ static T zero() { return DFC{DF{0.f, 0.f}, DF{0.f, 0.f}}; }
+  __device__ static T one() { return DFC{DF{1.f, 0.f}, DF{0.f, 0.f}}; }
+  __device__ static T from(float2 a) { return DFC{DF{a.x, 0.f}, DF{a.y, 0.f}}; }
+  __device__ static T from_d2(double2 a) { return dfc_from_d2(a); }
+  __device__ static T add(T a, T b) { return dfc_add(a, b); }
+  __device__ static T mul(T a, T b) { return dfc_mul(a, b); }
+  __device__ static float2 narrow(T a) { return make_float2(a.re.hi + a.re.lo, a.im.hi + a.im.lo); }
+  __device__ static T shfl_xor(T a, int o) {
+    T r;
+    r.re.hi = __shfl_xor_sync(0xffffffffu, a.re.hi, o);
+    r.re.lo = __shfl_xor_sync(0xffffffffu, a.re.lo, o);
+    r.im.hi = __shfl_xor_sync(0xffffffffu, a.im.hi, o);
+    r.im.lo = __shfl_xor_sync(0xffffffffu, a.im.lo, o);
+    return r;
+  }
+};
+
 template <typename V> __device__ __forceinline__ V ld_cg2(const V* p);
 template <> __device__ __forceinline__ float2 ld_cg2<float2>(const float2* p) { return __ldcg(p); }
 template <> __device__ __forceinline__ double2 ld_cg2<double2>(const double2* p) { return __ldcg(p); }
+template <> __device__ __forceinline__ DFC ld_cg2<DFC>(const DFC* p) {
+  const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+  return DFC{DF{v.x, v.y}, DF{v.z, v.w}};
+}
+
+template <typename V> __device__ __forceinline__ void st_cg2(V* p, V v) { __stcg(p, v); }
+template <> __device__ __forceinline__ void st_cg2<DFC>(DFC* p, DFC v) {
+  __stcg(reinterpret_cast<float4*>(p), make_float4(v.re.hi, v.re.lo, v.im.hi, v.im.lo));
+}
 
 }  // namespace msft

@@ -1,3 +1,4 @@
 // Scan kernel instantiations: rf f32p asft.
 #include "kernels_inst.cuh"
-MSFT_INST(kernel_rf_f32p_asft, float, float, FORM_RF, OUT_MORLET, true, 16)
+MSFT_INST(kernel_rf_f32p_asft, float, float2, FORM_RF, OUT_MORLET, true, 16)
+MSFT_INST_W(kernel_rf_f32p_asft_w, float, float2, OUT_MORLET, true, 16)

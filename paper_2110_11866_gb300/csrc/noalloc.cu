@@ -10,6 +10,7 @@
 
 #include "../../include/morlet_sft.h"
 #include "plan_internal.h"
+#include "work_plan.h"
 
 namespace msft {
 
@@ -43,73 +44,12 @@ constexpr int NA_MAX_DEVICES = 64;
 std::mutex na_mu;
 unsigned char* na_addr[NA_MAX_DEVICES] = {nullptr};
 
-// The work decomposition of the plan for one row, compensated precision: short windows (2L <= 2T)
-// get one segment per output sub-tile with its window prologue; long windows get look-back chains
-// over segments of max(4, ceil(4L / T)) output sub-tiles. With out == nullptr only counts the items.
-struct RowShape {
-  long long N, L, D;
-};
-
-__host__ __device__ long long row_items(const RowShape r, WorkItem* out, long long* n_slots) {
-  const long long T = NA_TILE;
-  const long long k_min = -((r.D + T - 1) / T);
-  const long long n_out = (r.N + T - 1) / T;
-  const long long h = (2 * r.L + T - 1) / T;
-  long long n = 0, slots = 0;
-  if (h <= 2) {
-    for (long long k0 = 0; k0 < n_out; ++k0) {
-      const long long t0 = r.D + k0 * T;
-      const long long t_dom = t0 - 2 * r.L > 0 ? t0 - 2 * r.L : 0;
-      long long kf = (t_dom - r.D >= 0) ? (t_dom - r.D) / T : -((r.D - t_dom + T - 1) / T);
-      if (kf < k_min) kf = k_min;
-      if (out) {
-        WorkItem w{};
-        w.chain = 0;
-        w.k_first = kf;
-        w.n_sub = (int)(k0 + 1 - kf);
-        w.k_out = k0;
-        w.t_dom = t_dom;
-        w.slot = -1;
-        w.slot_first = -1;
-        out[n] = w;
-      }
-      ++n;
-    }
-  } else {
-    long long seg = (4 * r.L + T - 1) / T;
-    if (seg < 4) seg = 4;
-    for (long long k0 = 0; k0 < n_out; k0 += seg) {
-      const long long t0 = r.D + k0 * T;
-      const long long t_dom = t0 - 2 * r.L > 0 ? t0 - 2 * r.L : 0;
-      long long kf = (t_dom - r.D >= 0) ? (t_dom - r.D) / T : -((r.D - t_dom + T - 1) / T);
-      if (kf < k_min) kf = k_min;
-      const long long kend = (k0 + seg < n_out) ? k0 + seg : n_out;
-      const long long first = slots;
-      for (long long k = kf; k < kend; ++k) {
-        if (out) {
-          WorkItem w{};
-          w.chain = 0;
-          w.k_first = k;
-          w.n_sub = 1;
-          w.k_out = k0;
-          w.t_dom = t_dom;
-          w.slot = slots;
-          w.slot_first = first;
-          out[n] = w;
-        }
-        ++n;
-        ++slots;
-      }
-    }
-  }
-  if (n_slots) *n_slots = slots;
-  return n;
-}
-
-// Writes the same items row_items counted on the host (same shape, same arithmetic).
-__global__ void na_build_row(RowShape r, ChainDesc* chain, WorkItem* work) {
+// Writes the work items of the row, the same decomposition the plan uses (work_plan.h).
+__global__ void na_build_row(RowSpec r, ChainDesc* chain, WorkItem* work) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    row_items(r, work, nullptr);
+    long long slots = 0, subtiles = 0;
+    bool chained = false;
+    row_work(r, NA_TILE, work, &slots, &subtiles, &chained);
     ChainDesc c{};
     c.x_off = 0;
     c.n = r.N;
@@ -146,9 +86,10 @@ extern "C" int morlet_forward_noalloc(const void* x, int64_t N, double sigma, do
   const long long ph_lo = std::max<long long>(0, pc - K);
   if (pc + kk > L) return MORLET_ERR_ARG;  // every harmonic p0 + j must stay below L (beta p < pi)
   // size limits of the scratch array
-  RowShape r{N, L, L};
-  long long n_slots = 0;
-  const long long n_work = row_items(r, nullptr, &n_slots);
+  RowSpec r{N, L, L, 0, 0, 0, 4, SEG_RESTART, 0, 32LL * NA_THREADS_ITEMS, 1};
+  long long n_slots = 0, n_sub = 0;
+  bool chained = false;
+  const long long n_work = row_work(r, NA_TILE, nullptr, &n_slots, &n_sub, &chained);
   if (n_work > NA_MAX_ITEMS || n_slots > NA_MAX_SLOTS) return MORLET_ERR_ARG;
 
   int dev = 0;
@@ -207,7 +148,8 @@ extern "C" int morlet_forward_noalloc(const void* x, int64_t N, double sigma, do
   if (e == cudaSuccess && n_slots > 0) e = cudaMemsetAsync(base + OFF_FLAGS, 0, sizeof(uint32_t) * n_slots, st);
   if (e != cudaSuccess) return na_status(e);
 
-  const void* func = kernel_for(V_RF_F32C_MORLET, kk);
+  // look-back rows on the CTA kernel, window rows on the warp-independent kernel (as the plan does)
+  const void* func = kernel_for(V_RF_F32C_MORLET, kk, !chained);
   if (!func) return MORLET_ERR_UNSUPPORTED;
   int sms = 0, occ = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -227,8 +169,10 @@ extern "C" int morlet_forward_noalloc(const void* x, int64_t N, double sigma, do
   kp.err = (int*)(base + OFF_ERR);
   kp.spin_limit = 1LL << 20;
   kp.accumulate = 0;
+  kp.n_chain = chained ? n_work : 0;
   void* args[] = {&kp};
-  const int grid = (int)std::min<long long>((long long)std::max(occ, 1) * sms, n_work);
+  const long long units = chained ? n_work : (n_work + WARPS - 1) / WARPS;  // CTAs, or warps per CTA
+  const int grid = (int)std::min<long long>((long long)std::max(occ, 1) * sms, units);
   e = cudaLaunchKernel(func, dim3(grid), dim3(THREADS), args, 0, st);
   if (e != cudaSuccess) return na_status(e);
   return prev_err ? MORLET_ERR_TIMEOUT : MORLET_OK;

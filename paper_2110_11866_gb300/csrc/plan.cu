@@ -12,37 +12,42 @@
 
 #include "../../include/morlet_sft.h"
 #include "plan_internal.h"
+#include "work_plan.h"
 
 namespace msft {
-const void* kernel_rf_f32c_morlet(int);
-const void* kernel_rf_f32p_morlet(int);
-const void* kernel_rf_f32p_asft(int);
-const void* kernel_rf_f64_morlet(int);
+#define MSFT_DECL(n) const void* n(int); const void* n##_w(int);
+MSFT_DECL(kernel_rf_f32c_morlet)
+MSFT_DECL(kernel_rf_f32p_morlet)
+MSFT_DECL(kernel_rf_f32p_asft)
+MSFT_DECL(kernel_rf_f64_morlet)
+MSFT_DECL(kernel_rf_f32c_real)
+MSFT_DECL(kernel_rf_f32p_real)
+MSFT_DECL(kernel_rf_f64_real)
+MSFT_DECL(kernel_rf_f32c_adj)
+MSFT_DECL(kernel_rf_f32p_adj)
+MSFT_DECL(kernel_rf_f64_adj)
+#undef MSFT_DECL
 const void* kernel_ki_f32c_morlet(int);
 const void* kernel_ki_f32p_morlet(int);
 const void* kernel_ki_f64_morlet(int);
-const void* kernel_rf_f32c_real(int);
-const void* kernel_rf_f32p_real(int);
-const void* kernel_rf_f64_real(int);
-const void* kernel_rf_f32c_adj(int);
-const void* kernel_rf_f32p_adj(int);
-const void* kernel_rf_f64_adj(int);
 
-const void* kernel_for(int variant, int K) {
+// The look-back (CTA) kernel of a variant, or with warp = true its warp-independent kernel
+// (rotating-form variants only).
+const void* kernel_for(int variant, int K, bool warp) {
   switch (variant) {
-    case V_RF_F32C_MORLET: return kernel_rf_f32c_morlet(K);
-    case V_RF_F32P_MORLET: return kernel_rf_f32p_morlet(K);
-    case V_RF_F32P_ASFT: return kernel_rf_f32p_asft(K);
-    case V_RF_F64_MORLET: return kernel_rf_f64_morlet(K);
-    case V_KI_F32C_MORLET: return kernel_ki_f32c_morlet(K);
-    case V_KI_F32P_MORLET: return kernel_ki_f32p_morlet(K);
-    case V_KI_F64_MORLET: return kernel_ki_f64_morlet(K);
-    case V_RF_F32C_REAL: return kernel_rf_f32c_real(K);
-    case V_RF_F32P_REAL: return kernel_rf_f32p_real(K);
-    case V_RF_F64_REAL: return kernel_rf_f64_real(K);
-    case V_RF_F32C_ADJ: return kernel_rf_f32c_adj(K);
-    case V_RF_F32P_ADJ: return kernel_rf_f32p_adj(K);
-    case V_RF_F64_ADJ: return kernel_rf_f64_adj(K);
+    case V_RF_F32C_MORLET: return warp ? kernel_rf_f32c_morlet_w(K) : kernel_rf_f32c_morlet(K);
+    case V_RF_F32P_MORLET: return warp ? kernel_rf_f32p_morlet_w(K) : kernel_rf_f32p_morlet(K);
+    case V_RF_F32P_ASFT: return warp ? kernel_rf_f32p_asft_w(K) : kernel_rf_f32p_asft(K);
+    case V_RF_F64_MORLET: return warp ? kernel_rf_f64_morlet_w(K) : kernel_rf_f64_morlet(K);
+    case V_KI_F32C_MORLET: return warp ? nullptr : kernel_ki_f32c_morlet(K);
+    case V_KI_F32P_MORLET: return warp ? nullptr : kernel_ki_f32p_morlet(K);
+    case V_KI_F64_MORLET: return warp ? nullptr : kernel_ki_f64_morlet(K);
+    case V_RF_F32C_REAL: return warp ? kernel_rf_f32c_real_w(K) : kernel_rf_f32c_real(K);
+    case V_RF_F32P_REAL: return warp ? kernel_rf_f32p_real_w(K) : kernel_rf_f32p_real(K);
+    case V_RF_F64_REAL: return warp ? kernel_rf_f64_real_w(K) : kernel_rf_f64_real(K);
+    case V_RF_F32C_ADJ: return warp ? kernel_rf_f32c_adj_w(K) : kernel_rf_f32c_adj(K);
+    case V_RF_F32P_ADJ: return warp ? kernel_rf_f32p_adj_w(K) : kernel_rf_f32p_adj(K);
+    case V_RF_F64_ADJ: return warp ? kernel_rf_f64_adj_w(K) : kernel_rf_f64_adj(K);
     default: return nullptr;
   }
 }
@@ -58,14 +63,17 @@ constexpr long long DEFAULT_SPIN = 1LL << 20;  // polls of ~64 ns sleep + an L2 
 
 // A launchable transform: kernel, work table, chains and status arrays.
 struct Launch {
-  const void* func = nullptr;
+  const void* func = nullptr;    // look-back (CTA) kernel: chain items, or every item of a KI plan
+  const void* func_w = nullptr;  // warp-independent kernel for window items (rotating form)
   WorkItem* d_work = nullptr;
   long long n_work = 0;
   ChainDesc* d_chains = nullptr;
   int grid = 0;
+  int grid_w = 0;
   long long sub_tiles = 0;
   long long rows_chain = 0, rows_halo = 0;
   std::vector<long long> scale_begin;  // adjoint: work items of scale s are [scale_begin[s], scale_begin[s+1])
+  std::vector<long long> chain_end;    // per launch range: look-back items come first, up to chain_end
 };
 
 }  // namespace
@@ -83,6 +91,7 @@ struct morlet_plan_s {
   size_t elem = 4;   // bytes per real sample
   ScaleTab* d_tabs = nullptr;
   FitJob* d_jobs = nullptr;
+  float2* d_phase = nullptr;  // kernel-integral form: per-scale phase tables
   std::vector<ScaleTab> h_tabs;
   Launch fwd, adj;
   uint32_t* d_flags = nullptr;
@@ -95,7 +104,9 @@ struct morlet_plan_s {
   long long spin = DEFAULT_SPIN;
   long long skip_tickets = 0;
   int latched = 0;
-  // graph of the forward (memsets + kernel) for a given (x, W)
+  cudaStream_t aux = nullptr;  // second stream: the warp-independent kernel runs beside the look-back one
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // graph of the forward (memsets + kernels) for a given (x, W)
   cudaGraphExec_t gexec = nullptr;
   const void* g_x = nullptr;
   void* g_out = nullptr;
@@ -137,32 +148,37 @@ int variant_of(const morlet_plan_s* p, bool adjoint) {
 
 long long floordiv(long long a, long long b) { return (a >= 0) ? a / b : -((-a + b - 1) / b); }
 
-// Work table of one transform. Rows are (signal, scale) pairs taken in `order`.
-//
-// FP32 rounding leaves a residue of about one unit of roundoff of |x| per sample in the carried
-// window state (the lagged subtraction never cancels the earlier addition bit for bit), and with
-// |rho| = 1 the residue is never forgotten. The compensated precision therefore restarts the scan
-// from a zero state 2L samples before each "segment" of outputs, which bounds the history that
-// can leave a residue to (segment + 2L) samples; FP64 carries make the rest exact. Short windows
-// (2L <= 2T) use one sub-tile per segment processed by one CTA ("window" rows, no look-back);
-// long windows use segments of max(4T, 4L) outputs, each a look-back chain of sub-tiles. The plain
-// precision keeps one chain per row (its errors grow with the row length), FP64 and ASFT (whose
-// damping forgets old residue) use long segments.
+// Work table of one transform. Rows are (signal, scale) pairs taken in `order`; each row is cut
+// into segments by row_work (work_plan.h), which explains the precision policies.
+int seg_policy(const morlet_plan_s* p) {
+  if (p->desc.precision == MORLET_FP32_PLAIN || (p->desc.flags & MORLET_FLAG_NO_HALO)) return SEG_PLAIN;
+  if (p->desc.precision == MORLET_FP32_COMP && p->desc.transform == MORLET_SFT) return SEG_RESTART;
+  return SEG_ROW;
+}
+
 void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& work, std::vector<ChainDesc>& chains,
                 long long& slots, Launch& ln) {
   const int S = (int)p->sigmas.size();
   const long long nsig = (long long)p->lengths.size();
-  const int prec = p->desc.precision;
-  const bool comp = prec == MORLET_FP32_COMP && p->desc.transform == MORLET_SFT;
-  const bool window_ok = prec != MORLET_FP32_PLAIN && !(p->desc.flags & MORLET_FLAG_NO_HALO);
+  // Row order. Forward: blocks of signals holding about 16 M input samples (their input stays in
+  // L2 across the scales), scale by scale inside a block, so that consecutive work items share a
+  // scale (a CTA restages its tables only when the scale changes). Adjoint: scale-major (each scale
+  // is one launch that adds into the gradient).
   std::vector<std::pair<long long, int>> order;  // (signal, scale)
   if (adjoint) {
     for (int s = 0; s < S; ++s)
       for (long long i = 0; i < nsig; ++i) order.push_back({i, s});
   } else {
-    for (long long i = 0; i < nsig; ++i)
-      for (int s = 0; s < S; ++s) order.push_back({i, s});
+    long long b0 = 0;
+    while (b0 < nsig) {
+      long long b1 = b0, acc = 0;
+      while (b1 < nsig && (b1 == b0 || acc + p->lengths[b1] <= (16LL << 20))) acc += p->lengths[b1++];
+      for (int s = 0; s < S; ++s)
+        for (long long i = b0; i < b1; ++i) order.push_back({i, s});
+      b0 = b1;
+    }
   }
+  const int esz = (int)p->elem * (adjoint ? 2 : 1);  // bytes per input element
   ln.scale_begin.assign(S + 1, 0);
   int prev_scale = -1;
   for (auto& rs : order) {
@@ -174,7 +190,6 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
     }
     const ScaleTab& tb = p->h_tabs[s];
     const long long N = p->lengths[i];
-    const long long L = tb.L, D = tb.D;
     ChainDesc c{};
     c.n = N;
     const long long row = (long long)S * p->x_off[i] + (long long)s * N;  // scalogram row
@@ -183,54 +198,35 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
     c.scale = s;
     const int ci = (int)chains.size();
     chains.push_back(c);
-    const long long k_min = -floordiv(D + TILE - 1, TILE);  // sub-tile holding t = 0
-    const long long n_out = (N + TILE - 1) / TILE;          // sub-tiles with outputs: 0 .. n_out-1
-    const long long h = (2 * L + TILE - 1) / TILE;          // sub-tiles covering the 2L-sample prologue
-    if (window_ok && h <= 2) {
-      // one CTA per segment: prologue sub-tiles + M output sub-tiles, zero state at t_dom
-      ln.rows_halo++;
-      const long long M = comp ? 1 : std::max<long long>(1, 4 * h);
-      for (long long k0 = 0; k0 < n_out; k0 += M) {
-        WorkItem w{};
-        w.chain = ci;
-        const long long t0 = D + k0 * TILE;
-        w.t_dom = std::max<long long>(0, t0 - 2 * L);
-        w.k_first = std::max(floordiv(w.t_dom - D, TILE), k_min);
-        const long long kend = std::min(k0 + M, n_out);
-        w.n_sub = (int)(kend - w.k_first);
-        w.k_out = k0;
-        w.slot = -1;
-        w.slot_first = -1;
-        work.push_back(w);
-        ln.sub_tiles += w.n_sub;
-      }
-    } else {
-      ln.rows_chain++;
-      long long seg = n_out;  // output sub-tiles per segment
-      if (comp && window_ok) seg = std::max<long long>(4, (4 * L + TILE - 1) / TILE);
-      for (long long k0 = 0; k0 < n_out; k0 += seg) {
-        const long long t0 = D + k0 * TILE;
-        const long long t_dom = std::max<long long>(0, t0 - 2 * L);
-        const long long kf = std::max(floordiv(t_dom - D, TILE), k_min);
-        const long long kend = std::min(k0 + seg, n_out);
-        const long long first = slots;
-        for (long long k = kf; k < kend; ++k) {
-          WorkItem w{};
-          w.chain = ci;
-          w.k_first = k;
-          w.n_sub = 1;
-          w.k_out = k0;
-          w.t_dom = t_dom;
-          w.slot = slots++;
-          w.slot_first = first;
-          work.push_back(w);
-          ln.sub_tiles += 1;
-        }
-      }
-    }
+    const bool warp_window = (p->form != 1);
+    RowSpec r{N, tb.L, tb.D, c.x_off, c.out_off, s, 16 / esz, seg_policy(p), ci,
+              warp_window ? (long long)32 * ITEMS : TILE, warp_window ? 1 : 0};
+    long long sl = slots, st = 0;
+    bool chained = false;
+    const long long n = row_work(r, TILE, nullptr, &sl, &st, &chained);
+    const size_t at = work.size();
+    work.resize(at + n);
+    ln.sub_tiles += st;
+    st = 0;
+    row_work(r, TILE, work.data() + at, &slots, &st, &chained);
+    if (chained) ln.rows_chain++;
+    else ln.rows_halo++;
   }
   if (adjoint)
     for (int q = prev_scale + 1; q <= S; ++q) ln.scale_begin[q] = (long long)work.size();
+  // Inside every launch range put the look-back items first (stable), so that independent items
+  // may claim their successor ticket early without ever holding an item that others wait on.
+  std::vector<std::pair<long long, long long>> ranges;
+  if (adjoint)
+    for (int q = 0; q < S; ++q) ranges.push_back({ln.scale_begin[q], ln.scale_begin[q + 1]});
+  else
+    ranges.push_back({0, (long long)work.size()});
+  ln.chain_end.clear();
+  for (auto& rg : ranges) {
+    auto mid = std::stable_partition(work.begin() + rg.first, work.begin() + rg.second,
+                                     [](const WorkItem& w) { return w.slot >= 0; });
+    ln.chain_end.push_back((long long)(mid - work.begin()));
+  }
 }
 
 int setup_launch(morlet_plan_s* p, bool adjoint, Launch& ln, long long& slots) {
@@ -238,13 +234,23 @@ int setup_launch(morlet_plan_s* p, bool adjoint, Launch& ln, long long& slots) {
   std::vector<WorkItem> work;
   std::vector<ChainDesc> chains;
   build_work(p, adjoint, work, chains, slots, ln);
-  ln.func = kernel_for(variant_of(p, adjoint), p->K_kernel);
+  ln.func = kernel_for(variant_of(p, adjoint), p->K_kernel, false);
   if (!ln.func) return MORLET_ERR_UNSUPPORTED;
+  if (p->form != 1) {
+    ln.func_w = kernel_for(variant_of(p, adjoint), p->K_kernel, true);
+    if (!ln.func_w) return MORLET_ERR_UNSUPPORTED;
+  }
   ln.n_work = (long long)work.size();
   int occ = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ln.func, THREADS, 0));
   if (occ < 1) occ = 1;
   ln.grid = (int)std::min<long long>((long long)occ * p->sms, std::max<long long>(1, ln.n_work));
+  if (ln.func_w) {
+    int occw = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occw, ln.func_w, THREADS, 0));
+    if (occw < 1) occw = 1;
+    ln.grid_w = occw * p->sms;
+  }
   CK(cudaMalloc(&ln.d_work, sizeof(WorkItem) * std::max<size_t>(1, work.size())));
   CK(cudaMalloc(&ln.d_chains, sizeof(ChainDesc) * std::max<size_t>(1, chains.size())));
   CK(cudaMemcpy(ln.d_work, work.data(), sizeof(WorkItem) * work.size(), cudaMemcpyHostToDevice));
@@ -271,45 +277,70 @@ int check_latched(morlet_plan_s* p) {
 }
 
 size_t carry_bytes(const morlet_plan_s* p) {
-  const size_t c = (p->desc.precision == MORLET_FP32_PLAIN || p->desc.transform == MORLET_ASFT) ? 8 : 16;
-  return c;
+  // float2 carries for the plain precision and the ASFT; two-float (DFC) or FP64 complex otherwise
+  return (p->desc.precision == MORLET_FP32_PLAIN || p->desc.transform == MORLET_ASFT) ? 8 : 16;
 }
 
-// Enqueue one scan launch: reset its work counter (and the status flags), then the kernel.
+// Enqueue one launch range: reset its work counters (and the status flags), then the look-back
+// kernel over the chain items on `st` and, concurrently on the plan's second stream, the
+// warp-independent kernel over the window items. tickets[0] / tickets[1] count the two kernels.
 cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out, long long w_begin, long long w_end,
-                    unsigned long long* ticket, bool clear_flags, cudaStream_t st, int accumulate = 0) {
-  cudaError_t e;
-  if (p->skip_tickets > 0) {
+                    long long w_chain_end, unsigned long long* tickets, bool clear_flags, cudaStream_t st,
+                    int accumulate = 0) {
+  cudaError_t e = cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned long long), st);
+  if (e == cudaSuccess && p->skip_tickets > 0) {
     const unsigned long long v = (unsigned long long)p->skip_tickets;
-    e = cudaMemcpyAsync(ticket, &v, sizeof(v), cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(tickets, &v, sizeof(v), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     p->skip_tickets = 0;
-  } else {
-    e = cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), st);
   }
   if (e != cudaSuccess) return e;
   if (clear_flags && p->n_slots > 0) {
     e = cudaMemsetAsync(p->d_flags, 0, sizeof(uint32_t) * p->n_slots, st);
     if (e != cudaSuccess) return e;
   }
+  const bool two = ln.func_w != nullptr;
+  const long long c_end = two ? w_chain_end : w_end;
   KParams kp{};
   kp.x = x;
   kp.out = out;
-  kp.work = ln.d_work + w_begin;
-  kp.n_work = w_end - w_begin;
   kp.chains = ln.d_chains;
   kp.tabs = p->d_tabs;
   kp.flags = p->d_flags;
   kp.agg = p->d_agg;
   kp.incl = p->d_incl;
-  kp.ticket = ticket;
   kp.err = p->d_err;
   kp.spin_limit = p->spin;
   kp.accumulate = accumulate;
-  if (kp.n_work <= 0) return cudaSuccess;
-  void* args[] = {&kp};
-  const int grid = (int)std::min<long long>(ln.grid, kp.n_work);
-  return cudaLaunchKernel(ln.func, dim3(grid), dim3(THREADS), args, 0, st);
+  bool forked = false;
+  if (two && w_end > c_end) {
+    KParams kw = kp;
+    kw.work = ln.d_work + c_end;
+    kw.n_work = w_end - c_end;
+    kw.n_chain = 0;
+    kw.ticket = tickets + 1;
+    e = cudaEventRecord(p->ev_fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->aux, p->ev_fork, 0);
+    if (e != cudaSuccess) return e;
+    void* args[] = {&kw};
+    const int grid = (int)std::min<long long>(ln.grid_w, (kw.n_work + WARPS - 1) / WARPS);
+    e = cudaLaunchKernel(ln.func_w, dim3(grid), dim3(THREADS), args, 0, p->aux);
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_join, p->aux);
+    if (e != cudaSuccess) return e;
+    forked = true;
+  }
+  if (c_end > w_begin) {
+    kp.work = ln.d_work + w_begin;
+    kp.n_work = c_end - w_begin;
+    kp.n_chain = std::min(w_chain_end, c_end) - w_begin;
+    kp.ticket = tickets;
+    void* args[] = {&kp};
+    const int grid = (int)std::min<long long>(ln.grid, kp.n_work);
+    e = cudaLaunchKernel(ln.func, dim3(grid), dim3(THREADS), args, 0, st);
+    if (e != cudaSuccess) return e;
+  }
+  if (forked) e = cudaStreamWaitEvent(st, p->ev_join, 0);
+  return e;
 }
 
 }  // namespace
@@ -337,11 +368,15 @@ void morlet_plan_destroy(morlet_plan_t p) {
   free_launch(p->adj);
   cudaFree(p->d_tabs);
   cudaFree(p->d_jobs);
+  cudaFree(p->d_phase);
   cudaFree(p->d_flags);
   cudaFree(p->d_agg);
   cudaFree(p->d_incl);
   cudaFree(p->d_ticket);
   if (p->h_err) cudaFreeHost(p->h_err);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
+  if (p->aux) cudaStreamDestroy(p->aux);
   delete p;
 }
 
@@ -446,6 +481,19 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
     for (int s = 0; s < S; ++s)
       if (p->h_tabs[s].p0 + p->K_kernel > jobs[s].L) { rc = MORLET_ERR_ARG; goto fail; }
     CK(run_tables(p->d_tabs, p->d_jobs, S, p->K_kernel, ITEMS, p->form, st));
+    if (p->form == 1) {
+      std::vector<long long> poff(S + 1, 0);
+      for (int s = 0; s < S; ++s) poff[s + 1] = poff[s] + (2 * jobs[s].L) / 1024 + 2 + 1024;
+      CK(cudaMalloc(&p->d_phase, sizeof(float2) * poff[S]));
+      long long* d_poff = nullptr;
+      CK(cudaMalloc(&d_poff, sizeof(long long) * (S + 1)));
+      CK(cudaMemcpyAsync(d_poff, poff.data(), sizeof(long long) * (S + 1), cudaMemcpyHostToDevice, st));
+      cudaError_t e2 = run_phase_tables(p->d_tabs, p->d_jobs, S, p->d_phase, d_poff, st);
+      cudaError_t e3 = cudaStreamSynchronize(st);
+      cudaFree(d_poff);
+      CK(e2);
+      CK(e3);
+    }
     CK(cudaMemcpyAsync(p->h_tabs.data(), p->d_tabs, sizeof(ScaleTab) * S, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
 
@@ -466,7 +514,10 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
       CK(cudaMalloc(&p->d_agg, carry_bytes(p) * nt_adj * p->n_slots));
       CK(cudaMalloc(&p->d_incl, carry_bytes(p) * nt_adj * p->n_slots));
     }
-    CK(cudaMalloc(&p->d_ticket, sizeof(unsigned long long) * (S + 1)));
+    CK(cudaMalloc(&p->d_ticket, sizeof(unsigned long long) * 2 * (S + 1)));
+    CK(cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
     CK(cudaHostAlloc((void**)&p->h_err, sizeof(int), cudaHostAllocMapped));
     *p->h_err = 0;
     CK(cudaHostGetDevicePointer((void**)&p->d_err, p->h_err, 0));
@@ -486,7 +537,8 @@ int morlet_forward(morlet_plan_t p, const void* x, void* W, void* stream) {
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const bool use_graph = !(p->desc.flags & MORLET_FLAG_NO_GRAPH) && p->skip_tickets == 0;
-  if (!use_graph) return cuda_status(enqueue(p, p->fwd, x, W, 0, p->fwd.n_work, p->d_ticket, true, st));
+  if (!use_graph)
+    return cuda_status(enqueue(p, p->fwd, x, W, 0, p->fwd.n_work, p->fwd.chain_end[0], p->d_ticket, true, st));
   if (!p->gexec || p->g_x != x || p->g_out != W) {
     // capture memsets + kernel once per (x, W); replays are a single graph launch
     if (p->gexec) {
@@ -499,7 +551,7 @@ int morlet_forward(morlet_plan_t p, const void* x, void* W, void* stream) {
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t e2 = enqueue(p, p->fwd, x, W, 0, p->fwd.n_work, p->d_ticket, true, cs);
+      cudaError_t e2 = enqueue(p, p->fwd, x, W, 0, p->fwd.n_work, p->fwd.chain_end[0], p->d_ticket, true, cs);
       e = cudaStreamEndCapture(cs, &g);
       if (e2 != cudaSuccess) e = e2;
     }
@@ -524,7 +576,7 @@ int morlet_backward(morlet_plan_t p, const void* gW, void* gx, void* stream) {
   const int S = (int)p->sigmas.size();
   for (int s = 0; s < S; ++s) {
     const cudaError_t e = enqueue(p, p->adj, gW, gx, p->adj.scale_begin[s], p->adj.scale_begin[s + 1],
-                                  p->d_ticket + 1 + s, s == 0, st, s > 0 ? 1 : 0);
+                                  p->adj.chain_end[s], p->d_ticket + 2 * (1 + s), s == 0, st, s > 0 ? 1 : 0);
     if (e != cudaSuccess) return cuda_status(e);
   }
   return MORLET_OK;

@@ -31,9 +31,12 @@ cudaError_t run_fit(const FitJob* d_jobs, int n_scales, long long max_L, double*
 cudaError_t run_tables(ScaleTab* d_tabs, const FitJob* d_jobs, int n_scales, int K_kernel, int items, int form,
                        cudaStream_t st);
 
-// Kernel lookup. variant: see kernels.h; returns nullptr if not built.
+cudaError_t run_phase_tables(ScaleTab* d_tabs, const FitJob* d_jobs, int n_scales, float2* d_phase,
+                             const long long* d_poff, cudaStream_t st);
+
+// Kernel lookup: the scan kernel of a variant and a built term count, or nullptr.
 enum Variant {
-  V_RF_F32C_MORLET = 0,  // rotating form, FP32 scan, FP64 carries
+  V_RF_F32C_MORLET = 0,  // rotating form, FP32 scan, two-float carries
   V_RF_F32P_MORLET,      // rotating form, FP32 scan, FP32 carries
   V_RF_F32P_ASFT,        // ASFT, FP32
   V_RF_F64_MORLET,
@@ -53,6 +56,6 @@ enum Variant {
 constexpr int N_KBUILT = 6;
 __host__ __device__ constexpr int kbuilt(int i) { return i == 0 ? 2 : i == 1 ? 3 : i == 2 ? 4 : i == 3 ? 6 : i == 4 ? 8 : 12; }
 
-const void* kernel_for(int variant, int K);
+const void* kernel_for(int variant, int K, bool warp);
 
 }  // namespace msft

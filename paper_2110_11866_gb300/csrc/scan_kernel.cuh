@@ -7,7 +7,7 @@
 //  kernelIntZenka): modulate a[t] = x[t] e^{i beta p t}, scan the lagged difference
 //  d[t] = a[t] - a[t-2L-1] (its prefix is the window sum u_(2L+1)[t]), then demodulate
 //  e^{-i beta p t} u_(2L+1)[t] and combine. Phases are advanced by a fixed step from a per-tile
-//  anchor that is computed in FP64 from the exact integer (p t) mod 2L.
+//  anchor e^{i beta p (t0-1)} looked up from the exact integer (p (t0-1)) mod 2L.
 //
 //  Rotating form (FORM_RF): the same window sum seen from the harmonic's own frame,
 //  V[t] = e^{-i beta p t} u_(2L+1)[t], which obeys the first-order recursion of Sec. II-C (eq. iir1
@@ -20,19 +20,17 @@
 // Both forms give (c_p - i s_p)[n] = (-1)^p V[n + L] and the direct-method output
 // W[n] = sum_p m_p c_p[n] + i l_p s_p[n] (signs folded into the weights cM, cL).
 //
-// Work decomposition: a row (signal, scale) is cut into sub-tiles of T = THREADS * ITEMS positions
-// on the output grid. A CTA takes work items from a global counter (so every predecessor of a
-// claimed item is already running) and, per sub-tile:
+// Work decomposition: a row (signal, scale) is cut into segments (work_plan.h); a CTA takes work
+// items from a global counter (so every predecessor of a claimed item is already running) and, per
+// sub-tile of T = THREADS * ITEMS positions:
 //   1. loads x[t] and x[t - 2L - 1] for its ITEMS consecutive positions per thread,
 //   2. pass 1: runs the recursion from a zero state -> per-thread aggregate,
 //   3. warp-shuffle scan of the aggregates (rotation powers rho^{ITEMS 2^l}),
-//   4. warp 0 combines the 8 warp totals, publishes the tile aggregate, looks back over the row's
-//      earlier tiles (decoupled look-back, bounded waits) or takes the carry of its own previous
-//      sub-tile, and publishes the inclusive state (carries in CR precision: FP64 for the
-//      compensated form),
-//   5. pass 2: reruns the recursion from each thread's exact start state and writes the outputs.
-// Rows with short windows (2L+1 <= 2T) use no look-back at all: the work item starts 2L samples
-// before its first output with a zero state, so no error accumulates along the row.
+//   4. warp 0 combines the 8 warp totals (lanes work on (warp, term) pairs in parallel), publishes
+//      the tile aggregate and looks back over the segment's earlier tiles (decoupled look-back,
+//      bounded waits), or takes the carry of its own previous sub-tile; carries are two-float FP32
+//      (compensated), FP32 (plain) or FP64 (FP64 precision),
+//   5. pass 2: reruns the recursion from each thread's start state and writes the outputs.
 #pragma once
 
 #include <type_traits>
@@ -44,12 +42,11 @@ namespace msft {
 enum { FORM_KI = 1, FORM_RF = 2 };
 enum { OUT_MORLET = 0, OUT_REAL = 1, OUT_ADJ = 2 };
 
-template <typename R_, typename CR_, int K_, int FORM_, int OUT_, bool ASFT_, int ITEMS_>
+template <typename R_, typename CV_, int K_, int FORM_, int OUT_, bool ASFT_, int ITEMS_>
 struct Cfg {
   using R = R_;
-  using CR = CR_;
   using V = typename C2<R_>::T;
-  using CV = typename C2<CR_>::T;
+  using CV = CV_;
   static constexpr int K = K_;
   static constexpr int FORM = FORM_;
   static constexpr int OUT = OUT_;
@@ -58,6 +55,7 @@ struct Cfg {
   static constexpr int CH = (OUT_ == OUT_ADJ) ? 2 : 1;
   static constexpr int NT = CH * K_;
   static constexpr int T = THREADS * ITEMS_;
+  static constexpr int MINB = (sizeof(R_) == 4 && NT <= 4) ? 3 : (NT <= 8 ? 2 : 1);
   static_assert(FORM_ == FORM_RF || CH == 1, "kernel-integral form is built for real input only");
   static_assert(NT <= 32, "one lane per scanned value in the block phase");
 };
@@ -68,11 +66,13 @@ struct Smem {
   using V = typename C::V;
   using CV = typename C::CV;
   WorkItem wi;
-  ChainDesc ch;
+  WorkItem nwi;  // the next work item, loaded while this one runs
   long long work;
   int cur_scale;
   int64_t L, D;
   int32_t p0;
+  const float2* ph_hi;
+  const float2* ph_lo;
   // staged per scale
   V rho[C::K];
   V pw_thr[5][C::K];
@@ -81,7 +81,6 @@ struct Smem {
   R cM[C::K], cL[C::K];
   V E;
   R kappa;
-  CV pw_warp_c[C::K];
   CV pw_wofs_c[8][C::K];
   CV pw_tile_c[33][C::K];
   // per sub-tile
@@ -94,7 +93,7 @@ struct Smem {
 };
 
 // ------------------------------------------------------------------------------------------------
-// loads and stores
+// loads
 // ------------------------------------------------------------------------------------------------
 
 // v[i] = p[t + i] if lo <= t + i < hi, else 0. 128-bit loads when the run is in range and aligned.
@@ -104,9 +103,9 @@ __device__ __forceinline__ void load_run(const E* __restrict__ p, int64_t t, int
   if (t >= lo && t + N <= hi) {
     const E* q = p + t;
     constexpr int VEC = 16 / sizeof(E);
-    if (VEC >= 1 && (reinterpret_cast<uintptr_t>(q) & 15) == 0) {
+    if ((reinterpret_cast<uintptr_t>(q) & 15) == 0) {
 #pragma unroll
-      for (int i = 0; i < N; i += (VEC > 0 ? VEC : 1)) {
+      for (int i = 0; i < N; i += VEC) {
         const int4 u = __ldg(reinterpret_cast<const int4*>(q + i));
         const E* e = reinterpret_cast<const E*>(&u);
 #pragma unroll
@@ -125,8 +124,30 @@ __device__ __forceinline__ void load_run(const E* __restrict__ p, int64_t t, int
   }
 }
 
-__device__ __forceinline__ void st_cs(float2* p, float2 a, float2 b) {
-  __stcs(reinterpret_cast<float4*>(p), make_float4(a.x, a.y, b.x, b.y));
+// Output of item i (position tf + i) at element oo + i. In the common case (all ITEMS positions of
+// the lane inside the stored range, 16-byte aligned complex64 output) pairs of items go out as one
+// 16-byte streaming store; otherwise each item is checked and stored alone.
+template <class C>
+__device__ __forceinline__ void store_item(const KParams& P, int64_t oo, int i, typename C::V o, typename C::V prev,
+                                           bool all_in, bool in) {
+  using R = typename C::R;
+  using V = typename C::V;
+  if constexpr (C::OUT == OUT_MORLET) {
+    V* op = reinterpret_cast<V*>(P.out) + oo;
+    if constexpr (sizeof(R) == 4) {
+      if (all_in && ((reinterpret_cast<uintptr_t>(op) & 15) == 0)) {
+        if (i & 1) __stcs(reinterpret_cast<float4*>(op + (i - 1)), make_float4(prev.x, prev.y, o.x, o.y));
+        return;
+      }
+    }
+    if (all_in || in) __stcs(op + i, o);
+  } else if constexpr (C::OUT == OUT_ADJ) {
+    R* op = reinterpret_cast<R*>(P.out) + oo;
+    if (all_in || in) op[i] = P.accumulate ? op[i] + o.x : o.x;
+  } else {
+    R* op = reinterpret_cast<R*>(P.out) + oo;
+    if (all_in || in) __stcs(op + i, o.x);
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -134,11 +155,11 @@ __device__ __forceinline__ void st_cs(float2* p, float2 a, float2 b) {
 // ------------------------------------------------------------------------------------------------
 
 template <class C>
-__global__ void __launch_bounds__(THREADS) scan_kernel(const KParams P) {
+__global__ void __launch_bounds__(THREADS, C::MINB) scan_kernel(const KParams P) {
   using R = typename C::R;
-  using CR = typename C::CR;
   using V = typename C::V;
   using CV = typename C::CV;
+  using CO = CarryOps<CV>;
   constexpr int K = C::K, NT = C::NT, CH = C::CH, ITEMS = C::ITEMS, T = C::T;
   constexpr bool ROT = (C::FORM == FORM_RF);
   // element type of one input sample (real, or complex for the adjoint's two channels)
@@ -146,71 +167,79 @@ __global__ void __launch_bounds__(THREADS) scan_kernel(const KParams P) {
 
   __shared__ Smem<C> s;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s.cur_scale = -1;
+  if (tid == 0) {
+    s.cur_scale = -1;
+    const long long w = (long long)atomicAdd(P.ticket, 1ull);
+    s.work = w;
+    if (w < P.n_work) s.wi = P.work[w];
+  }
+  __syncthreads();
 
   for (;;) {
-    __syncthreads();  // everyone is done with the previous work item
-    if (tid == 0) {
-      const long long w = (long long)atomicAdd(P.ticket, 1ull);
-      s.work = w;
-      if (w < P.n_work) {
-        s.wi = P.work[w];
-        s.ch = P.chains[s.wi.chain];
-      }
-    }
-    __syncthreads();
     if (s.work >= P.n_work) return;
     const WorkItem wi = s.wi;
-    const ChainDesc ch = s.ch;
+    // Independent work items (after the look-back ones) claim the next ticket now, so that its
+    // latency hides behind this item; an item that others may wait on is never held unstarted.
+    long long next = 0;
+    const bool early = s.work >= P.n_chain;
+    if (tid == 0 && early) next = (long long)atomicAdd(P.ticket, 1ull);
 
-    if (ch.scale != s.cur_scale) {  // stage this scale's constants (uniform branch)
-      const ScaleTab* tb = P.tabs + ch.scale;
+    if (wi.scale != s.cur_scale) {  // stage this scale's constants (uniform branch)
+      const ScaleTab* tb = P.tabs + wi.scale;
       for (int i = tid; i < K; i += THREADS) {
         s.rho[i] = conv2<V>(tb->rho[i]);
         s.cM[i] = (R)tb->cM[i];
         s.cL[i] = (C::OUT == OUT_ADJ) ? (R)(-tb->cL[i]) : (R)tb->cL[i];
-        s.pw_warp_c[i] = conv2<CV>(tb->pw_warp[i]);
       }
       for (int i = tid; i < 5 * K; i += THREADS) s.pw_thr[i / K][i % K] = conv2<V>(tb->pw_thr[i / K][i % K]);
       for (int i = tid; i < 32 * K; i += THREADS) s.pw_lane[i / K][i % K] = conv2<V>(tb->pw_lane[i / K][i % K]);
       for (int i = tid; i < 8 * K; i += THREADS) {
         s.pw_wofs_r[i / K][i % K] = conv2<V>(tb->pw_wofs[i / K][i % K]);
-        s.pw_wofs_c[i / K][i % K] = conv2<CV>(tb->pw_wofs[i / K][i % K]);
+        s.pw_wofs_c[i / K][i % K] = CO::from_d2(tb->pw_wofs[i / K][i % K]);
       }
-      for (int i = tid; i < 33 * K; i += THREADS) s.pw_tile_c[i / K][i % K] = conv2<CV>(tb->pw_tile[i / K][i % K]);
+      for (int i = tid; i < 33 * K; i += THREADS) s.pw_tile_c[i / K][i % K] = CO::from_d2(tb->pw_tile[i / K][i % K]);
       if (tid == 0) {
         s.E = conv2<V>(tb->E);
         s.kappa = (R)tb->kappa;
         s.L = tb->L;
         s.D = tb->D;
         s.p0 = tb->p0;
+        s.ph_hi = tb->ph_hi;
+        s.ph_lo = tb->ph_lo;
       }
       __syncthreads();
-      if (tid == 0) s.cur_scale = ch.scale;
+      if (tid == 0) s.cur_scale = wi.scale;
     }
     const int64_t L = s.L, D = s.D, Wl = 2 * L + 1;
     const R kap = s.kappa;
 
-    const EIn* __restrict__ xs = reinterpret_cast<const EIn*>(P.x) + ch.x_off;
-    const int64_t N = ch.n;
-    const int64_t lo = wi.t_dom;  // samples before t_dom count as zero (>= 0)
-    if (tid < NT) s.carry[tid] = CV{};
+    const EIn* __restrict__ xs = reinterpret_cast<const EIn*>(P.x) + wi.x_off;
+    const int64_t N = wi.n;
+    const int64_t lo = wi.t_dom;  // samples before t_dom count as zero (t_dom >= 0)
+    const int64_t t_out = wi.t_out > D ? wi.t_out : D;
+    const int64_t t_end = wi.t_end < D + N ? wi.t_end : D + N;
+    if (tid < NT) s.carry[tid] = CO::zero();
 
     for (int sub = 0; sub < wi.n_sub; ++sub) {
-      const int64_t k = wi.k_first + sub;
-      const int64_t t0 = D + k * (int64_t)T;
+      const int64_t t0 = wi.t_a + (int64_t)sub * T;
       const int64_t tf = t0 + (int64_t)tid * ITEMS;  // this thread's first position
-      const bool store = (k >= wi.k_out);
 
       if constexpr (!ROT) {
-        // phase anchor e^{i beta p (t0 - 1)} from the exact integer (p (t0-1)) mod 2L, in FP64
+        // phase anchor e^{i beta p (t0 - 1)} from the exact integer (p (t0 - 1)) mod 2L
         if (tid < K) {
           const long long p = s.p0 + tid, m = 2 * L;
           long long r = (p * (long long)(t0 - 1)) % m;
           if (r < 0) r += m;
-          double sn, cs;
-          sincospi((double)r / (double)L, &sn, &cs);
-          s.base[tid] = cmake<R>((R)cs, (R)sn);
+          if constexpr (sizeof(R) == 8) {  // FP64 path: the anchor itself in FP64
+            double sn, cs;
+            sincospi((double)r / (double)L, &sn, &cs);
+            s.base[tid] = cmake<R>((R)cs, (R)sn);
+          } else {  // two-level table, rounded once per level
+            const float2 a = __ldg(s.ph_hi + (r >> 10));
+            const float2 b = __ldg(s.ph_lo + (r & 1023));
+            const float2 c = cmul(a, b);
+            s.base[tid] = cmake<R>((R)c.x, (R)c.y);
+          }
         }
         __syncthreads();
       }
@@ -291,7 +320,10 @@ __global__ void __launch_bounds__(THREADS) scan_kernel(const KParams P) {
           const V u = shfl_up2(B[v], o);
           if (lane >= o) {
             if constexpr (ROT) B[v] = cfma(s.pw_thr[l][v % K], u, B[v]);
-            else { B[v].x += u.x; B[v].y += u.y; }
+            else {
+              B[v].x += u.x;
+              B[v].y += u.y;
+            }
           }
         }
       }
@@ -299,7 +331,6 @@ __global__ void __launch_bounds__(THREADS) scan_kernel(const KParams P) {
 #pragma unroll
         for (int v = 0; v < NT; ++v) s.wtot[warp][v] = B[v];
       }
-      // exclusive value: the inclusive of the previous lane
 #pragma unroll
       for (int v = 0; v < NT; ++v) {
         V u = shfl_up2(B[v], 1);
@@ -308,39 +339,62 @@ __global__ void __launch_bounds__(THREADS) scan_kernel(const KParams P) {
       }
       __syncthreads();
 
-      // ---- 4. block phase: warp 0 ----
+      // ---- 4. block phase: warp 0; lanes take (warp w, term v) pairs, 4 terms per round ----
       if (warp == 0) {
-        // tile aggregate A (zero entering state)
-        CV A = CV{};
-        if (lane < NT) {
+        const int w8 = lane & 7;
+        // the tile aggregate is needed for a following sub-tile or for the look-back chain
+        const bool need_agg = (sub + 1 < wi.n_sub) || (wi.slot >= 0);
+        // a nonzero state enters this sub-tile after an earlier sub-tile or from a predecessor
+        const bool has_carry = (sub > 0) || (wi.slot >= 0 && wi.slot != wi.slot_first);
+        for (int v0 = 0; v0 < NT; v0 += 4) {
+          const int v = v0 + (lane >> 3);
+          const bool act = v < NT;
+          const int vv = act ? v : 0;
+          const V tw = s.wtot[w8][vv];
+          // exclusive prefix over the warps (zero entering state), sample precision
+          V X = tw;
 #pragma unroll
-          for (int w = 0; w < WARPS; ++w) {
-            const double2 t2 = wide2<V>(s.wtot[w][lane]);
-            CV twc;
-            twc.x = (CR)t2.x;
-            twc.y = (CR)t2.y;
-            if constexpr (ROT) A = cfma(s.pw_warp_c[lane % K], A, twc);
-            else { A.x += twc.x; A.y += twc.y; }
+          for (int o = 1; o < 8; o <<= 1) {
+            const V u = shfl_up2(X, o);
+            if (w8 >= o) {
+              if constexpr (ROT) X = cfma(s.pw_wofs_r[o][vv % K], u, X);
+              else {
+                X.x += u.x;
+                X.y += u.y;
+              }
+            }
+          }
+          V Xe = shfl_up2(X, 1);
+          if (w8 == 0) Xe = V{};
+          if (act) s.xw[w8][vv] = Xe;
+          if (need_agg) {
+            // tile aggregate in carry precision: sum_w rho^{T_w (7 - w)} wtot_w
+            CV a = CO::from(tw);
+            if constexpr (ROT) a = CO::mul(s.pw_wofs_c[7 - w8][vv % K], a);
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) a = CO::add(a, CO::shfl_xor(a, o));
+            if (act && w8 == 0) s.agg[vv] = a;
           }
         }
+        __syncwarp();
         const bool lookback = (sub == 0) && (wi.slot >= 0);
         if (lookback) {
           const int64_t slot = wi.slot;
           CV* aggp = reinterpret_cast<CV*>(P.agg);
           CV* inclp = reinterpret_cast<CV*>(P.incl);
           if (slot == wi.slot_first) {
-            if (lane < NT) s.carry[lane] = CV{};
+            if (lane < NT) s.carry[lane] = CO::zero();
           } else {
             // publish the aggregate, then look back
             if (lane < NT) {
-              __stcg(aggp + slot * NT + lane, A);
+              st_cg2(aggp + slot * NT + lane, s.agg[lane]);
               __threadfence();
             }
             __syncwarp();
             if (lane == 0) st_release(P.flags + slot, ST_AGG);
             if (lane < NT) {
-              s.carry[lane] = CV{};
-              s.rot[lane] = ROT ? conv2<CV>(make_double2(1.0, 0.0)) : CV{};
+              s.carry[lane] = CO::zero();
+              s.rot[lane] = CO::one();
             }
             __syncwarp();
             int64_t base = slot - 1;
@@ -369,30 +423,28 @@ __global__ void __launch_bounds__(THREADS) scan_kernel(const KParams P) {
                 }
               }
               const int first = incl_mask ? (__ffs(incl_mask) - 1) : 32;
+              const bool use = (lane <= first) && valid && !forced;
               // sum of predecessor values, lane q rotated by rho^{T q} (times rho^{32 T} per batch)
+#pragma unroll
               for (int v = 0; v < NT; ++v) {
-                CV val = CV{};
-                if (lane <= first && valid && !forced) {
+                CV val = CO::zero();
+                if (use) {
                   const CV* src = (f == ST_INCL) ? inclp : aggp;
                   val = ld_cg2<CV>(src + j * NT + v);
-                  if constexpr (ROT) val = cmul(s.pw_tile_c[lane][v % K], val);
+                  if constexpr (ROT) val = CO::mul(s.pw_tile_c[lane][v % K], val);
                 }
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                  const CV u = shfl_xor2(val, o);
-                  val.x += u.x;
-                  val.y += u.y;
-                }
+                for (int o = 16; o > 0; o >>= 1) val = CO::add(val, CO::shfl_xor(val, o));
                 if (lane == 0) {
-                  if constexpr (ROT) s.carry[v] = cfma(s.rot[v], val, s.carry[v]);
-                  else { s.carry[v].x += val.x; s.carry[v].y += val.y; }
+                  if constexpr (ROT) s.carry[v] = CO::add(CO::mul(s.rot[v], val), s.carry[v]);
+                  else s.carry[v] = CO::add(s.carry[v], val);
                 }
               }
               __syncwarp();
               if (first < 32) break;
               base -= 32;
               if constexpr (ROT) {
-                if (lane < NT) s.rot[lane] = cmul(s.rot[lane], s.pw_tile_c[32][lane % K]);
+                if (lane < NT) s.rot[lane] = CO::mul(s.rot[lane], s.pw_tile_c[32][lane % K]);
               }
               __syncwarp();
             }
@@ -401,55 +453,61 @@ __global__ void __launch_bounds__(THREADS) scan_kernel(const KParams P) {
           // publish the inclusive state after this tile
           if (lane < NT) {
             CV inc = s.carry[lane];
-            if constexpr (ROT) inc = cfma(s.pw_tile_c[1][lane % K], inc, A);
-            else { inc.x += A.x; inc.y += A.y; }
-            __stcg(inclp + slot * NT + lane, inc);
+            if constexpr (ROT) inc = CO::mul(s.pw_tile_c[1][lane % K], inc);
+            inc = CO::add(inc, s.agg[lane]);
+            st_cg2(inclp + slot * NT + lane, inc);
             __threadfence();
           }
           __syncwarp();
           if (lane == 0) st_release(P.flags + slot, ST_INCL);
         }
         __syncwarp();
-        // start state of each warp, and the carry into the next sub-tile
-        if (lane < NT) {
-          const CV c0 = s.carry[lane];
-          CV X = CV{};
-#pragma unroll
-          for (int w = 0; w < WARPS; ++w) {
-            CV xw;
-            if constexpr (ROT) xw = cfma(s.pw_wofs_c[w][lane % K], c0, X);
-            else { xw.x = X.x + c0.x; xw.y = X.y + c0.y; }
-            s.xw[w][lane] = cmake<R>((R)xw.x, (R)xw.y);
-            const double2 t2 = wide2<V>(s.wtot[w][lane]);
-            CV twc;
-            twc.x = (CR)t2.x;
-            twc.y = (CR)t2.y;
-            if constexpr (ROT) X = cfma(s.pw_warp_c[lane % K], X, twc);
-            else { X.x += twc.x; X.y += twc.y; }
+        // start state of each warp (sample precision), and the carry into the next sub-tile
+        const bool carry_in = has_carry || lookback;
+        for (int v0 = 0; carry_in && v0 < NT; v0 += 4) {
+          const int v = v0 + (lane >> 3);
+          if (v < NT) {
+            CV c = s.carry[v];
+            if constexpr (ROT) c = CO::mul(s.pw_wofs_c[w8][v % K], c);
+            const V cr = conv2<V>(wide2(CO::narrow(c)));
+            V xw = s.xw[w8][v];
+            xw.x += cr.x;
+            xw.y += cr.y;
+            s.xw[w8][v] = xw;
           }
-          CV nxt;
-          if constexpr (ROT) nxt = cfma(s.pw_tile_c[1][lane % K], c0, A);
-          else { nxt.x = c0.x + A.x; nxt.y = c0.y + A.y; }
-          s.carry[lane] = nxt;
+        }
+        __syncwarp();
+        if (lane < NT && sub + 1 < wi.n_sub) {
+          CV c = s.carry[lane];
+          if constexpr (ROT) c = CO::mul(s.pw_tile_c[1][lane % K], c);
+          s.carry[lane] = CO::add(c, s.agg[lane]);
+        }
+        if (lane == 0 && sub == wi.n_sub - 1) {
+          if (!early) next = (long long)atomicAdd(P.ticket, 1ull);
+          if (next < P.n_work) s.nwi = P.work[next];
         }
       }
       __syncthreads();
 
-      // ---- 5. pass 2: outputs ----
-      const int64_t nf = tf - D;  // first output index of this thread
-      if (!store || nf >= N || nf + ITEMS <= 0) continue;
+      // ---- 5. pass 2: outputs for positions in [t_out, t_end) ----
+      if (tf >= t_end || tf + ITEMS <= t_out) continue;
       V S[NT];
 #pragma unroll
       for (int v = 0; v < NT; ++v) {
         if constexpr (ROT) S[v] = cfma(s.pw_lane[lane][v % K], s.xw[warp][v], B[v]);
-        else { S[v].x = s.xw[warp][v].x + B[v].x; S[v].y = s.xw[warp][v].y + B[v].y; }
+        else {
+          S[v].x = s.xw[warp][v].x + B[v].x;
+          S[v].y = s.xw[warp][v].y + B[v].y;
+        }
       }
       V ph[ROT ? 1 : K];
       if constexpr (!ROT) {
 #pragma unroll
         for (int j = 0; j < K; ++j) ph[j] = ph0[j];
       }
-      const int64_t oo = ch.out_off + nf;
+      const int64_t oo = wi.out_off - D + tf;  // output element of position tf
+      const bool all_in = (tf >= t_out) && (tf + ITEMS <= t_end);
+      V prev{};
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i) {
         V o = V{};
@@ -493,7 +551,7 @@ __global__ void __launch_bounds__(THREADS) scan_kernel(const KParams P) {
             S[j].x += fma(xv, pn.x, -xlv * ph[j].x);
             S[j].y += fma(xv, pn.y, -xlv * ph[j].y);
             ph[j] = pn;
-            const R qx = fma(pn.x, S[j].x, pn.y * S[j].y);   // conj(phase) * window sum
+            const R qx = fma(pn.x, S[j].x, pn.y * S[j].y);  // conj(phase) * window sum
             const R qy = fma(pn.x, S[j].y, -pn.y * S[j].x);
             if constexpr (C::OUT == OUT_MORLET) {
               o.x = fma(s.cM[j], qx, o.x);
@@ -504,23 +562,17 @@ __global__ void __launch_bounds__(THREADS) scan_kernel(const KParams P) {
           }
         }
         if constexpr (C::ASFT) o = cmul(o, s.E);
-        // store output n = nf + i
-        const int64_t n = nf + i;
-        if constexpr (C::OUT == OUT_MORLET) {
-          V* op = reinterpret_cast<V*>(P.out);
-          if (n >= 0 && n < N) {
-            if constexpr (sizeof(R) == 4) __stcs(reinterpret_cast<float2*>(op + (oo + i)), reinterpret_cast<const float2&>(o));
-            else __stcs(reinterpret_cast<double2*>(op + (oo + i)), reinterpret_cast<const double2&>(o));
-          }
-        } else if constexpr (C::OUT == OUT_ADJ) {
-          R* op = reinterpret_cast<R*>(P.out);
-          if (n >= 0 && n < N) op[oo + i] = P.accumulate ? op[oo + i] + o.x : o.x;
-        } else {
-          R* op = reinterpret_cast<R*>(P.out);
-          if (n >= 0 && n < N) __stcs(op + (oo + i), o.x);
-        }
+        store_item<C>(P, oo, i, o, prev, all_in, tf + i >= t_out && tf + i < t_end);
+        prev = o;
       }
     }
+    // hand over to the next work item (its descriptor was loaded during the last block phase)
+    __syncthreads();  // everyone is done with this work item's shared state
+    if (tid == 0) {
+      s.work = next;
+      s.wi = s.nwi;
+    }
+    __syncthreads();
   }
 }
 

@@ -242,6 +242,23 @@ __global__ void build_tables(ScaleTab* tabs, const FitJob* jobs, int n_scales, i
     else if (q < 47) tb.pw_lane[q - 15][j] = power(p, (long long)items * (q - 15));
     else tb.pw_tile[q - 47][j] = power(p, T * (q - 47));
   }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < K_kernel * (5 + 32 + 1); idx += blockDim.x) {
+    const int j = idx % K_kernel;
+    const int q = idx / K_kernel;
+    if (q < 5) {
+      const double2 v = tb.pw_thr[q][j];
+      tb.f_pw_thr[q][j] = make_float2((float)v.x, (float)v.y);
+    } else if (q < 37) {
+      const double2 v = tb.pw_lane[q - 5][j];
+      tb.f_pw_lane[q - 5][j] = make_float2((float)v.x, (float)v.y);
+    } else {
+      const double2 v = tb.pw_warp[j];
+      const float hx = (float)v.x, hy = (float)v.y;
+      tb.f_pwt[0][j] = make_float2(hx, hy);
+      tb.f_pwt[1][j] = make_float2((float)(v.x - (double)hx), (float)(v.y - (double)hy));
+    }
+  }
   if (threadIdx.x == 0) {
     tb.L = L;
     tb.n0 = J.n0;
@@ -261,6 +278,36 @@ __global__ void build_tables(ScaleTab* tabs, const FitJob* jobs, int n_scales, i
       tb.cL[j] = -gain * sg * tb.l[j];
     }
   }
+}
+
+// Kernel-integral form: two-level table of e^{i pi r / L} = hi[r >> 10] * lo[r & 1023] for the
+// per-tile phase anchors (r = (p t) mod 2L is exact; each entry is one FP64 sincospi, rounded once).
+__global__ void phase_tables(ScaleTab* tabs, const FitJob* jobs, float2* buf, const long long* poff) {
+  const int s = blockIdx.x;
+  const long long L = jobs[s].L;
+  const long long nhi = (2 * L) / 1024 + 2;
+  float2* hi = buf + poff[s];
+  float2* lo = hi + nhi;
+  for (long long a = threadIdx.x; a < nhi; a += blockDim.x) {
+    double sn, cs;
+    sincospi((double)((1024 * a) % (2 * L)) / (double)L, &sn, &cs);
+    hi[a] = make_float2((float)cs, (float)sn);
+  }
+  for (int b = threadIdx.x; b < 1024; b += blockDim.x) {
+    double sn, cs;
+    sincospi((double)b / (double)L, &sn, &cs);
+    lo[b] = make_float2((float)cs, (float)sn);
+  }
+  if (threadIdx.x == 0) {
+    tabs[s].ph_hi = hi;
+    tabs[s].ph_lo = lo;
+  }
+}
+
+cudaError_t run_phase_tables(ScaleTab* d_tabs, const FitJob* d_jobs, int n_scales, float2* d_phase,
+                             const long long* d_poff, cudaStream_t st) {
+  phase_tables<<<n_scales, 256, 0, st>>>(d_tabs, d_jobs, d_phase, d_poff);
+  return cudaGetLastError();
 }
 
 cudaError_t run_fit(const FitJob* d_jobs, int n_scales, long long max_L, double* d_partial, int nblk,

@@ -1,0 +1,115 @@
+// How one (signal, scale) row is cut into work items. Shared by the plan (host) and the
+// allocation-free entry point (host and device), so both decompose a row identically.
+#pragma once
+
+#include "common.cuh"
+
+namespace msft {
+
+constexpr int ITEMS_DEFAULT = 16;
+constexpr long long TILE_DEFAULT = (long long)THREADS * ITEMS_DEFAULT;
+
+// Segment policies.
+//   SEG_RESTART: compensated FP32. FP32 rounding leaves about one unit of roundoff of |x| per sample
+//     in the carried window state and, with |rho| = 1, nothing ever forgets it; restarting the scan
+//     from a zero state 2L samples before each segment bounds that history to (segment + 2L)
+//     samples. Windows of 2L <= 2T samples: one CTA per segment of ceil(10 L / T) sub-tiles (the
+//     window prologue costs at most about a fifth of the segment). Longer windows: a look-back chain
+//     per segment of max(4T, 4L) outputs.
+//   SEG_ROW: one segment per row (plain FP32, whose error grows with the row length; the damped ASFT;
+//     FP64) -- windows of 2L <= 2T still go to one CTA per segment of ceil(10 L / T) sub-tiles
+//     except in the plain precision, which always keeps one look-back chain per row.
+enum { SEG_RESTART = 0, SEG_ROW = 1, SEG_PLAIN = 2 };
+
+struct RowSpec {
+  long long N, L, D;   // row length, half window, output shift
+  long long x_off;     // first input element of the row
+  long long out_off;   // first output element of the row
+  int scale;
+  int align;           // input elements per 16 bytes (segment starts are aligned to it)
+  int policy;
+  int chain;           // row index stored in the work items
+  long long wt;        // positions per step of a window segment: a CTA sub-tile, or one warp-tile
+  int warp_window;     // 1: window segments go to the warp-independent kernel
+};
+
+__host__ __device__ inline long long ws_floordiv(long long a, long long b) {
+  return (a >= 0) ? a / b : -((-a + b - 1) / b);
+}
+
+// Appends the row's work items to out (if not null) and returns their number; *slots is advanced by
+// the number of look-back slots the row uses, *subtiles by the sub-tiles it processes.
+__host__ __device__ inline long long row_work(const RowSpec& r, long long T, WorkItem* out, long long* slots,
+                                              long long* subtiles, bool* chained) {
+  const long long t_first_out = r.D, t_last_out = r.D + r.N;  // output positions [D, D + N)
+  const bool short_window = 2 * r.L <= 2 * T;
+  long long n = 0;
+  *chained = !(short_window && r.policy != SEG_PLAIN);
+  long long R;  // outputs per segment
+  if (!*chained) {
+    // CTA windows: ceil(10 L / T) sub-tiles; warp windows: max(2, ceil(16 L / WT)) warp-tiles,
+    // i.e. a prologue of at most about an eighth of the segment
+    long long sub = r.warp_window ? (16 * r.L + r.wt - 1) / r.wt : (10 * r.L + r.wt - 1) / r.wt;
+    if (sub < (r.warp_window ? 2 : 1)) sub = r.warp_window ? 2 : 1;
+    R = sub * r.wt - 2 * r.L - (r.align - 1);  // room for rounding the segment start down to 16 bytes
+  } else if (r.policy == SEG_RESTART) {
+    R = 4 * T > 4 * r.L ? 4 * T : 4 * r.L;
+  } else {
+    R = r.N;
+  }
+  if (R < 1) R = 1;
+  for (long long ts = t_first_out; ts < t_last_out; ts += R) {
+    const long long te = (ts + R < t_last_out) ? ts + R : t_last_out;
+    const long long t_dom = (ts - 2 * r.L > 0) ? ts - 2 * r.L : 0;
+    // first processed position: t_dom rounded down so that the lead loads start 16-byte aligned
+    long long t_a = t_dom - ((((r.x_off + t_dom) % r.align) + r.align) % r.align);
+    const long long step = *chained ? T : r.wt;
+    const long long n_tiles = (te - t_a + step - 1) / step;
+    if (!*chained) {
+      if (out) {
+        WorkItem w{};
+        w.x_off = r.x_off;
+        w.n = r.N;
+        w.out_off = r.out_off;
+        w.scale = r.scale;
+        w.chain = r.chain;
+        w.n_sub = (int)n_tiles;
+        w.t_a = t_a;
+        w.t_dom = t_dom;
+        w.t_out = ts;
+        w.t_end = te;
+        w.slot = -1;
+        w.slot_first = -1;
+        out[n] = w;
+      }
+      ++n;
+      *subtiles += n_tiles;
+    } else {
+      const long long first = *slots;
+      for (long long k = 0; k < n_tiles; ++k) {
+        if (out) {
+          WorkItem w{};
+          w.x_off = r.x_off;
+          w.n = r.N;
+          w.out_off = r.out_off;
+          w.scale = r.scale;
+          w.chain = r.chain;
+          w.n_sub = 1;
+          w.t_a = t_a + k * T;
+          w.t_dom = t_dom;
+          w.t_out = ts;
+          w.t_end = te;
+          w.slot = *slots;
+          w.slot_first = first;
+          out[n] = w;
+        }
+        ++n;
+        ++*slots;
+      }
+      *subtiles += n_tiles;
+    }
+  }
+  return n;
+}
+
+}  // namespace msft
