@@ -92,6 +92,7 @@ struct KParams {
   int* err;                  // host-mapped error word (device view)
   long long spin_limit;
   int64_t n_chain;           // work items [0, n_chain) use the look-back; later ones are independent
+  int64_t n_x;               // elements of the input buffer (bounds the widened loads)
   int accumulate;            // adjoint: add to the output instead of overwriting it
 };
 

@@ -170,6 +170,7 @@ extern "C" int morlet_forward_noalloc(const void* x, int64_t N, double sigma, do
   kp.spin_limit = 1LL << 20;
   kp.accumulate = 0;
   kp.n_chain = chained ? n_work : 0;
+  kp.n_x = N;
   void* args[] = {&kp};
   const long long units = chained ? n_work : (n_work + WARPS - 1) / WARPS;  // CTAs, or warps per CTA
   const int grid = (int)std::min<long long>((long long)std::max(occ, 1) * sms, units);

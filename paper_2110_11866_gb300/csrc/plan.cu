@@ -85,6 +85,7 @@ struct morlet_plan_s {
   std::vector<int64_t> lengths;
   std::vector<double> sigmas;
   std::vector<int64_t> x_off;
+  long long n_in = 0;  // input samples of the batch (sum of lengths)
   int K_fit = 0;     // terms per scale after the fit (max over scales)
   int K_kernel = 0;  // compiled term count used
   int form = 2;
@@ -312,6 +313,7 @@ cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out
   kp.err = p->d_err;
   kp.spin_limit = p->spin;
   kp.accumulate = accumulate;
+  kp.n_x = (&ln == &p->adj) ? p->n_in * (long long)p->sigmas.size() : p->n_in;  // adjoint reads the scalogram
   bool forked = false;
   if (two && w_end > c_end) {
     KParams kw = kp;
@@ -426,6 +428,7 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
       p->x_off[i] = acc;
       acc += p->lengths[i];
     }
+    p->n_in = acc;
     CK(cudaGetDevice(&p->device));
     CK(cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device));
 

@@ -96,14 +96,36 @@ struct Smem {
 // loads
 // ------------------------------------------------------------------------------------------------
 
-// v[i] = p[t + i] if lo <= t + i < hi, else 0. 128-bit loads when the run is in range and aligned.
+// v[i] = p[t + i] if lo <= t + i < hi, else 0. In range and 16-byte aligned: 128-bit loads. In
+// range but misaligned by r elements (uniform across a warp in this library's layouts): the aligned
+// 128-bit chunks covering the run plus one, shifted by r in registers, provided that superset lies
+// inside [0, cap) (cap = elements of the input buffer reachable from p). Otherwise element loads.
+template <typename E, int N, int S>
+__device__ __forceinline__ void shift_copy(const E* e, E (&v)[N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) v[i] = e[i + S];
+}
+
+template <typename E, int N, int VEC>
+__device__ __forceinline__ void shift_in(const int4 (&c)[N / VEC + 1], int r, E (&v)[N]) {
+  const E* e = reinterpret_cast<const E*>(c);
+  if (r == 1) shift_copy<E, N, 1>(e, v);
+  if constexpr (VEC > 2) {
+    if (r == 2) shift_copy<E, N, 2>(e, v);
+  }
+  if constexpr (VEC > 3) {
+    if (r == 3) shift_copy<E, N, 3>(e, v);
+  }
+}
+
 template <typename E, int N>
 __device__ __forceinline__ void load_run(const E* __restrict__ p, int64_t t, int64_t lo, int64_t hi,
-                                         E (&v)[N]) {
+                                         E (&v)[N], int64_t cap = -1) {
+  constexpr int VEC = 16 / sizeof(E);
   if (t >= lo && t + N <= hi) {
     const E* q = p + t;
-    constexpr int VEC = 16 / sizeof(E);
-    if ((reinterpret_cast<uintptr_t>(q) & 15) == 0) {
+    const int r = (int)((reinterpret_cast<uintptr_t>(q) & 15) / sizeof(E));
+    if (r == 0) {
 #pragma unroll
       for (int i = 0; i < N; i += VEC) {
         const int4 u = __ldg(reinterpret_cast<const int4*>(q + i));
@@ -111,10 +133,20 @@ __device__ __forceinline__ void load_run(const E* __restrict__ p, int64_t t, int
 #pragma unroll
         for (int j = 0; j < VEC; ++j) v[i + j] = e[j];
       }
-    } else {
-#pragma unroll
-      for (int i = 0; i < N; ++i) v[i] = __ldg(q + i);
+      return;
     }
+    if constexpr (VEC > 1 && N % VEC == 0) {
+      if (cap >= 0 && t - r >= 0 && t - r + N + VEC <= cap) {
+        int4 c[N / VEC + 1];
+        const int4* a = reinterpret_cast<const int4*>(q - r);
+#pragma unroll
+        for (int i = 0; i <= N / VEC; ++i) c[i] = __ldg(a + i);
+        shift_in<E, N, VEC>(c, r, v);
+        return;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = __ldg(q + i);
   } else {
 #pragma unroll
     for (int i = 0; i < N; ++i) {
@@ -249,7 +281,7 @@ __global__ void __launch_bounds__(THREADS, C::MINB) scan_kernel(const KParams P)
       const bool live = (tf + ITEMS > lo && tf < N) || (tf - Wl + ITEMS > lo && tf - Wl < N);
       if (live) {
         load_run<EIn, ITEMS>(xs, tf, lo, N, xa);
-        load_run<EIn, ITEMS>(xs, tf - Wl, lo, N, xl);
+        load_run<EIn, ITEMS>(xs, tf - Wl, lo, N, xl, P.n_x - wi.x_off);
       } else {
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) xa[i] = xl[i] = EIn{};

@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
       const bool live = (tf + ITEMS > lo && tf < N) || (tf - Wl + ITEMS > lo && tf - Wl < N);
       if (live) {
         load_run<EIn, ITEMS>(xs, tf, lo, N, xa);
-        load_run<EIn, ITEMS>(xs, tf - Wl, lo, N, xl);
+        load_run<EIn, ITEMS>(xs, tf - Wl, lo, N, xl, P.n_x - wi.x_off);
       } else {
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) xa[i] = xl[i] = EIn{};
