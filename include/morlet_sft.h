@@ -148,12 +148,13 @@ int morlet_plan_info(morlet_plan_t plan, int32_t s, int64_t* L, int32_t* p0, int
                      double* l, int32_t* n0);
 
 /*
- * morlet_plan_stats - launch shape and work of the forward kernel, for measurement:
- * out[0] = threads per CTA, out[1] = samples per thread, out[2] = CTAs launched,
- * out[3] = work items, out[4] = sub-tiles processed (incl. window prologues), out[5] = rows in
- * look-back mode, out[6] = rows in per-tile window mode, out[7] = kernel launches per forward.
+ * morlet_plan_stats - launch shape and work of the forward, for measurement:
+ * out[0] = threads per CTA, out[1] = samples per thread, out[2] = CTAs of the look-back kernel,
+ * out[3] = work items of the scan kernels, out[4] = sub-tiles processed (incl. window prologues),
+ * out[5] = rows in look-back mode, out[6] = rows in window-segment mode, out[7] = kernel launches
+ * per forward, out[8] = rows whose work items start from prefix sums, out[9] = prefix-sum work items.
  */
-int morlet_plan_stats(morlet_plan_t plan, int64_t out[8]);
+int morlet_plan_stats(morlet_plan_t plan, int64_t out[10]);
 
 /*
  * morlet_plan_set_spin_limit - change the bounded-wait limit (polls) of later launches; used to make
@@ -162,9 +163,11 @@ int morlet_plan_stats(morlet_plan_t plan, int64_t out[8]);
 int morlet_plan_set_spin_limit(morlet_plan_t plan, int64_t polls);
 
 /*
- * morlet_debug_skip_tickets - testing hook: the next forward starts its work-item counter at `skip`
- * instead of 0, so the first `skip` work items are never processed and tiles that wait on them hit
- * the bounded wait. Must be followed by morlet_last_device_error.
+ * morlet_debug_skip_tickets - testing hook: in the next forward, the first kernel that waits on
+ * predecessors (the prefix-sum kernel when the plan has start-state rows, else the look-back scan
+ * kernel) starts its work-item counter at `skip` instead of 0, so its first `skip` work items are
+ * never processed and items that wait on them hit the bounded wait. The outputs of that forward are
+ * undefined. Must be followed by morlet_last_device_error.
  */
 int morlet_debug_skip_tickets(morlet_plan_t plan, int64_t skip);
 

@@ -217,9 +217,10 @@ def morlet_plan_info(plan: Plan, s: int) -> dict:
 
 
 def morlet_plan_stats(plan: Plan) -> dict:
-    o = (ctypes.c_int64 * 8)()
+    o = (ctypes.c_int64 * 10)()
     _check(lib().morlet_plan_stats(plan.handle, o), "morlet_plan_stats")
-    keys = ["threads", "items", "ctas", "work_items", "sub_tiles", "rows_lookback", "rows_window", "launches"]
+    keys = ["threads", "items", "ctas", "work_items", "sub_tiles", "rows_lookback", "rows_window", "launches",
+            "rows_start_state", "prefix_items"]
     return dict(zip(keys, list(o)))
 
 

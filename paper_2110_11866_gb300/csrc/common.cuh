@@ -32,9 +32,14 @@ struct ChainDesc {
 
 // One unit of work: `n_sub` consecutive sub-tiles of one row, sub-tile s covering scan positions
 // t in [t_a + s*T, t_a + (s+1)*T) (the output of position t is n = t - D). Samples before t_dom
-// count as zero; outputs are stored for positions in [t_out, t_end). When slot < 0 the scan starts
-// from a zero state at t_a (the window is recomputed from t_dom); otherwise the state entering the
-// work item comes from the look-back over status slots [slot_first, slot).
+// count as zero; outputs are stored for positions in [t_out, t_end). The state entering the work
+// item is, in this order of precedence:
+//  - p_row >= 0 (start-state items of the warp kernel): computed from the row's lag-free prefix
+//    sums P at 512-position tile ends, tile 0 starting at t_grid (psum_kernel.cuh);
+//  - slot >= 0: the look-back over status slots [slot_first, slot);
+//  - otherwise zero at t_a (the window is recomputed from t_dom).
+// Prefix-sum items (psum kernel) use the same record: tiles [t_a, t_a + n_sub * 512) of a row,
+// results at prefix index p_row, look-back slot `slot`.
 struct WorkItem {
   int64_t x_off;       // the row: first input element, length, first output element, scale
   int64_t n;
@@ -49,6 +54,8 @@ struct WorkItem {
   int64_t t_end;
   int64_t slot;        // status slot of this work item, or -1
   int64_t slot_first;  // status slot of the first work item of the segment
+  int64_t p_row;       // prefix-sum index of the row's tile 0 (psum: of the item's first tile), or -1
+  int64_t t_grid;      // first position of the row's tile 0 (tiles are 512 positions)
 };
 
 // Per-scale constants, all computed on the GPU in FP64 from the fit (tables.cu).
@@ -76,6 +83,7 @@ struct ScaleTab {
   float2 f_pw_thr[5][KMAX];   // rho^{items * 2^l}
   float2 f_pw_lane[32][KMAX]; // rho^{items * lane}
   float2 f_pwt[2][KMAX];      // rho^{items * 32} as hi + lo
+  float4 c_pw_tile[33][KMAX]; // pw_tile as two-float complex (re.hi, re.lo, im.hi, im.lo)
 };
 
 struct KParams {
@@ -93,6 +101,7 @@ struct KParams {
   long long spin_limit;
   int64_t n_chain;           // work items [0, n_chain) use the look-back; later ones are independent
   int64_t n_x;               // elements of the input buffer (bounds the widened loads)
+  void* pbuf;                // lag-free prefix sums at tile ends: per tile, K two-float complex
   int accumulate;            // adjoint: add to the output instead of overwriting it
 };
 
@@ -269,6 +278,9 @@ template <> __device__ __forceinline__ DFC ld_cg2<DFC>(const DFC* p) {
   const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
   return DFC{DF{v.x, v.y}, DF{v.z, v.w}};
 }
+
+__device__ __forceinline__ DFC dfc_from_f4(float4 v) { return DFC{DF{v.x, v.y}, DF{v.z, v.w}}; }
+__device__ __forceinline__ DFC dfc_neg(DFC a) { return DFC{df_neg(a.re), df_neg(a.im)}; }
 
 template <typename V> __device__ __forceinline__ void st_cg2(V* p, V v) { __stcg(p, v); }
 template <> __device__ __forceinline__ void st_cg2<DFC>(DFC* p, DFC v) {

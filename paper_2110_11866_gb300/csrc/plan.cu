@@ -60,6 +60,13 @@ namespace {
 constexpr int ITEMS = 16;
 constexpr long long TILE = (long long)THREADS * ITEMS;
 constexpr long long DEFAULT_SPIN = 1LL << 20;  // polls of ~64 ns sleep + an L2 round trip: about 1 s
+// work counters per launch: look-back kernel, warp kernel (window items), warp kernel (start-state
+// items), prefix-sum kernel
+constexpr int TICKETS = 4;
+constexpr long long PS_TILE_H = 512, PS_CHUNK_H = 8;  // prefix-sum tile and chunk (psum_kernel.cuh)
+// Rows whose half window exceeds this take their start states from prefix sums: a window segment
+// of such a row (about 16 L positions per warp) would leave too few, too long work items.
+constexpr long long SS_MIN_L = 2048;
 
 // A launchable transform: kernel, work table, chains and status arrays.
 struct Launch {
@@ -74,6 +81,14 @@ struct Launch {
   long long rows_chain = 0, rows_halo = 0;
   std::vector<long long> scale_begin;  // adjoint: work items of scale s are [scale_begin[s], scale_begin[s+1])
   std::vector<long long> chain_end;    // per launch range: look-back items come first, up to chain_end
+  // start-state rows (forward, compensated FP32, long windows): warp-kernel items [ss_begin, n_work)
+  // start from the prefix sums that the psum kernel computes over the work items d_pwork
+  long long ss_begin = 0;
+  const void* func_p = nullptr;
+  WorkItem* d_pwork = nullptr;
+  long long n_pwork = 0;
+  int grid_p = 0;
+  long long n_pslots = 0, n_ptiles = 0, rows_ss = 0;
 };
 
 }  // namespace
@@ -99,7 +114,12 @@ struct morlet_plan_s {
   void* d_agg = nullptr;
   void* d_incl = nullptr;
   long long n_slots = 0;
-  unsigned long long* d_ticket = nullptr;  // one counter per launch (adjoint: one per scale)
+  uint32_t* d_pflags = nullptr;  // prefix-sum kernel: status flags, aggregates, inclusive states
+  void* d_pagg = nullptr;
+  void* d_pincl = nullptr;
+  void* d_pbuf = nullptr;        // prefix sums at tile ends
+  long long ss_min_L = 0;        // rows with L above this use start states (0: none)
+  unsigned long long* d_ticket = nullptr;  // TICKETS counters per launch (adjoint: per scale)
   int* h_err = nullptr;                    // host-mapped error word
   int* d_err = nullptr;
   long long spin = DEFAULT_SPIN;
@@ -157,8 +177,23 @@ int seg_policy(const morlet_plan_s* p) {
   return SEG_ROW;
 }
 
+// Start-state rows: forward, compensated FP32 SFT in the rotating form, real input, long window.
+bool ss_row(const morlet_plan_s* p, bool adjoint, const ScaleTab& tb) {
+  return !adjoint && p->ss_min_L > 0 && p->form == 2 && p->desc.precision == MORLET_FP32_COMP &&
+         p->desc.transform == MORLET_SFT && !(p->desc.flags & MORLET_FLAG_NO_HALO) && tb.L > p->ss_min_L;
+}
+
+// Tiles of a start-state row: tile 0 starts at t_grid (the input element of every tile start is
+// 16-byte aligned); the outputs (positions [D, D + N)) lie in tiles [kD, kE].
+void ss_tiles(long long x_off, long long N, long long D, long long& t_grid, long long& kD, long long& kE) {
+  const long long g = (4 - (x_off % 4)) % 4;
+  t_grid = g - PS_TILE_H;
+  kD = (D - t_grid) / PS_TILE_H;
+  kE = (D + N - 1 - t_grid) / PS_TILE_H;
+}
+
 void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& work, std::vector<ChainDesc>& chains,
-                long long& slots, Launch& ln) {
+                long long& slots, Launch& ln, std::vector<WorkItem>& pwork, long long warp_slots) {
   const int S = (int)p->sigmas.size();
   const long long nsig = (long long)p->lengths.size();
   // Row order. Forward: blocks of signals holding about 16 M input samples (their input stays in
@@ -180,6 +215,16 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
     }
   }
   const int esz = (int)p->elem * (adjoint ? 2 : 1);  // bytes per input element
+  // start-state items: n_ss tiles each, as many tiles as leaves about four items per warp slot
+  long long ss_total = 0;
+  for (auto& rs : order) {
+    const ScaleTab& tb = p->h_tabs[rs.second];
+    if (!ss_row(p, adjoint, tb)) continue;
+    long long tg, kD, kE;
+    ss_tiles(p->x_off[rs.first], p->lengths[rs.first], tb.D, tg, kD, kE);
+    ss_total += kE - kD + 1;
+  }
+  const long long n_ss = std::max(4LL, std::min(32LL, ss_total / std::max(1LL, 4 * warp_slots)));
   ln.scale_begin.assign(S + 1, 0);
   int prev_scale = -1;
   for (auto& rs : order) {
@@ -199,6 +244,54 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
     c.scale = s;
     const int ci = (int)chains.size();
     chains.push_back(c);
+    if (ss_row(p, adjoint, tb)) {
+      long long tg, kD, kE;
+      ss_tiles(c.x_off, N, tb.D, tg, kD, kE);
+      const long long pbase = ln.n_ptiles;
+      long long k_last = kD;  // tile of the last item start
+      for (long long k = kD; k <= kE; k += n_ss) {
+        const long long nsub = std::min(n_ss, kE - k + 1);
+        WorkItem w{};
+        w.x_off = c.x_off;
+        w.n = N;
+        w.out_off = c.out_off;
+        w.scale = s;
+        w.chain = ci;
+        w.n_sub = (int)nsub;
+        w.t_a = tg + PS_TILE_H * k;
+        w.t_dom = 0;
+        w.t_out = std::max<int64_t>(w.t_a, tb.D);
+        w.t_end = std::min<int64_t>(w.t_a + PS_TILE_H * nsub, tb.D + N);
+        w.slot = -1;
+        w.slot_first = -1;
+        w.p_row = pbase;
+        w.t_grid = tg;
+        work.push_back(w);
+        ln.sub_tiles += nsub;
+        k_last = k;
+      }
+      // prefix sums at the ends of tiles 0 .. k_last - 1, in chunks of PS_CHUNK_H tiles
+      const long long n_t = k_last;
+      const long long first = ln.n_pslots;
+      for (long long k = 0; k < n_t; k += PS_CHUNK_H) {
+        WorkItem w{};
+        w.x_off = c.x_off;
+        w.n = N;
+        w.out_off = c.out_off;
+        w.scale = s;
+        w.chain = ci;
+        w.n_sub = (int)std::min(PS_CHUNK_H, n_t - k);
+        w.t_a = tg + PS_TILE_H * k;
+        w.slot = ln.n_pslots++;
+        w.slot_first = first;
+        w.p_row = pbase + k;
+        w.t_grid = tg;
+        pwork.push_back(w);
+      }
+      ln.n_ptiles += n_t;
+      ln.rows_ss++;
+      continue;
+    }
     const bool warp_window = (p->form != 1);
     RowSpec r{N, tb.L, tb.D, c.x_off, c.out_off, s, 16 / esz, seg_policy(p), ci,
               warp_window ? (long long)32 * ITEMS : TILE, warp_window ? 1 : 0};
@@ -227,30 +320,45 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
     auto mid = std::stable_partition(work.begin() + rg.first, work.begin() + rg.second,
                                      [](const WorkItem& w) { return w.slot >= 0; });
     ln.chain_end.push_back((long long)(mid - work.begin()));
+    // then the window items, then the start-state items (which wait for the prefix sums)
+    auto ss = std::stable_partition(mid, work.begin() + rg.second, [](const WorkItem& w) { return w.p_row < 0; });
+    ln.ss_begin = (long long)(ss - work.begin());
   }
+  if (adjoint) ln.ss_begin = (long long)work.size();
 }
 
 int setup_launch(morlet_plan_s* p, bool adjoint, Launch& ln, long long& slots) {
   int rc = MORLET_OK;
-  std::vector<WorkItem> work;
+  std::vector<WorkItem> work, pwork;
   std::vector<ChainDesc> chains;
-  build_work(p, adjoint, work, chains, slots, ln);
   ln.func = kernel_for(variant_of(p, adjoint), p->K_kernel, false);
   if (!ln.func) return MORLET_ERR_UNSUPPORTED;
   if (p->form != 1) {
     ln.func_w = kernel_for(variant_of(p, adjoint), p->K_kernel, true);
     if (!ln.func_w) return MORLET_ERR_UNSUPPORTED;
-  }
-  ln.n_work = (long long)work.size();
-  int occ = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ln.func, THREADS, 0));
-  if (occ < 1) occ = 1;
-  ln.grid = (int)std::min<long long>((long long)occ * p->sms, std::max<long long>(1, ln.n_work));
-  if (ln.func_w) {
     int occw = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occw, ln.func_w, THREADS, 0));
     if (occw < 1) occw = 1;
     ln.grid_w = occw * p->sms;
+  }
+  build_work(p, adjoint, work, chains, slots, ln, pwork, (long long)ln.grid_w * WARPS);
+  ln.n_work = (long long)work.size();
+  {
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ln.func, THREADS, 0));
+    if (occ < 1) occ = 1;
+    ln.grid = (int)std::min<long long>((long long)occ * p->sms, std::max<long long>(1, ln.n_work));
+  }
+  if (!pwork.empty()) {
+    ln.func_p = kernel_psum(p->K_kernel);
+    if (!ln.func_p) return MORLET_ERR_UNSUPPORTED;
+    int occp = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occp, ln.func_p, THREADS, 0));
+    if (occp < 1) occp = 1;
+    ln.grid_p = occp * p->sms;
+    ln.n_pwork = (long long)pwork.size();
+    CK(cudaMalloc(&ln.d_pwork, sizeof(WorkItem) * pwork.size()));
+    CK(cudaMemcpy(ln.d_pwork, pwork.data(), sizeof(WorkItem) * pwork.size(), cudaMemcpyHostToDevice));
   }
   CK(cudaMalloc(&ln.d_work, sizeof(WorkItem) * std::max<size_t>(1, work.size())));
   CK(cudaMalloc(&ln.d_chains, sizeof(ChainDesc) * std::max<size_t>(1, chains.size())));
@@ -264,8 +372,10 @@ fail:
 void free_launch(Launch& ln) {
   cudaFree(ln.d_work);
   cudaFree(ln.d_chains);
+  cudaFree(ln.d_pwork);
   ln.d_work = nullptr;
   ln.d_chains = nullptr;
+  ln.d_pwork = nullptr;
 }
 
 int check_latched(morlet_plan_s* p) {
@@ -282,16 +392,23 @@ size_t carry_bytes(const morlet_plan_s* p) {
   return (p->desc.precision == MORLET_FP32_PLAIN || p->desc.transform == MORLET_ASFT) ? 8 : 16;
 }
 
-// Enqueue one launch range: reset its work counters (and the status flags), then the look-back
-// kernel over the chain items on `st` and, concurrently on the plan's second stream, the
-// warp-independent kernel over the window items. tickets[0] / tickets[1] count the two kernels.
+// Enqueue one launch range: reset its work counters (and the status flags), then
+//  - on the plan's second stream, the warp kernel over the window items;
+//  - on `st`, the prefix-sum kernel and after it the warp kernel over the start-state items, then
+//    the look-back kernel over the chain items.
+// tickets[0..3] count the look-back, window, start-state and prefix-sum kernels.
 cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out, long long w_begin, long long w_end,
                     long long w_chain_end, unsigned long long* tickets, bool clear_flags, cudaStream_t st,
                     int accumulate = 0) {
-  cudaError_t e = cudaMemsetAsync(tickets, 0, 2 * sizeof(unsigned long long), st);
+  const bool two = ln.func_w != nullptr;
+  const long long c_end = two ? w_chain_end : w_end;
+  const long long s_beg = two ? std::min(std::max(ln.ss_begin, c_end), w_end) : w_end;
+  cudaError_t e = cudaMemsetAsync(tickets, 0, TICKETS * sizeof(unsigned long long), st);
   if (e == cudaSuccess && p->skip_tickets > 0) {
+    // testing hook: skip the first work items of the first look-back kernel of this launch
     const unsigned long long v = (unsigned long long)p->skip_tickets;
-    e = cudaMemcpyAsync(tickets, &v, sizeof(v), cudaMemcpyHostToDevice, st);
+    const int at = (w_end > s_beg && ln.n_pwork > 0) ? 3 : 0;
+    e = cudaMemcpyAsync(tickets + at, &v, sizeof(v), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     p->skip_tickets = 0;
   }
@@ -300,8 +417,6 @@ cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out
     e = cudaMemsetAsync(p->d_flags, 0, sizeof(uint32_t) * p->n_slots, st);
     if (e != cudaSuccess) return e;
   }
-  const bool two = ln.func_w != nullptr;
-  const long long c_end = two ? w_chain_end : w_end;
   KParams kp{};
   kp.x = x;
   kp.out = out;
@@ -314,11 +429,12 @@ cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out
   kp.spin_limit = p->spin;
   kp.accumulate = accumulate;
   kp.n_x = (&ln == &p->adj) ? p->n_in * (long long)p->sigmas.size() : p->n_in;  // adjoint reads the scalogram
+  kp.pbuf = p->d_pbuf;
   bool forked = false;
-  if (two && w_end > c_end) {
+  if (two && s_beg > c_end) {
     KParams kw = kp;
     kw.work = ln.d_work + c_end;
-    kw.n_work = w_end - c_end;
+    kw.n_work = s_beg - c_end;
     kw.n_chain = 0;
     kw.ticket = tickets + 1;
     e = cudaEventRecord(p->ev_fork, st);
@@ -330,6 +446,33 @@ cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out
     if (e == cudaSuccess) e = cudaEventRecord(p->ev_join, p->aux);
     if (e != cudaSuccess) return e;
     forked = true;
+  }
+  if (two && w_end > s_beg) {
+    if (ln.n_pwork > 0) {
+      e = cudaMemsetAsync(p->d_pflags, 0, sizeof(uint32_t) * ln.n_pslots, st);
+      if (e != cudaSuccess) return e;
+      KParams kq = kp;
+      kq.work = ln.d_pwork;
+      kq.n_work = ln.n_pwork;
+      kq.n_chain = ln.n_pwork;
+      kq.flags = p->d_pflags;
+      kq.agg = p->d_pagg;
+      kq.incl = p->d_pincl;
+      kq.ticket = tickets + 3;
+      void* args[] = {&kq};
+      const int grid = (int)std::min<long long>(ln.grid_p, (kq.n_work + WARPS - 1) / WARPS);
+      e = cudaLaunchKernel(ln.func_p, dim3(grid), dim3(THREADS), args, 0, st);
+      if (e != cudaSuccess) return e;
+    }
+    KParams ks = kp;
+    ks.work = ln.d_work + s_beg;
+    ks.n_work = w_end - s_beg;
+    ks.n_chain = 0;
+    ks.ticket = tickets + 2;
+    void* args[] = {&ks};
+    const int grid = (int)std::min<long long>(ln.grid_w, (ks.n_work + WARPS - 1) / WARPS);
+    e = cudaLaunchKernel(ln.func_w, dim3(grid), dim3(THREADS), args, 0, st);
+    if (e != cudaSuccess) return e;
   }
   if (c_end > w_begin) {
     kp.work = ln.d_work + w_begin;
@@ -375,6 +518,10 @@ void morlet_plan_destroy(morlet_plan_t p) {
   cudaFree(p->d_agg);
   cudaFree(p->d_incl);
   cudaFree(p->d_ticket);
+  cudaFree(p->d_pflags);
+  cudaFree(p->d_pagg);
+  cudaFree(p->d_pincl);
+  cudaFree(p->d_pbuf);
   if (p->h_err) cudaFreeHost(p->h_err);
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
@@ -501,6 +648,7 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
     CK(cudaStreamSynchronize(st));
 
     // work tables and status arrays
+    p->ss_min_L = SS_MIN_L;
     long long slots = 0;
     rc = setup_launch(p, false, p->fwd, slots);
     if (rc) goto fail;
@@ -517,7 +665,14 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
       CK(cudaMalloc(&p->d_agg, carry_bytes(p) * nt_adj * p->n_slots));
       CK(cudaMalloc(&p->d_incl, carry_bytes(p) * nt_adj * p->n_slots));
     }
-    CK(cudaMalloc(&p->d_ticket, sizeof(unsigned long long) * 2 * (S + 1)));
+    if (p->fwd.n_pwork > 0) {
+      const size_t kb = sizeof(float4) * p->K_kernel;  // K two-float complex values
+      CK(cudaMalloc(&p->d_pflags, sizeof(uint32_t) * p->fwd.n_pslots));
+      CK(cudaMalloc(&p->d_pagg, kb * p->fwd.n_pslots));
+      CK(cudaMalloc(&p->d_pincl, kb * p->fwd.n_pslots));
+      CK(cudaMalloc(&p->d_pbuf, kb * std::max(1LL, p->fwd.n_ptiles)));
+    }
+    CK(cudaMalloc(&p->d_ticket, sizeof(unsigned long long) * TICKETS * (S + 1)));
     CK(cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
@@ -579,7 +734,7 @@ int morlet_backward(morlet_plan_t p, const void* gW, void* gx, void* stream) {
   const int S = (int)p->sigmas.size();
   for (int s = 0; s < S; ++s) {
     const cudaError_t e = enqueue(p, p->adj, gW, gx, p->adj.scale_begin[s], p->adj.scale_begin[s + 1],
-                                  p->adj.chain_end[s], p->d_ticket + 2 * (1 + s), s == 0, st, s > 0 ? 1 : 0);
+                                  p->adj.chain_end[s], p->d_ticket + TICKETS * (1 + s), s == 0, st, s > 0 ? 1 : 0);
     if (e != cudaSuccess) return cuda_status(e);
   }
   return MORLET_OK;
@@ -608,16 +763,22 @@ int morlet_plan_info(morlet_plan_t p, int32_t s, int64_t* L, int32_t* p0, int32_
   return MORLET_OK;
 }
 
-int morlet_plan_stats(morlet_plan_t p, int64_t o[8]) {
+int morlet_plan_stats(morlet_plan_t p, int64_t o[10]) {
   if (!p || !o) return MORLET_ERR_ARG;
+  const Launch& f = p->fwd;
+  const bool two = f.func_w != nullptr;
+  const long long c_end = two ? f.chain_end[0] : f.n_work;
+  const long long s_beg = two ? std::min(std::max(f.ss_begin, c_end), f.n_work) : f.n_work;
   o[0] = THREADS;
   o[1] = ITEMS;
-  o[2] = p->fwd.grid;
-  o[3] = p->fwd.n_work;
-  o[4] = p->fwd.sub_tiles;
-  o[5] = p->fwd.rows_chain;
-  o[6] = p->fwd.rows_halo;
-  o[7] = 1;
+  o[2] = f.grid;
+  o[3] = f.n_work;
+  o[4] = f.sub_tiles;
+  o[5] = f.rows_chain;
+  o[6] = f.rows_halo;
+  o[7] = (c_end > 0) + (s_beg > c_end) + (f.n_work > s_beg) + (f.n_pwork > 0 && f.n_work > s_beg);
+  o[8] = f.rows_ss;
+  o[9] = f.n_pwork;
   return MORLET_OK;
 }
 

@@ -1,0 +1,258 @@
+// Lag-free prefix sums of the rotating-form recursion at tile ends: the start states of the warp
+// kernel's long-window rows (compensated FP32, SFT, real input).
+//
+// For one row and one harmonic let P(t) = sum_{0 <= u <= t} rho^{t-u} x[u], so P(t) = rho P(t-1) + x[t].
+// Substituting into the rotating form V[t] = rho V[t-1] + x[t] - kappa rho x[t-2L-1] shows that
+//     V(t) = P(t) - kappa rho P(t - 2L - 1)
+// (both sides obey the same recursion and vanish for t < 0). P is the running sum behind the
+// sliding sum of Sec. II-B without its lagged subtraction; with |rho| = 1 it grows without bound
+// when x holds the harmonic's own frequency, so it is kept in two-float precision. A window state
+// taken as the difference of two such values then carries only the FP32 rounding of the tile sums
+// inside its own window: a work item of the warp kernel can start anywhere in a row from an exact
+// state, with neither a look-back nor a 2L-sample prologue.
+//
+// Tiles are 512 positions (32 lanes x 16 samples), tile 0 of a row starting at the position t_grid
+// whose input element is 16-byte aligned. A work item is a chunk of up to 8 tiles (4096 positions,
+// the unit of the pw_tile powers) of one row, taken by one warp:
+//   per tile: lane-serial Horner sum of its 16 samples, a warp reduction weighted by
+//             rho^{16 (31 - lane)} -> the tile sum G (FP32), and the chunk aggregate in FP32;
+//   warp-level decoupled look-back over the row's earlier chunks (two-float) -> P before the chunk;
+//   P at the end of every tile of the chunk, two-float, stored for the warp kernel.
+#pragma once
+
+#include "scan_kernel.cuh"
+
+namespace msft {
+
+constexpr int PS_TILE = 512;                // positions per tile of the prefix sums
+constexpr int PS_CHUNK = 8;                 // tiles per prefix-sum work item
+static_assert(PS_TILE * PS_CHUNK == THREADS * 16, "a chunk is one pw_tile unit");
+
+// Two-float complex from the hi / lo FP32 copies of rho^{512} of term j.
+__device__ __forceinline__ DFC dfc_rho512(const ScaleTab* tb, int j) {
+  const float2 h = __ldg(&tb->f_pwt[0][j]);
+  const float2 l = __ldg(&tb->f_pwt[1][j]);
+  return DFC{DF{h.x, l.x}, DF{h.y, l.y}};
+}
+
+// Warp-level decoupled look-back in two-float precision. Lane v < NT holds `mine`, the aggregate of
+// term v over this item; the function publishes it (unless the item is the first of its chain),
+// sums the predecessors' published values back to the first inclusive one, each rotated by
+// rho^{4096 d} for a predecessor ending 4096 d positions before this item, and returns in lane v
+// the state entering the item. Every wait is bounded by P.spin_limit polls; on timeout the error
+// word is set and unpublished predecessors count as zero.
+template <int NT>
+__device__ __forceinline__ DFC warp_lookback(const KParams& P, int64_t slot, int64_t slot_first, DFC mine,
+                                             const ScaleTab* tb, int lane) {
+  using CO = CarryOps<DFC>;
+  DFC carry = CO::zero();
+  if (slot == slot_first) return carry;
+  DFC* aggp = reinterpret_cast<DFC*>(P.agg);
+  const DFC* inclp = reinterpret_cast<const DFC*>(P.incl);
+  if (lane < NT) {
+    st_cg2(aggp + slot * NT + lane, mine);
+    __threadfence();
+  }
+  __syncwarp();
+  if (lane == 0) st_release(P.flags + slot, ST_AGG);
+  DFC rot = CO::one();
+  int64_t base = slot - 1;
+  long long polls = 0;
+  bool timed_out = false;
+  for (;;) {
+    const int64_t j = base - lane;
+    const bool valid = (j >= slot_first);
+    uint32_t f = ST_INCL;
+    bool forced = false;
+    unsigned incl_mask;
+    for (;;) {
+      f = valid ? ld_acquire(P.flags + j) : ST_INCL;
+      forced = timed_out && f == 0;
+      if (forced) f = ST_INCL;
+      incl_mask = __ballot_sync(0xffffffffu, f == ST_INCL);
+      const unsigned zero_mask = __ballot_sync(0xffffffffu, f == 0);
+      const int first = incl_mask ? (__ffs(incl_mask) - 1) : 31;
+      const unsigned need = (first == 31) ? 0xffffffffu : ((2u << first) - 1u);
+      if ((zero_mask & need) == 0) break;
+      if (++polls > P.spin_limit) {
+        timed_out = true;
+        if (lane == 0) *reinterpret_cast<volatile int*>(P.err) = DERR_TIMEOUT;
+      } else {
+        __nanosleep(64);
+      }
+    }
+    const int first = incl_mask ? (__ffs(incl_mask) - 1) : 32;
+    const bool use = (lane <= first) && valid && !forced;
+#pragma unroll
+    for (int v = 0; v < NT; ++v) {
+      DFC val = CO::zero();
+      if (use) {
+        const DFC* src = (f == ST_INCL) ? inclp : aggp;
+        val = CO::mul(dfc_from_f4(__ldg(&tb->c_pw_tile[lane][v])), ld_cg2<DFC>(src + j * NT + v));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) val = CO::add(val, CO::shfl_xor(val, o));
+      if (lane == v) carry = CO::add(CO::mul(rot, val), carry);
+    }
+    if (first < 32) break;
+    base -= 32;
+    if (lane < NT) rot = CO::mul(rot, dfc_from_f4(__ldg(&tb->c_pw_tile[32][lane])));
+  }
+  return carry;
+}
+
+// Horner sum of 16 samples with the lane's weight: returns sum_i rho^{15 - i} x_i times w.
+template <int K, int ITEMS>
+__device__ __forceinline__ void lane_sums(const float (&xa)[ITEMS], const float2 (&rho)[K], const float2 (&w)[K],
+                                          float2 (&b)[K]) {
+#pragma unroll
+  for (int j = 0; j < K; ++j) b[j] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const float vr = fmaf(rho[j].x, b[j].x, fmaf(-rho[j].y, b[j].y, xa[i]));
+      const float vi = fmaf(rho[j].y, b[j].x, rho[j].x * b[j].y);
+      b[j].x = vr;
+      b[j].y = vi;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < K; ++j) b[j] = cmul(b[j], w[j]);
+}
+
+// Sum over the warp of each b[j] (all lanes receive the sums); returns the sum of term `lane`
+// (zero in lanes >= K).
+template <int K>
+__device__ __forceinline__ float2 warp_tile_sum(float2 (&b)[K], int lane) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const float2 u = shfl_xor2(b[j], o);
+      b[j].x += u.x;
+      b[j].y += u.y;
+    }
+  }
+  float2 g = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < K; ++j)
+    if (lane == j) g = b[j];
+  return g;
+}
+
+// State entering a start-state work item of the warp kernel, returned in Cw[j] (uniform across the
+// warp, FP32). With b = wi.t_a a tile start and q = b - 2L - 2:
+//     V(b - 1) = P(b - 1) - kappa rho P(q),
+//     P(q)     = rho^{-(e - q)} (rho^{512} P(e - 512) + sum_{u = e-511}^{q} rho^{e-u} x[u])
+// for the tile [e - 511, e] holding q; P at tile ends comes from the prefix sums, the partial tile
+// sum from the samples. kappa rho rho^{-(e-q)} = rho^{1-(e-q)} is formed in FP64 from the exact
+// integer angle (p (e - q - 1)) mod 2L (SFT: |rho| = 1 and kappa = 1).
+template <int K, int ITEMS>
+__device__ __forceinline__ void start_state(const KParams& P, const WorkItem& wi, const ScaleTab* tb,
+                                            const float2 (&rho)[K], int lane, float2 (&Cw)[K]) {
+  using CO = CarryOps<DFC>;
+  const int jl = lane < K ? lane : 0;
+  const DFC* pb = reinterpret_cast<const DFC*>(P.pbuf) + wi.p_row * K;
+  const int64_t L = tb->L;
+  const int64_t kb = (wi.t_a - wi.t_grid) / PS_TILE;
+  DFC v = CO::zero();
+  if (kb >= 1) v = dfc_from_f4(__ldg(reinterpret_cast<const float4*>(pb + (kb - 1) * K + jl)));
+  const int64_t q = wi.t_a - 2 * L - 2;
+  if (q >= 0) {  // warp-uniform
+    const int64_t k0 = (q - wi.t_grid) / PS_TILE;
+    const int64_t a0 = wi.t_grid + k0 * PS_TILE;
+    const int m = (int)(a0 + PS_TILE - 1 - q);  // e - q, 0 .. 511
+    const float* __restrict__ xs = reinterpret_cast<const float*>(P.x) + wi.x_off;
+    float xa[ITEMS];
+    load_run<float, ITEMS>(xs, a0 + (int64_t)lane * ITEMS, 0, wi.n < q + 1 ? wi.n : q + 1, xa);
+    float2 wl[K], b[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) wl[j] = __ldg(&tb->f_pw_lane[31 - lane][j]);
+    lane_sums<K, ITEMS>(xa, rho, wl, b);
+    DFC pt = CO::from(warp_tile_sum<K>(b, lane));
+    if (k0 >= 1)
+      pt = dfc_add(dfc_mul(dfc_rho512(tb, jl), dfc_from_f4(__ldg(reinterpret_cast<const float4*>(pb + (k0 - 1) * K + jl)))), pt);
+    const long long pj = (long long)tb->p0 + jl, M = 2 * L;
+    long long r = (pj * (long long)(m - 1)) % M;
+    if (r < 0) r += M;
+    double sn, cs;
+    sincospi((double)r / (double)L, &sn, &cs);
+    v = dfc_add(v, dfc_neg(dfc_mul(dfc_from_d2(make_double2(cs, sn)), pt)));
+  }
+  const float2 vn = CO::narrow(v);
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    Cw[j].x = __shfl_sync(0xffffffffu, vn.x, j);
+    Cw[j].y = __shfl_sync(0xffffffffu, vn.y, j);
+  }
+}
+
+template <class C>
+__global__ void __launch_bounds__(THREADS, 2) psum_kernel(const KParams P) {
+  static_assert(std::is_same<typename C::R, float>::value && C::CH == 1 && C::ITEMS == 16,
+                "prefix sums are built for the FP32 real-input kernels");
+  constexpr int K = C::K, ITEMS = C::ITEMS;
+  static_assert(K <= 32, "one lane per term");
+  const int lane = threadIdx.x & 31;
+  const int jl = lane < K ? lane : 0;  // the term this lane carries
+
+  long long w = 0;
+  if (lane == 0) w = (long long)atomicAdd(P.ticket, 1ull);
+  w = __shfl_sync(0xffffffffu, w, 0);
+  while (w < P.n_work) {
+    const WorkItem wi = P.work[w];
+    const ScaleTab* tb = P.tabs + wi.scale;
+    float2 rho[K], wl[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      rho[j] = to_f2(tb->rho[j]);
+      wl[j] = __ldg(&tb->f_pw_lane[31 - lane][j]);  // rho^{16 (31 - lane)}
+    }
+    const float2 r512 = __ldg(&tb->f_pwt[0][jl]);
+    const float* __restrict__ xs = reinterpret_cast<const float*>(P.x) + wi.x_off;
+    const int64_t N = wi.n;
+
+    float2 G[PS_CHUNK];
+    float2 acc = make_float2(0.f, 0.f);  // aggregate of the chunk so far (term jl)
+#pragma unroll
+    for (int k = 0; k < PS_CHUNK; ++k) {
+      G[k] = make_float2(0.f, 0.f);
+      const int64_t t0 = wi.t_a + (int64_t)k * PS_TILE;
+      if (k < wi.n_sub && t0 < N && t0 + PS_TILE > 0) {  // warp-uniform
+        float xa[ITEMS];
+        load_run<float, ITEMS>(xs, t0 + (int64_t)lane * ITEMS, 0, N, xa);
+        float2 b[K];
+        lane_sums<K, ITEMS>(xa, rho, wl, b);
+        G[k] = warp_tile_sum<K>(b, lane);
+      }
+      if (k < wi.n_sub) acc = cfma(r512, acc, G[k]);
+    }
+    const DFC carry = warp_lookback<K>(P, wi.slot, wi.slot_first, CarryOps<DFC>::from(acc), tb, lane);
+    // inclusive state after a full chunk, published at once for the successors' look-back
+    if (wi.n_sub == PS_CHUNK) {
+      if (lane < K) {
+        const DFC inc = dfc_add(dfc_mul(dfc_from_f4(__ldg(&tb->c_pw_tile[1][lane])), carry), CarryOps<DFC>::from(acc));
+        st_cg2(reinterpret_cast<DFC*>(P.incl) + wi.slot * K + lane, inc);
+        __threadfence();
+      }
+      __syncwarp();
+      if (lane == 0) st_release(P.flags + wi.slot, ST_INCL);
+    }
+    // P at the end of each tile of the chunk, in two-float
+    const DFC r = dfc_rho512(tb, jl);
+    DFC pp = carry;
+    DFC* pb = reinterpret_cast<DFC*>(P.pbuf) + wi.p_row * K;
+#pragma unroll
+    for (int k = 0; k < PS_CHUNK; ++k) {
+      if (k < wi.n_sub) {
+        pp = dfc_add(dfc_mul(r, pp), CarryOps<DFC>::from(G[k]));
+        if (lane < K) st_cg2(pb + (int64_t)k * K + lane, pp);
+      }
+    }
+    if (lane == 0) w = (long long)atomicAdd(P.ticket, 1ull);
+    w = __shfl_sync(0xffffffffu, w, 0);
+  }
+}
+
+}  // namespace msft

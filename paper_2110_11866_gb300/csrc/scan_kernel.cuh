@@ -56,6 +56,8 @@ struct Cfg {
   static constexpr int NT = CH * K_;
   static constexpr int T = THREADS * ITEMS_;
   static constexpr int MINB = (sizeof(R_) == 4 && NT <= 4) ? 3 : (NT <= 8 ? 2 : 1);
+  // start states from prefix sums (warp kernel): compensated FP32, real input, rotating form
+  static constexpr bool START = std::is_same<CV_, DFC>::value && CH == 1 && FORM_ == FORM_RF && !ASFT_;
   static_assert(FORM_ == FORM_RF || CH == 1, "kernel-integral form is built for real input only");
   static_assert(NT <= 32, "one lane per scanned value in the block phase");
 };

@@ -243,6 +243,12 @@ __global__ void build_tables(ScaleTab* tabs, const FitJob* jobs, int n_scales, i
     else tb.pw_tile[q - 47][j] = power(p, T * (q - 47));
   }
   __syncthreads();
+  for (int idx = threadIdx.x; idx < K_kernel * 33; idx += blockDim.x) {
+    const double2 v = tb.pw_tile[idx / K_kernel][idx % K_kernel];
+    const float rh = (float)v.x, ih = (float)v.y;
+    tb.c_pw_tile[idx / K_kernel][idx % K_kernel] =
+        make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+  }
   for (int idx = threadIdx.x; idx < K_kernel * (5 + 32 + 1); idx += blockDim.x) {
     const int j = idx % K_kernel;
     const int q = idx / K_kernel;

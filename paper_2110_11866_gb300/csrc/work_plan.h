@@ -80,6 +80,7 @@ __host__ __device__ inline long long row_work(const RowSpec& r, long long T, Wor
         w.t_end = te;
         w.slot = -1;
         w.slot_first = -1;
+        w.p_row = -1;
         out[n] = w;
       }
       ++n;
@@ -101,6 +102,7 @@ __host__ __device__ inline long long row_work(const RowSpec& r, long long T, Wor
           w.t_end = te;
           w.slot = *slots;
           w.slot_first = first;
+          w.p_row = -1;
           out[n] = w;
         }
         ++n;

@@ -5,11 +5,13 @@
 //   -> pass 2 (outputs) -> carry C <- rho^{32 ITEMS} C + warp total.
 // There is no barrier and no shared memory on the data path, so a stalled warp never holds up the
 // others of its CTA. The segment starts from a zero state 2L samples before its first output
-// (samples before t_dom count as zero), which keeps the FP32 residue history short. The carry step
-// uses rho^{32 ITEMS} split into two floats so that repeated steps do not drift.
+// (samples before t_dom count as zero), which keeps the FP32 residue history short; start-state
+// items (long windows, compensated FP32) instead begin from the exact state given by the row's
+// prefix sums (psum_kernel.cuh). The carry step uses rho^{32 ITEMS} split into two floats so that
+// repeated steps do not drift.
 #pragma once
 
-#include "scan_kernel.cuh"
+#include "psum_kernel.cuh"
 
 namespace msft {
 
@@ -66,6 +68,9 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
     V Cw[NT];  // state entering the current warp-tile (uniform across lanes)
 #pragma unroll
     for (int v = 0; v < NT; ++v) Cw[v] = V{};
+    if constexpr (C::START) {
+      if (wi.p_row >= 0) start_state<K, ITEMS>(P, wi, tb, rho, lane, Cw);
+    }
 
     for (int k = 0; k < wi.n_sub; ++k) {
       const int64_t tf = wi.t_a + (int64_t)k * WT + (int64_t)lane * ITEMS;

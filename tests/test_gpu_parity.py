@@ -1,7 +1,7 @@
 """GPU parity: the CUDA library through its C ABI against the CPU oracle on the same seeded inputs.
 
 Tolerances (relative max-abs error over max |W| of the oracle):
-  compensated FP32 (FP32 scan, FP64 carries): 1e-5;  FP64: 1e-12;
+  compensated FP32 (FP32 scan, two-float carries and prefix sums): 1e-5;  FP64: 1e-12;
   plain FP32 and ASFT FP32: reported by print, gated only loosely (1e-3 / 1e-4) since the method's
   plain-FP32 error grows with the row length.
 """
@@ -45,6 +45,28 @@ def test_c1_fp64_single_signal(form):
     # approximation error of the method itself (reported, K = 4, L = 4 sigma)
     true = om.morlet_true_direct(x, 64.0, 6.0)
     print(f"c1 SFT vs direct +-8 sigma Morlet: {rel_err(ref, true):.3e}")
+
+
+@pytest.mark.parametrize("K", [3, 4, 6])
+def test_start_state_rows(K):
+    """Long windows in compensated FP32: work items start from the lag-free prefix sums (several
+    chunks per row, every input alignment mod 16 bytes, rows shorter than a tile, shorter than the
+    window, and rows spanning many work items), next to short-window rows of the same plan."""
+    rng = np.random.default_rng(300 + K)
+    lens = [100000, 3, 50001, 262149, 1030, 77777]
+    sigs = [rng.standard_normal(n).astype(np.float32) for n in lens]
+    sigmas = [20.0, 255.0, 1030.0, 2000.0, 9000.0]
+    plan, out = gpu_forward(sigs, sigmas, K=K, precision=m.MORLET_FP32_COMP)
+    st = m.morlet_plan_stats(plan)
+    assert st["rows_start_state"] == len(lens) * 3 and st["prefix_items"] > 0
+    worst = 0.0
+    for i, x in enumerate(sigs):
+        for s, sg in enumerate(sigmas):
+            ref = oracle_forward(x.astype(np.float64), sg, K)
+            e = rel_err(out[i][s], ref)
+            worst = max(worst, e)
+            assert e < 1e-5, (i, sg, e)
+    print(f"start-state rows K={K}: worst {worst:.3e}")
 
 
 @pytest.mark.parametrize("precision", [m.MORLET_FP32_COMP, m.MORLET_FP32_PLAIN, m.MORLET_FP64])
@@ -127,3 +149,23 @@ def test_timeout_is_reported_and_context_survives():
     assert m.morlet_last_device_error(plan) == 0
     ref = oracle_forward(x, 3000.0, 4)
     assert rel_err(W.cpu().numpy(), ref) < 1e-3
+
+
+def test_prefix_sum_timeout_is_reported_and_context_survives():
+    """The same for the warp-level look-back of the prefix-sum kernel (compensated FP32, a long
+    window whose work items start from prefix sums)."""
+    import torch
+    x = WL.white(5, 300000)
+    plan = m.morlet_plan([len(x)], [3000.0], K=4, precision=m.MORLET_FP32_COMP, flags=m.MORLET_FLAG_NO_GRAPH)
+    st = m.morlet_plan_stats(plan)
+    assert st["rows_start_state"] == 1 and st["prefix_items"] > 2
+    m.morlet_plan_set_spin_limit(plan, 2000)
+    xt = torch.from_numpy(x).cuda()
+    W = torch.empty(len(x), dtype=torch.complex64, device="cuda")
+    m.morlet_debug_skip_tickets(plan, 1)   # the row's first chunk of prefix sums is never computed
+    m.morlet_forward(plan, xt, W)
+    assert m.morlet_last_device_error(plan) == m.MORLET_ERR_TIMEOUT
+    m.morlet_forward(plan, xt, W)
+    assert m.morlet_last_device_error(plan) == 0
+    ref = oracle_forward(x, 3000.0, 4)
+    assert rel_err(W.cpu().numpy(), ref) < 1e-5
