@@ -84,6 +84,7 @@ struct ScaleTab {
   float2 f_pw_lane[32][KMAX]; // rho^{items * lane}
   float2 f_pwt[2][KMAX];      // rho^{items * 32} as hi + lo
   float4 c_pw_tile[33][KMAX]; // pw_tile as two-float complex (re.hi, re.lo, im.hi, im.lo)
+  float4 c_pw_chunk[8][KMAX]; // rho^{32 items (m + 1)}, m = 0..7, two-float complex
 };
 
 struct KParams {
@@ -261,6 +262,14 @@ template <> struct CarryOps<DFC> {
   __device__ static T add(T a, T b) { return dfc_add(a, b); }
   __device__ static T mul(T a, T b) { return dfc_mul(a, b); }
   __device__ static float2 narrow(T a) { return make_float2(a.re.hi + a.re.lo, a.im.hi + a.im.lo); }
+  __device__ static T shfl_idx(T a, int src) {
+    T r;
+    r.re.hi = __shfl_sync(0xffffffffu, a.re.hi, src);
+    r.re.lo = __shfl_sync(0xffffffffu, a.re.lo, src);
+    r.im.hi = __shfl_sync(0xffffffffu, a.im.hi, src);
+    r.im.lo = __shfl_sync(0xffffffffu, a.im.lo, src);
+    return r;
+  }
   __device__ static T shfl_xor(T a, int o) {
     T r;
     r.re.hi = __shfl_xor_sync(0xffffffffu, a.re.hi, o);

@@ -83,15 +83,19 @@ __device__ __forceinline__ DFC warp_lookback(const KParams& P, int64_t slot, int
     }
     const int first = incl_mask ? (__ffs(incl_mask) - 1) : 32;
     const bool use = (lane <= first) && valid && !forced;
+    // lanes 0 .. first contribute: a butterfly over the smallest power of two covering them
+    int span = 1;
+    while (span < first + 1 && span < 32) span <<= 1;
 #pragma unroll
     for (int v = 0; v < NT; ++v) {
       DFC val = CO::zero();
       if (use) {
         const DFC* src = (f == ST_INCL) ? inclp : aggp;
-        val = CO::mul(dfc_from_f4(__ldg(&tb->c_pw_tile[lane][v])), ld_cg2<DFC>(src + j * NT + v));
+        val = ld_cg2<DFC>(src + j * NT + v);
+        if (lane > 0) val = CO::mul(dfc_from_f4(__ldg(&tb->c_pw_tile[lane][v])), val);
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) val = CO::add(val, CO::shfl_xor(val, o));
+      for (int o = span >> 1; o > 0; o >>= 1) val = CO::add(val, CO::shfl_xor(val, o));
+      val = CO::shfl_idx(val, 0);
       if (lane == v) carry = CO::add(CO::mul(rot, val), carry);
     }
     if (first < 32) break;
@@ -139,6 +143,44 @@ __device__ __forceinline__ float2 warp_tile_sum(float2 (&b)[K], int lane) {
   for (int j = 0; j < K; ++j)
     if (lane == j) g = b[j];
   return g;
+}
+
+// Term count padded to a power of two, and lanes per term after a reduce-scatter.
+template <int K> struct KPad {
+  static constexpr int V = K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : 16;
+  static constexpr int G = 32 / V;
+};
+
+// Reduce-scatter of b[0..K) (zero-padded to KP terms) over the warp: each butterfly level sends
+// half of the lane's remaining terms to its partner and keeps the other half, so that after log2 KP
+// levels a lane holds one term; the remaining levels complete that term's sum. Returns in every lane
+// the warp sum of term lane / G (G = 32 / KP lanes per term; terms >= K are zero padding).
+template <int K>
+__device__ __forceinline__ float2 warp_sum_scatter(const float2 (&b)[K], int lane) {
+  constexpr int KP = KPad<K>::V, G = KPad<K>::G;
+  float2 cur[KP];
+#pragma unroll
+  for (int j = 0; j < KP; ++j) cur[j] = j < K ? b[j] : make_float2(0.f, 0.f);
+  constexpr int LG = KP == 2 ? 1 : KP == 4 ? 2 : KP == 8 ? 3 : 4;  // log2 KP
+#pragma unroll
+  for (int lvl = 0; lvl < LG; ++lvl) {
+    const int H = KP >> (lvl + 1), o = 16 >> lvl;
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      const float2 snd = up ? cur[h] : cur[h + H];
+      const float2 kp = up ? cur[h + H] : cur[h];
+      const float2 rcv = shfl_xor2(snd, o);
+      cur[h] = make_float2(kp.x + rcv.x, kp.y + rcv.y);
+    }
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const float2 u = shfl_xor2(cur[0], o);
+    cur[0].x += u.x;
+    cur[0].y += u.y;
+  }
+  return cur[0];
 }
 
 // State entering a start-state work item of the warp kernel, returned in Cw[j] (uniform across the
@@ -189,13 +231,18 @@ __device__ __forceinline__ void start_state(const KParams& P, const WorkItem& wi
 }
 
 template <class C>
-__global__ void __launch_bounds__(THREADS, 2) psum_kernel(const KParams P) {
+__global__ void __launch_bounds__(THREADS, C::K <= 6 ? 3 : 2) psum_kernel(const KParams P) {
   static_assert(std::is_same<typename C::R, float>::value && C::CH == 1 && C::ITEMS == 16,
                 "prefix sums are built for the FP32 real-input kernels");
   constexpr int K = C::K, ITEMS = C::ITEMS;
-  static_assert(K <= 32, "one lane per term");
+  constexpr int G = KPad<K>::G;                         // lanes per term after the reduce-scatter
+  constexpr int OWN = G < PS_CHUNK ? G : PS_CHUNK;      // lanes of a term that own tiles
+  constexpr int TPL = PS_CHUNK / OWN;                   // consecutive tiles per owner lane
   const int lane = threadIdx.x & 31;
-  const int jl = lane < K ? lane : 0;  // the term this lane carries
+  const int tl = lane / G;                 // this lane's term (>= K: padding)
+  const int sl = lane % G;                 // slot in the term's lane group
+  const int tq = tl < K ? tl : 0;          // table index
+  const bool owner = tl < K && sl < OWN;   // owns tiles sl * TPL .. sl * TPL + TPL - 1
 
   long long w = 0;
   if (lane == 0) w = (long long)atomicAdd(P.ticket, 1ull);
@@ -209,45 +256,77 @@ __global__ void __launch_bounds__(THREADS, 2) psum_kernel(const KParams P) {
       rho[j] = to_f2(tb->rho[j]);
       wl[j] = __ldg(&tb->f_pw_lane[31 - lane][j]);  // rho^{16 (31 - lane)}
     }
-    const float2 r512 = __ldg(&tb->f_pwt[0][jl]);
     const float* __restrict__ xs = reinterpret_cast<const float*>(P.x) + wi.x_off;
     const int64_t N = wi.n;
+    const int n_sub = wi.n_sub;
 
-    float2 G[PS_CHUNK];
-    float2 acc = make_float2(0.f, 0.f);  // aggregate of the chunk so far (term jl)
+    // tile sums G_k, kept by the owner lane of tile k for this lane's term
+    float2 Gm[TPL];
+#pragma unroll
+    for (int r = 0; r < TPL; ++r) Gm[r] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < PS_CHUNK; ++k) {
-      G[k] = make_float2(0.f, 0.f);
       const int64_t t0 = wi.t_a + (int64_t)k * PS_TILE;
-      if (k < wi.n_sub && t0 < N && t0 + PS_TILE > 0) {  // warp-uniform
+      if (k < n_sub && t0 < N && t0 + PS_TILE > 0) {  // warp-uniform
         float xa[ITEMS];
         load_run<float, ITEMS>(xs, t0 + (int64_t)lane * ITEMS, 0, N, xa);
         float2 b[K];
         lane_sums<K, ITEMS>(xa, rho, wl, b);
-        G[k] = warp_tile_sum<K>(b, lane);
+        const float2 g = warp_sum_scatter<K>(b, lane);
+        if (sl == k / TPL) Gm[k % TPL] = g;
       }
-      if (k < wi.n_sub) acc = cfma(r512, acc, G[k]);
     }
+    // in-chunk prefix at each tile end (FP32): owner-local over its tiles, then a scan over the
+    // owner slots of the term's lane group
+    auto f32 = [&](int mm) {  // rho^{512 (mm + 1)} of this lane's term, FP32
+      const float4 c = __ldg(&tb->c_pw_chunk[mm][tq]);
+      return make_float2(c.x, c.z);
+    };
+    float2 loc[TPL];
+    loc[0] = Gm[0];
+#pragma unroll
+    for (int r = 1; r < TPL; ++r) loc[r] = cfma(f32(0), loc[r - 1], Gm[r]);
+    float2 inc = loc[TPL - 1];
+#pragma unroll
+    for (int o = 1; o < OWN; o <<= 1) {
+      const float2 u = shfl_up2(inc, o);
+      if (sl >= o) inc = cfma(f32(TPL * o - 1), u, inc);
+    }
+    float2 e = shfl_up2(inc, 1);
+    if (sl == 0) e = make_float2(0.f, 0.f);
+    float2 pre[TPL];
+#pragma unroll
+    for (int r = 0; r < TPL; ++r) pre[r] = cfma(f32(r), e, loc[r]);
+    // chunk aggregate of term v into lane v, for the look-back
+    const int k_last = n_sub - 1;
+    float2 pl_last = pre[0];
+#pragma unroll
+    for (int r = 1; r < TPL; ++r)
+      if (k_last % TPL == r) pl_last = pre[r];
+    const int src = (lane < K ? lane : 0) * G + k_last / TPL;
+    const float2 acc = make_float2(__shfl_sync(0xffffffffu, pl_last.x, src), __shfl_sync(0xffffffffu, pl_last.y, src));
     const DFC carry = warp_lookback<K>(P, wi.slot, wi.slot_first, CarryOps<DFC>::from(acc), tb, lane);
     // inclusive state after a full chunk, published at once for the successors' look-back
-    if (wi.n_sub == PS_CHUNK) {
+    if (n_sub == PS_CHUNK) {
       if (lane < K) {
-        const DFC inc = dfc_add(dfc_mul(dfc_from_f4(__ldg(&tb->c_pw_tile[1][lane])), carry), CarryOps<DFC>::from(acc));
-        st_cg2(reinterpret_cast<DFC*>(P.incl) + wi.slot * K + lane, inc);
+        const DFC inc2 = dfc_add(dfc_mul(dfc_from_f4(__ldg(&tb->c_pw_tile[1][lane])), carry), CarryOps<DFC>::from(acc));
+        st_cg2(reinterpret_cast<DFC*>(P.incl) + wi.slot * K + lane, inc2);
         __threadfence();
       }
       __syncwarp();
       if (lane == 0) st_release(P.flags + wi.slot, ST_INCL);
     }
-    // P at the end of each tile of the chunk, in two-float
-    const DFC r = dfc_rho512(tb, jl);
-    DFC pp = carry;
+    // P at the end of each owned tile: rho^{512 (k + 1)} carry + in-chunk prefix, two-float
+    const DFC cy = CarryOps<DFC>::shfl_idx(carry, tq);
     DFC* pb = reinterpret_cast<DFC*>(P.pbuf) + wi.p_row * K;
+    if (owner) {
 #pragma unroll
-    for (int k = 0; k < PS_CHUNK; ++k) {
-      if (k < wi.n_sub) {
-        pp = dfc_add(dfc_mul(r, pp), CarryOps<DFC>::from(G[k]));
-        if (lane < K) st_cg2(pb + (int64_t)k * K + lane, pp);
+      for (int r = 0; r < TPL; ++r) {
+        const int k = sl * TPL + r;
+        if (k < n_sub) {
+          const DFC pk = dfc_add(dfc_mul(dfc_from_f4(__ldg(&tb->c_pw_chunk[k][tq])), cy), CarryOps<DFC>::from(pre[r]));
+          st_cg2(pb + (int64_t)k * K + tl, pk);
+        }
       }
     }
     if (lane == 0) w = (long long)atomicAdd(P.ticket, 1ull);

@@ -243,11 +243,15 @@ __global__ void build_tables(ScaleTab* tabs, const FitJob* jobs, int n_scales, i
     else tb.pw_tile[q - 47][j] = power(p, T * (q - 47));
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < K_kernel * 33; idx += blockDim.x) {
-    const double2 v = tb.pw_tile[idx / K_kernel][idx % K_kernel];
+  auto dfc4 = [](double2 v) {
     const float rh = (float)v.x, ih = (float)v.y;
-    tb.c_pw_tile[idx / K_kernel][idx % K_kernel] =
-        make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+    return make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+  };
+  for (int idx = threadIdx.x; idx < K_kernel * 33; idx += blockDim.x)
+    tb.c_pw_tile[idx / K_kernel][idx % K_kernel] = dfc4(tb.pw_tile[idx / K_kernel][idx % K_kernel]);
+  for (int idx = threadIdx.x; idx < K_kernel * 8; idx += blockDim.x) {
+    const int j = idx % K_kernel, mm = idx / K_kernel;
+    tb.c_pw_chunk[mm][j] = dfc4(power((long long)tb.p0 + j, (long long)items * 32 * (mm + 1)));
   }
   for (int idx = threadIdx.x; idx < K_kernel * (5 + 32 + 1); idx += blockDim.x) {
     const int j = idx % K_kernel;

@@ -29,12 +29,67 @@ template <> __device__ __forceinline__ double2 pwt<double2>(const ScaleTab* tb, 
   return h == 0 ? tb->pw_warp[j] : make_double2(0.0, 0.0);
 }
 
+// One position of the recursion V <- rho (V - kappa xl) + x, for every term of every channel, and
+// (OUT) the output combine. Returns the output of the position.
+template <class C, bool OUT>
+__device__ __forceinline__ typename C::V step(typename C::V (&S)[C::NT], const typename C::V (&rho)[C::K],
+                                              const typename C::R (&cM)[C::K], const typename C::R (&cL)[C::K],
+                                              typename C::R kap, const typename C::R (&xv)[C::CH],
+                                              const typename C::R (&xlv)[C::CH]) {
+  using R = typename C::R;
+  using V = typename C::V;
+  V o = V{};
+#pragma unroll
+  for (int c = 0; c < C::CH; ++c) {
+#pragma unroll
+    for (int j = 0; j < C::K; ++j) {
+      V& b = S[c * C::K + j];
+      const R tt = fma(-kap, xlv[c], b.x);
+      const R vr = fma(rho[j].x, tt, fma(-rho[j].y, b.y, xv[c]));
+      const R vi = fma(rho[j].y, tt, rho[j].x * b.y);
+      b.x = vr;
+      b.y = vi;
+      if constexpr (OUT) {
+        if constexpr (C::OUT == OUT_MORLET) {
+          o.x = fma(cM[j], vr, o.x);
+          o.y = fma(cL[j], vi, o.y);
+        } else if constexpr (C::OUT == OUT_REAL) {
+          o.x = fma(cM[j], vr, fma(cL[j], vi, o.x));
+        } else {
+          if (c == 0) o.x = fma(cM[j], vr, o.x);
+          else o.x = fma(cL[j], vi, o.x);
+        }
+      }
+    }
+  }
+  return o;
+}
+
+template <class C, typename EIn>
+__device__ __forceinline__ void split_in(const EIn& a, const EIn& l, typename C::R (&xv)[C::CH],
+                                         typename C::R (&xlv)[C::CH]) {
+  using R = typename C::R;
+  using V = typename C::V;
+  if constexpr (C::CH == 2) {
+    xv[0] = reinterpret_cast<const V&>(a).x;
+    xv[1] = reinterpret_cast<const V&>(a).y;
+    xlv[0] = reinterpret_cast<const V&>(l).x;
+    xlv[1] = reinterpret_cast<const V&>(l).y;
+  } else {
+    xv[0] = reinterpret_cast<const R&>(a);
+    xlv[0] = reinterpret_cast<const R&>(l);
+  }
+}
+
 template <class C>
 __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P) {
   using R = typename C::R;
   using V = typename C::V;
   constexpr int K = C::K, NT = C::NT, CH = C::CH, ITEMS = C::ITEMS;
   constexpr int WT = 32 * ITEMS;  // positions per warp-tile
+  // |rho| = 1 (SFT): the warp scan runs in the frame of the tile start, where combining two lanes is
+  // a plain sum; the damped ASFT keeps the multiplicative scan (rho^{-n} would amplify).
+  constexpr bool ABS = !C::ASFT;
   using EIn = typename std::conditional<CH == 2, V, R>::type;
   const int lane = threadIdx.x & 31;
 
@@ -50,13 +105,18 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
     const ScaleTab* tb = P.tabs + wi.scale;
     const int64_t L = tb->L, D = tb->D, Wl = 2 * L + 1;
     const R kap = (R)tb->kappa;
-    V rho[K];
+    V rho[K], pn[ABS ? K : 1];
     R cM[K], cL[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
       rho[j] = conv2<V>(tb->rho[j]);
       cM[j] = (R)tb->cM[j];
       cL[j] = (C::OUT == OUT_ADJ) ? (R)(-tb->cL[j]) : (R)tb->cL[j];
+      if constexpr (ABS) {  // conj(rho^{ITEMS (lane + 1)}) = rho^{-ITEMS (lane + 1)}
+        const V q = cmul(pw_lane<V>(tb, lane, j), pw_thr<V>(tb, 0, j));
+        pn[j].x = q.x;
+        pn[j].y = -q.y;
+      }
     }
     const V E = conv2<V>(tb->E);
     const EIn* __restrict__ xs = reinterpret_cast<const EIn*>(P.x) + wi.x_off;
@@ -83,96 +143,101 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) xa[i] = xl[i] = EIn{};
       }
-      // pass 1
+      // pass 1: the lane's aggregate from a zero state
       V B[NT];
 #pragma unroll
       for (int v = 0; v < NT; ++v) B[v] = V{};
       if (live) {
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
+          R xv[CH], xlv[CH];
+          split_in<C>(xa[i], xl[i], xv, xlv);
+          step<C, false>(B, rho, cM, cL, kap, xv, xlv);
+        }
+      }
+      // warp scan -> S: state before the lane's first position; Cw advances by one warp-tile
+      V S[NT];
+      if constexpr (ABS) {
+        // B'_l = rho^{-ITEMS (l+1)} B_l; the state before lane l is rho^{ITEMS l} (Cw + sum_{l'<l} B'_l')
+        // and the state after the tile rho^{WT} (Cw + sum_l B'_l).
 #pragma unroll
-          for (int c = 0; c < CH; ++c) {
-            R xv, xlv;
-            if constexpr (CH == 2) {
-              xv = c ? reinterpret_cast<const V&>(xa[i]).y : reinterpret_cast<const V&>(xa[i]).x;
-              xlv = c ? reinterpret_cast<const V&>(xl[i]).y : reinterpret_cast<const V&>(xl[i]).x;
-            } else {
-              xv = reinterpret_cast<const R&>(xa[i]);
-              xlv = reinterpret_cast<const R&>(xl[i]);
-            }
+        for (int v = 0; v < NT; ++v) B[v] = cmul(pn[v % K], B[v]);
 #pragma unroll
-            for (int j = 0; j < K; ++j) {
-              V& b = B[c * K + j];
-              const R tt = fma(-kap, xlv, b.x);
-              const R vr = fma(rho[j].x, tt, fma(-rho[j].y, b.y, xv));
-              const R vi = fma(rho[j].y, tt, rho[j].x * b.y);
-              b.x = vr;
-              b.y = vi;
+        for (int l = 0; l < 5; ++l) {
+          const int o = 1 << l;
+#pragma unroll
+          for (int v = 0; v < NT; ++v) {
+            const V u = shfl_up2(B[v], o);
+            if (lane >= o) {
+              B[v].x += u.x;
+              B[v].y += u.y;
             }
           }
         }
-      }
-      // warp scan
-#pragma unroll
-      for (int l = 0; l < 5; ++l) {
-        const int o = 1 << l;
 #pragma unroll
         for (int v = 0; v < NT; ++v) {
-          const V u = shfl_up2(B[v], o);
-          if (lane >= o) B[v] = cfma(pw_thr<V>(tb, l, v % K), u, B[v]);
+          const V tot = cmake<R>(__shfl_sync(0xffffffffu, B[v].x, 31), __shfl_sync(0xffffffffu, B[v].y, 31));
+          V e = shfl_up2(B[v], 1);
+          if (lane == 0) e = V{};
+          S[v] = cmul(pw_lane<V>(tb, lane, v % K), cmake<R>(Cw[v].x + e.x, Cw[v].y + e.y));
+          // rho^{WT} = hi + lo (two floats) so that repeated steps do not drift
+          const V c = cmake<R>(Cw[v].x + tot.x, Cw[v].y + tot.y);
+          Cw[v] = cfma(pwt<V>(tb, 0, v % K), c, cmul(pwt<V>(tb, 1, v % K), c));
+        }
+      } else {
+#pragma unroll
+        for (int l = 0; l < 5; ++l) {
+          const int o = 1 << l;
+#pragma unroll
+          for (int v = 0; v < NT; ++v) {
+            const V u = shfl_up2(B[v], o);
+            if (lane >= o) B[v] = cfma(pw_thr<V>(tb, l, v % K), u, B[v]);
+          }
+        }
+#pragma unroll
+        for (int v = 0; v < NT; ++v) {
+          const V tot = cmake<R>(__shfl_sync(0xffffffffu, B[v].x, 31), __shfl_sync(0xffffffffu, B[v].y, 31));
+          V e = shfl_up2(B[v], 1);
+          if (lane == 0) e = V{};
+          S[v] = cfma(pw_lane<V>(tb, lane, v % K), Cw[v], e);
+          V c = cfma(pwt<V>(tb, 0, v % K), Cw[v], tot);
+          Cw[v] = cfma(pwt<V>(tb, 1, v % K), Cw[v], c);
         }
       }
-      V S[NT];
-#pragma unroll
-      for (int v = 0; v < NT; ++v) {
-        const V tot = cmake<R>(__shfl_sync(0xffffffffu, B[v].x, 31), __shfl_sync(0xffffffffu, B[v].y, 31));
-        V e = shfl_up2(B[v], 1);
-        if (lane == 0) e = V{};
-        S[v] = cfma(pw_lane<V>(tb, lane, v % K), Cw[v], e);  // state before this lane's first position
-        // carry into the next warp-tile: rho^{WT} C + total, with rho^{WT} = hi + lo
-        V c = cfma(pwt<V>(tb, 0, v % K), Cw[v], tot);
-        Cw[v] = cfma(pwt<V>(tb, 1, v % K), Cw[v], c);
-      }
-      // pass 2
+      // pass 2: outputs for positions in [t_out, t_end)
       if (tf >= t_end || tf + ITEMS <= t_out) continue;
       const int64_t oo = wi.out_off - D + tf;
       const bool all_in = (tf >= t_out) && (tf + ITEMS <= t_end);
-      V prev{};
+      bool fast = false;
+      if constexpr (C::OUT == OUT_MORLET && sizeof(R) == 4)
+        fast = all_in && ((reinterpret_cast<uintptr_t>(reinterpret_cast<V*>(P.out) + oo) & 15) == 0);
+      if (fast) {
+        // every position stored: pairs of outputs as 16-byte streaming stores
+        float4* op = reinterpret_cast<float4*>(reinterpret_cast<V*>(P.out) + oo);
 #pragma unroll
-      for (int i = 0; i < ITEMS; ++i) {
-        V o = V{};
-#pragma unroll
-        for (int c = 0; c < CH; ++c) {
-          R xv, xlv;
-          if constexpr (CH == 2) {
-            xv = c ? reinterpret_cast<const V&>(xa[i]).y : reinterpret_cast<const V&>(xa[i]).x;
-            xlv = c ? reinterpret_cast<const V&>(xl[i]).y : reinterpret_cast<const V&>(xl[i]).x;
-          } else {
-            xv = reinterpret_cast<const R&>(xa[i]);
-            xlv = reinterpret_cast<const R&>(xl[i]);
+        for (int i = 0; i < ITEMS; i += 2) {
+          R xv[CH], xlv[CH];
+          split_in<C>(xa[i], xl[i], xv, xlv);
+          V o0 = step<C, true>(S, rho, cM, cL, kap, xv, xlv);
+          split_in<C>(xa[i + 1], xl[i + 1], xv, xlv);
+          V o1 = step<C, true>(S, rho, cM, cL, kap, xv, xlv);
+          if constexpr (C::ASFT) {
+            o0 = cmul(o0, E);
+            o1 = cmul(o1, E);
           }
-#pragma unroll
-          for (int j = 0; j < K; ++j) {
-            V& b = S[c * K + j];
-            const R tt = fma(-kap, xlv, b.x);
-            const R vr = fma(rho[j].x, tt, fma(-rho[j].y, b.y, xv));
-            const R vi = fma(rho[j].y, tt, rho[j].x * b.y);
-            b.x = vr;
-            b.y = vi;
-            if constexpr (C::OUT == OUT_MORLET) {
-              o.x = fma(cM[j], vr, o.x);
-              o.y = fma(cL[j], vi, o.y);
-            } else if constexpr (C::OUT == OUT_REAL) {
-              o.x = fma(cM[j], vr, fma(cL[j], vi, o.x));
-            } else {
-              if (c == 0) o.x = fma(cM[j], vr, o.x);
-              else o.x = fma(cL[j], vi, o.x);
-            }
-          }
+          __stcs(op + i / 2, make_float4((float)o0.x, (float)o0.y, (float)o1.x, (float)o1.y));
         }
-        if constexpr (C::ASFT) o = cmul(o, E);
-        store_item<C>(P, oo, i, o, prev, all_in, tf + i >= t_out && tf + i < t_end);
-        prev = o;
+      } else {
+        V prev{};
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+          R xv[CH], xlv[CH];
+          split_in<C>(xa[i], xl[i], xv, xlv);
+          V o = step<C, true>(S, rho, cM, cL, kap, xv, xlv);
+          if constexpr (C::ASFT) o = cmul(o, E);
+          store_item<C>(P, oo, i, o, prev, false, tf + i >= t_out && tf + i < t_end);
+          prev = o;
+        }
       }
     }
     w = __shfl_sync(0xffffffffu, nxt, 0);
