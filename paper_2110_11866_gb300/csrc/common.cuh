@@ -85,6 +85,8 @@ struct ScaleTab {
   float2 f_pwt[2][KMAX];      // rho^{items * 32} as hi + lo
   float4 c_pw_tile[33][KMAX]; // pw_tile as two-float complex (re.hi, re.lo, im.hi, im.lo)
   float4 c_pw_chunk[8][KMAX]; // rho^{32 items (m + 1)}, m = 0..7, two-float complex
+  float f_lam[KMAX];          // 4 sin^2(beta p / 2) = |1 - rho|^2 for |rho| = 1 (Reinsch's recurrence)
+  double d_lam[KMAX];         // the same in FP64
 };
 
 struct KParams {

@@ -105,24 +105,31 @@ __device__ __forceinline__ DFC warp_lookback(const KParams& P, int64_t slot, int
   return carry;
 }
 
-// Horner sum of 16 samples with the lane's weight: returns sum_i rho^{15 - i} x_i times w.
+// Sum of 16 samples with the lane's weight: returns w sum_i rho^{15 - i} x_i for rho = e^{-i theta}.
+// The sum runs as the real second-order recurrence s_i = x_i + 2 cos(theta) s_{i-1} - s_{i-2} in
+// Reinsch's form, which stays accurate for small theta: with lam = 4 sin^2(theta / 2),
+//     d_i = d_{i-1} + x_i - lam s_{i-1},  s_i = s_{i-1} + d_i,
+// and at the end sum_i rho^{15-i} x_i = (d_15 + (lam / 2) s_14) - i sin(theta) s_14 with
+// s_14 = s_15 - d_15. Three operations per sample and term instead of a complex rotation's five.
 template <int K, int ITEMS>
-__device__ __forceinline__ void lane_sums(const float (&xa)[ITEMS], const float2 (&rho)[K], const float2 (&w)[K],
-                                          float2 (&b)[K]) {
+__device__ __forceinline__ void lane_sums(const float (&xa)[ITEMS], const float2 (&rho)[K], const float (&lam)[K],
+                                          const float2 (&w)[K], float2 (&b)[K]) {
+  float s[K], d[K];
 #pragma unroll
-  for (int j = 0; j < K; ++j) b[j] = make_float2(0.f, 0.f);
+  for (int j = 0; j < K; ++j) s[j] = d[j] = 0.f;
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-      const float vr = fmaf(rho[j].x, b[j].x, fmaf(-rho[j].y, b[j].y, xa[i]));
-      const float vi = fmaf(rho[j].y, b[j].x, rho[j].x * b[j].y);
-      b[j].x = vr;
-      b[j].y = vi;
+      d[j] = fmaf(-lam[j], s[j], d[j] + xa[i]);
+      s[j] += d[j];
     }
   }
 #pragma unroll
-  for (int j = 0; j < K; ++j) b[j] = cmul(b[j], w[j]);
+  for (int j = 0; j < K; ++j) {
+    const float s14 = s[j] - d[j];
+    b[j] = cmul(make_float2(fmaf(0.5f * lam[j], s14, d[j]), rho[j].y * s14), w[j]);
+  }
 }
 
 // Sum over the warp of each b[j] (all lanes receive the sums); returns the sum of term `lane`
@@ -184,12 +191,13 @@ __device__ __forceinline__ float2 warp_sum_scatter(const float2 (&b)[K], int lan
 }
 
 // State entering a start-state work item of the warp kernel, returned in Cw[j] (uniform across the
-// warp, FP32). With b = wi.t_a a tile start and q = b - 2L - 2:
-//     V(b - 1) = P(b - 1) - kappa rho P(q),
+// warp, FP32). The warp kernel runs the SFT in its G form, G(t) = sum_{u = t-2L+1}^{t} rho^{t-u} x[u]
+// = P(t) - rho^{2L} P(t - 2L) = P(t) - P(t - 2L). With b = wi.t_a a tile start and q = b - 1 - 2L:
+//     G(b - 1) = P(b - 1) - P(q),
 //     P(q)     = rho^{-(e - q)} (rho^{512} P(e - 512) + sum_{u = e-511}^{q} rho^{e-u} x[u])
 // for the tile [e - 511, e] holding q; P at tile ends comes from the prefix sums, the partial tile
-// sum from the samples. kappa rho rho^{-(e-q)} = rho^{1-(e-q)} is formed in FP64 from the exact
-// integer angle (p (e - q - 1)) mod 2L (SFT: |rho| = 1 and kappa = 1).
+// sum from the samples. rho^{-(e-q)} is formed in FP64 from the exact integer angle
+// (p (e - q)) mod 2L (|rho| = 1).
 template <int K, int ITEMS>
 __device__ __forceinline__ void start_state(const KParams& P, const WorkItem& wi, const ScaleTab* tb,
                                             const float2 (&rho)[K], int lane, float2 (&Cw)[K]) {
@@ -200,7 +208,7 @@ __device__ __forceinline__ void start_state(const KParams& P, const WorkItem& wi
   const int64_t kb = (wi.t_a - wi.t_grid) / PS_TILE;
   DFC v = CO::zero();
   if (kb >= 1) v = dfc_from_f4(__ldg(reinterpret_cast<const float4*>(pb + (kb - 1) * K + jl)));
-  const int64_t q = wi.t_a - 2 * L - 2;
+  const int64_t q = wi.t_a - 1 - 2 * L;
   if (q >= 0) {  // warp-uniform
     const int64_t k0 = (q - wi.t_grid) / PS_TILE;
     const int64_t a0 = wi.t_grid + k0 * PS_TILE;
@@ -209,15 +217,18 @@ __device__ __forceinline__ void start_state(const KParams& P, const WorkItem& wi
     float xa[ITEMS];
     load_run<float, ITEMS>(xs, a0 + (int64_t)lane * ITEMS, 0, wi.n < q + 1 ? wi.n : q + 1, xa);
     float2 wl[K], b[K];
+    float lam[K];
 #pragma unroll
-    for (int j = 0; j < K; ++j) wl[j] = __ldg(&tb->f_pw_lane[31 - lane][j]);
-    lane_sums<K, ITEMS>(xa, rho, wl, b);
+    for (int j = 0; j < K; ++j) {
+      wl[j] = __ldg(&tb->f_pw_lane[31 - lane][j]);
+      lam[j] = __ldg(&tb->f_lam[j]);
+    }
+    lane_sums<K, ITEMS>(xa, rho, lam, wl, b);
     DFC pt = CO::from(warp_tile_sum<K>(b, lane));
     if (k0 >= 1)
       pt = dfc_add(dfc_mul(dfc_rho512(tb, jl), dfc_from_f4(__ldg(reinterpret_cast<const float4*>(pb + (k0 - 1) * K + jl)))), pt);
     const long long pj = (long long)tb->p0 + jl, M = 2 * L;
-    long long r = (pj * (long long)(m - 1)) % M;
-    if (r < 0) r += M;
+    const long long r = (pj * (long long)m) % M;
     double sn, cs;
     sincospi((double)r / (double)L, &sn, &cs);
     v = dfc_add(v, dfc_neg(dfc_mul(dfc_from_d2(make_double2(cs, sn)), pt)));
@@ -251,10 +262,12 @@ __global__ void __launch_bounds__(THREADS, C::K <= 6 ? 3 : 2) psum_kernel(const 
     const WorkItem wi = P.work[w];
     const ScaleTab* tb = P.tabs + wi.scale;
     float2 rho[K], wl[K];
+    float lam[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
       rho[j] = to_f2(tb->rho[j]);
       wl[j] = __ldg(&tb->f_pw_lane[31 - lane][j]);  // rho^{16 (31 - lane)}
+      lam[j] = __ldg(&tb->f_lam[j]);
     }
     const float* __restrict__ xs = reinterpret_cast<const float*>(P.x) + wi.x_off;
     const int64_t N = wi.n;
@@ -271,7 +284,7 @@ __global__ void __launch_bounds__(THREADS, C::K <= 6 ? 3 : 2) psum_kernel(const 
         float xa[ITEMS];
         load_run<float, ITEMS>(xs, t0 + (int64_t)lane * ITEMS, 0, N, xa);
         float2 b[K];
-        lane_sums<K, ITEMS>(xa, rho, wl, b);
+        lane_sums<K, ITEMS>(xa, rho, lam, wl, b);
         const float2 g = warp_sum_scatter<K>(b, lane);
         if (sl == k / TPL) Gm[k % TPL] = g;
       }

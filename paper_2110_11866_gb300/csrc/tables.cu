@@ -249,6 +249,11 @@ __global__ void build_tables(ScaleTab* tabs, const FitJob* jobs, int n_scales, i
   };
   for (int idx = threadIdx.x; idx < K_kernel * 33; idx += blockDim.x)
     tb.c_pw_tile[idx / K_kernel][idx % K_kernel] = dfc4(tb.pw_tile[idx / K_kernel][idx % K_kernel]);
+  for (int j = threadIdx.x; j < KMAX; j += blockDim.x) {
+    const double sh = sinpi((double)(tb.p0 + j) / (double)(2 * L));  // sin(beta p / 2)
+    tb.d_lam[j] = j < K_kernel ? 4.0 * sh * sh : 0.0;
+    tb.f_lam[j] = (float)tb.d_lam[j];
+  }
   for (int idx = threadIdx.x; idx < K_kernel * 8; idx += blockDim.x) {
     const int j = idx % K_kernel, mm = idx / K_kernel;
     tb.c_pw_chunk[mm][j] = dfc4(power((long long)tb.p0 + j, (long long)items * 32 * (mm + 1)));

@@ -30,7 +30,7 @@ template <> __device__ __forceinline__ double2 pwt<double2>(const ScaleTab* tb, 
 }
 
 // One position of the recursion V <- rho (V - kappa xl) + x, for every term of every channel, and
-// (OUT) the output combine. Returns the output of the position.
+// (OUT) the output combine. Returns the output of the position. (ASFT form.)
 template <class C, bool OUT>
 __device__ __forceinline__ typename C::V step(typename C::V (&S)[C::NT], const typename C::V (&rho)[C::K],
                                               const typename C::R (&cM)[C::K], const typename C::R (&cL)[C::K],
@@ -65,6 +65,43 @@ __device__ __forceinline__ typename C::V step(typename C::V (&S)[C::NT], const t
   return o;
 }
 
+// SFT form. With rho^{2L} = 1 the window state splits as V(t) = G(t) + x[t - 2L], where G, the sum
+// over the 2L samples x[t-2L+1 .. t], obeys G <- rho G + d with the real input d = x[t] - x[t - 2L]
+// shared by all terms. One position of that recursion and (OUT) the combine of V; cx = sum_j cM_j
+// carries the x[t - 2L] part of Re V (channel 0).
+template <class C, bool OUT>
+__device__ __forceinline__ typename C::V step_g(typename C::V (&S)[C::NT], const typename C::V (&rho)[C::K],
+                                                const typename C::R (&cM)[C::K], const typename C::R (&cL)[C::K],
+                                                typename C::R cx, const typename C::R (&d)[C::CH], typename C::R xg0) {
+  using R = typename C::R;
+  using V = typename C::V;
+  V o = V{};
+#pragma unroll
+  for (int c = 0; c < C::CH; ++c) {
+#pragma unroll
+    for (int j = 0; j < C::K; ++j) {
+      V& b = S[c * C::K + j];
+      const R vr = fma(rho[j].x, b.x, fma(-rho[j].y, b.y, d[c]));
+      const R vi = fma(rho[j].y, b.x, rho[j].x * b.y);
+      b.x = vr;
+      b.y = vi;
+      if constexpr (OUT) {
+        if constexpr (C::OUT == OUT_MORLET) {
+          o.x = fma(cM[j], vr, o.x);
+          o.y = fma(cL[j], vi, o.y);
+        } else if constexpr (C::OUT == OUT_REAL) {
+          o.x = fma(cM[j], vr, fma(cL[j], vi, o.x));
+        } else {
+          if (c == 0) o.x = fma(cM[j], vr, o.x);
+          else o.x = fma(cL[j], vi, o.x);
+        }
+      }
+    }
+  }
+  if constexpr (OUT) o.x = fma(cx, xg0, o.x);
+  return o;
+}
+
 template <class C, typename EIn>
 __device__ __forceinline__ void split_in(const EIn& a, const EIn& l, typename C::R (&xv)[C::CH],
                                          typename C::R (&xlv)[C::CH]) {
@@ -87,32 +124,44 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
   using V = typename C::V;
   constexpr int K = C::K, NT = C::NT, CH = C::CH, ITEMS = C::ITEMS;
   constexpr int WT = 32 * ITEMS;  // positions per warp-tile
-  // |rho| = 1 (SFT): the warp scan runs in the frame of the tile start, where combining two lanes is
-  // a plain sum; the damped ASFT keeps the multiplicative scan (rho^{-n} would amplify).
-  constexpr bool ABS = !C::ASFT;
+  // SFT (|rho| = 1, rho^{2L} = 1): the G form above, and a warp scan in the frame of the tile start,
+  // where combining two lanes is a plain sum. The damped ASFT keeps the V recursion and the
+  // multiplicative scan (rho^{-n} would amplify).
+  constexpr bool GF = !C::ASFT;
   using EIn = typename std::conditional<CH == 2, V, R>::type;
   const int lane = threadIdx.x & 31;
 
-  long long w = 0;
-  if (lane == 0) w = (long long)atomicAdd(P.ticket, 1ull);
+  // Work items are claimed two ahead, and the record of the next one is prefetched into L1 while the
+  // current one runs, so an item starts without waiting on the work counter. Items are independent,
+  // so holding them is harmless.
+  long long w = 0, w1 = 0;
+  if (lane == 0) {
+    w = (long long)atomicAdd(P.ticket, 1ull);
+    w1 = (long long)atomicAdd(P.ticket, 1ull);
+  }
   w = __shfl_sync(0xffffffffu, w, 0);
+  w1 = __shfl_sync(0xffffffffu, w1, 0);
   while (w < P.n_work) {
     const WorkItem wi = P.work[w];
-    // claim the next segment now; segments are independent, so holding it is harmless
-    long long nxt = 0;
-    if (lane == 0) nxt = (long long)atomicAdd(P.ticket, 1ull);
+    long long w2 = 0;
+    if (lane == 0) w2 = (long long)atomicAdd(P.ticket, 1ull);
+    if (w1 < P.n_work && lane < (int)(sizeof(WorkItem) + 127) / 128)
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<const char*>(P.work + w1) + 128 * lane));
 
     const ScaleTab* tb = P.tabs + wi.scale;
-    const int64_t L = tb->L, D = tb->D, Wl = 2 * L + 1;
+    const int64_t L = tb->L, D = tb->D;
+    const int64_t Wl = GF ? 2 * L : 2 * L + 1;  // lag of the second input stream
     const R kap = (R)tb->kappa;
-    V rho[K], pn[ABS ? K : 1];
+    V rho[K], pn[GF ? K : 1];
     R cM[K], cL[K];
+    R cx = 0;
 #pragma unroll
     for (int j = 0; j < K; ++j) {
       rho[j] = conv2<V>(tb->rho[j]);
       cM[j] = (R)tb->cM[j];
       cL[j] = (C::OUT == OUT_ADJ) ? (R)(-tb->cL[j]) : (R)tb->cL[j];
-      if constexpr (ABS) {  // conj(rho^{ITEMS (lane + 1)}) = rho^{-ITEMS (lane + 1)}
+      cx += cM[j];
+      if constexpr (GF) {  // conj(rho^{ITEMS (lane + 1)}) = rho^{-ITEMS (lane + 1)}
         const V q = cmul(pw_lane<V>(tb, lane, j), pw_thr<V>(tb, 0, j));
         pn[j].x = q.x;
         pn[j].y = -q.y;
@@ -148,16 +197,52 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
 #pragma unroll
       for (int v = 0; v < NT; ++v) B[v] = V{};
       if (live) {
+        if constexpr (GF) {
+          // 16 steps of G <- rho G + d from zero as the real second-order recurrence in Reinsch's
+          // form (rho = e^{-i theta}, lam = 4 sin^2(theta / 2)):
+          //     e_i = e_{i-1} + d_i - lam s_{i-1},  s_i = s_{i-1} + e_i,
+          // then G = (e_15 + (lam / 2) s_14) - i sin(theta) s_14 with s_14 = s_15 - e_15.
+          R sv[NT], ev[NT], lam[K];
 #pragma unroll
-        for (int i = 0; i < ITEMS; ++i) {
-          R xv[CH], xlv[CH];
-          split_in<C>(xa[i], xl[i], xv, xlv);
-          step<C, false>(B, rho, cM, cL, kap, xv, xlv);
+          for (int j = 0; j < K; ++j) {
+            if constexpr (sizeof(R) == 4) lam[j] = __ldg(&tb->f_lam[j]);
+            else lam[j] = tb->d_lam[j];
+          }
+#pragma unroll
+          for (int v = 0; v < NT; ++v) sv[v] = ev[v] = R(0);
+#pragma unroll
+          for (int i = 0; i < ITEMS; ++i) {
+            R xv[CH], xgv[CH];
+            split_in<C>(xa[i], xl[i], xv, xgv);
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+              const R dd = xv[c] - xgv[c];
+#pragma unroll
+              for (int j = 0; j < K; ++j) {
+                const int v = c * K + j;
+                ev[v] = fma(-lam[j], sv[v], ev[v] + dd);
+                sv[v] += ev[v];
+              }
+            }
+          }
+#pragma unroll
+          for (int v = 0; v < NT; ++v) {
+            const R s14 = sv[v] - ev[v];
+            B[v].x = fma(R(0.5) * lam[v % K], s14, ev[v]);
+            B[v].y = rho[v % K].y * s14;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < ITEMS; ++i) {
+            R xv[CH], xlv[CH];
+            split_in<C>(xa[i], xl[i], xv, xlv);
+            step<C, false>(B, rho, cM, cL, kap, xv, xlv);
+          }
         }
       }
       // warp scan -> S: state before the lane's first position; Cw advances by one warp-tile
       V S[NT];
-      if constexpr (ABS) {
+      if constexpr (GF) {
         // B'_l = rho^{-ITEMS (l+1)} B_l; the state before lane l is rho^{ITEMS l} (Cw + sum_{l'<l} B'_l')
         // and the state after the tile rho^{WT} (Cw + sum_l B'_l).
 #pragma unroll
@@ -211,36 +296,42 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
       bool fast = false;
       if constexpr (C::OUT == OUT_MORLET && sizeof(R) == 4)
         fast = all_in && ((reinterpret_cast<uintptr_t>(reinterpret_cast<V*>(P.out) + oo) & 15) == 0);
+      auto one = [&](int i) -> V {
+        R xv[CH], xlv[CH];
+        split_in<C>(xa[i], xl[i], xv, xlv);
+        V o;
+        if constexpr (GF) {
+          R dd[CH];
+#pragma unroll
+          for (int c = 0; c < CH; ++c) dd[c] = xv[c] - xlv[c];
+          o = step_g<C, true>(S, rho, cM, cL, cx, dd, xlv[0]);
+        } else {
+          o = step<C, true>(S, rho, cM, cL, kap, xv, xlv);
+        }
+        if constexpr (C::ASFT) o = cmul(o, E);
+        return o;
+      };
       if (fast) {
         // every position stored: pairs of outputs as 16-byte streaming stores
         float4* op = reinterpret_cast<float4*>(reinterpret_cast<V*>(P.out) + oo);
 #pragma unroll
         for (int i = 0; i < ITEMS; i += 2) {
-          R xv[CH], xlv[CH];
-          split_in<C>(xa[i], xl[i], xv, xlv);
-          V o0 = step<C, true>(S, rho, cM, cL, kap, xv, xlv);
-          split_in<C>(xa[i + 1], xl[i + 1], xv, xlv);
-          V o1 = step<C, true>(S, rho, cM, cL, kap, xv, xlv);
-          if constexpr (C::ASFT) {
-            o0 = cmul(o0, E);
-            o1 = cmul(o1, E);
-          }
+          const V o0 = one(i);
+          const V o1 = one(i + 1);
           __stcs(op + i / 2, make_float4((float)o0.x, (float)o0.y, (float)o1.x, (float)o1.y));
         }
       } else {
         V prev{};
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
-          R xv[CH], xlv[CH];
-          split_in<C>(xa[i], xl[i], xv, xlv);
-          V o = step<C, true>(S, rho, cM, cL, kap, xv, xlv);
-          if constexpr (C::ASFT) o = cmul(o, E);
+          const V o = one(i);
           store_item<C>(P, oo, i, o, prev, false, tf + i >= t_out && tf + i < t_end);
           prev = o;
         }
       }
     }
-    w = __shfl_sync(0xffffffffu, nxt, 0);
+    w = w1;
+    w1 = __shfl_sync(0xffffffffu, w2, 0);
   }
 }
 
