@@ -87,6 +87,8 @@ struct ScaleTab {
   float4 c_pw_chunk[8][KMAX]; // rho^{32 items (m + 1)}, m = 0..7, two-float complex
   float f_lam[KMAX];          // 4 sin^2(beta p / 2) = |1 - rho|^2 for |rho| = 1 (Reinsch's recurrence)
   double d_lam[KMAX];         // the same in FP64
+  float4 c_neg16[32][KMAX];   // rho^{-16 a}, a = 0..31, two-float complex (|rho| = 1)
+  float4 c_neg1[16][KMAX];    // rho^{-b}, b = 0..15, two-float complex
 };
 
 struct KParams {

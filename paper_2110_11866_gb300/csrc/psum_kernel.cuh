@@ -196,8 +196,8 @@ __device__ __forceinline__ float2 warp_sum_scatter(const float2 (&b)[K], int lan
 //     G(b - 1) = P(b - 1) - P(q),
 //     P(q)     = rho^{-(e - q)} (rho^{512} P(e - 512) + sum_{u = e-511}^{q} rho^{e-u} x[u])
 // for the tile [e - 511, e] holding q; P at tile ends comes from the prefix sums, the partial tile
-// sum from the samples. rho^{-(e-q)} is formed in FP64 from the exact integer angle
-// (p (e - q)) mod 2L (|rho| = 1).
+// sum from the samples. rho^{-(e-q)} = rho^{-16 a} rho^{-b} (e - q = 16 a + b) comes from two
+// two-float tables, each entry rounded once from FP64 at the exact integer angle (|rho| = 1).
 template <int K, int ITEMS>
 __device__ __forceinline__ void start_state(const KParams& P, const WorkItem& wi, const ScaleTab* tb,
                                             const float2 (&rho)[K], int lane, float2 (&Cw)[K]) {
@@ -227,11 +227,8 @@ __device__ __forceinline__ void start_state(const KParams& P, const WorkItem& wi
     DFC pt = CO::from(warp_tile_sum<K>(b, lane));
     if (k0 >= 1)
       pt = dfc_add(dfc_mul(dfc_rho512(tb, jl), dfc_from_f4(__ldg(reinterpret_cast<const float4*>(pb + (k0 - 1) * K + jl)))), pt);
-    const long long pj = (long long)tb->p0 + jl, M = 2 * L;
-    const long long r = (pj * (long long)m) % M;
-    double sn, cs;
-    sincospi((double)r / (double)L, &sn, &cs);
-    v = dfc_add(v, dfc_neg(dfc_mul(dfc_from_d2(make_double2(cs, sn)), pt)));
+    const DFC wm = dfc_mul(dfc_from_f4(__ldg(&tb->c_neg16[m >> 4][jl])), dfc_from_f4(__ldg(&tb->c_neg1[m & 15][jl])));
+    v = dfc_add(v, dfc_neg(dfc_mul(wm, pt)));
   }
   const float2 vn = CO::narrow(v);
 #pragma unroll
@@ -278,6 +275,7 @@ __global__ void __launch_bounds__(THREADS, C::K <= 6 ? 3 : 2) psum_kernel(const 
 #pragma unroll
     for (int r = 0; r < TPL; ++r) Gm[r] = make_float2(0.f, 0.f);
 #pragma unroll
+    if (lane == 0) prefetch_l2(xs, N, wi.t_a, wi.t_a + (int64_t)n_sub * PS_TILE);  // the chunk, into L2
     for (int k = 0; k < PS_CHUNK; ++k) {
       const int64_t t0 = wi.t_a + (int64_t)k * PS_TILE;
       if (k < n_sub && t0 < N && t0 + PS_TILE > 0) {  // warp-uniform

@@ -158,6 +158,19 @@ __device__ __forceinline__ void load_run(const E* __restrict__ p, int64_t t, int
   }
 }
 
+// Hint: bring elements [a, b) of the n-element buffer at base into L2 with one bulk prefetch (the
+// range is shrunk to whole 16-byte granules inside the buffer; nothing is read into registers).
+template <typename E>
+__device__ __forceinline__ void prefetch_l2(const E* base, int64_t n, int64_t a, int64_t b) {
+  if (a < 0) a = 0;
+  if (b > n) b = n;
+  if (a >= b) return;
+  const uintptr_t lo = (reinterpret_cast<uintptr_t>(base + a) + 15) & ~uintptr_t(15);
+  const uintptr_t hi = reinterpret_cast<uintptr_t>(base + b) & ~uintptr_t(15);
+  if (hi <= lo) return;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((unsigned)(hi - lo)) : "memory");
+}
+
 // Output of item i (position tf + i) at element oo + i. In the common case (all ITEMS positions of
 // the lane inside the stored range, 16-byte aligned complex64 output) pairs of items go out as one
 // 16-byte streaming store; otherwise each item is checked and stored alone.

@@ -249,6 +249,12 @@ __global__ void build_tables(ScaleTab* tabs, const FitJob* jobs, int n_scales, i
   };
   for (int idx = threadIdx.x; idx < K_kernel * 33; idx += blockDim.x)
     tb.c_pw_tile[idx / K_kernel][idx % K_kernel] = dfc4(tb.pw_tile[idx / K_kernel][idx % K_kernel]);
+  for (int idx = threadIdx.x; idx < K_kernel * 48; idx += blockDim.x) {  // e^{+i beta p n} = rho^{-n}
+    const int j = idx % K_kernel, q = idx / K_kernel;
+    const long long p = (long long)tb.p0 + j;
+    if (q < 32) tb.c_neg16[q][j] = dfc4(harmonic(p, 16LL * q, L));
+    else tb.c_neg1[q - 32][j] = dfc4(harmonic(p, (long long)(q - 32), L));
+  }
   for (int j = threadIdx.x; j < KMAX; j += blockDim.x) {
     const double sh = sinpi((double)(tb.p0 + j) / (double)(2 * L));  // sin(beta p / 2)
     tb.d_lam[j] = j < K_kernel ? 4.0 * sh * sh : 0.0;
