@@ -2,9 +2,9 @@
 
 Workload (default): the batched scalogram -- 256 float32 signals with lengths log-uniform in
 [1024, 1048576] (seed 2), 32 scales sigma = 2^(3 + j/3), omega0 = 6/sigma, K = 4, compensated FP32
-(FP32 scan, FP64 carries), complex64 outputs, one graph-captured persistent launch per step. A step
-is one whole transform of the batch (all hot-path steps: load, phase/rotation, scan, look-back,
-combine, store). Metric: complex output samples per second; the roofline counts the algorithmic
+(FP32 scan, two-float carries and prefix sums), complex64 outputs, one graph-captured forward per
+step (prefix-sum kernel and two warp-scan launches). A step is one whole transform of the batch (all
+hot-path steps: load, rotation, scan, start states, combine, store). Metric: complex output samples per second; the roofline counts the algorithmic
 12 bytes per output (4-byte input read + 8-byte output write) against the measured copy bandwidth.
 
 --impl reference times the CPU oracle (double-double kernel-integral SFT, oracle/sft_dd.c) on a
@@ -289,7 +289,7 @@ def main():
             "config": {"workload": w.name if args.workload == "c3" else "c3_small_64sig_max65536_32scales_K4",
                        "signals": len(lens),
                        "samples": int(sum(lens)), "scales": S, "K": w.K, "outputs_per_step": n_out,
-                       "precision": "FP32 scan + FP64 carries", "form": "rotating" if args.form != 1 else "kernel-integral",
+                       "precision": "FP32 scan, two-float carries and prefix sums", "form": "rotating" if args.form != 1 else "kernel-integral",
                        "l2": "inputs+outputs (10 GB) far exceed the 129 MB L2; no flush needed",
                        "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -66,7 +66,7 @@ constexpr int TICKETS = 4;
 constexpr long long PS_TILE_H = 512, PS_CHUNK_H = 8;  // prefix-sum tile and chunk (psum_kernel.cuh)
 // Rows whose half window exceeds this take their start states from prefix sums: a window segment
 // of such a row (about 16 L positions per warp) would leave too few, too long work items.
-constexpr long long SS_MIN_L = 2048;
+constexpr long long SS_MIN_L = 4096;
 
 // A launchable transform: kernel, work table, chains and status arrays.
 struct Launch {

@@ -295,12 +295,6 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
         }
       }
       // pass 2: outputs for positions in [t_out, t_end)
-      if (tf >= t_end || tf + ITEMS <= t_out) continue;
-      const int64_t oo = wi.out_off - D + tf;
-      const bool all_in = (tf >= t_out) && (tf + ITEMS <= t_end);
-      bool fast = false;
-      if constexpr (C::OUT == OUT_MORLET && sizeof(R) == 4)
-        fast = all_in && ((reinterpret_cast<uintptr_t>(reinterpret_cast<V*>(P.out) + oo) & 15) == 0);
       auto one = [&](int i) -> V {
         R xv[CH], xlv[CH];
         split_in<C>(xa[i], xl[i], xv, xlv);
@@ -316,22 +310,68 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
         if constexpr (C::ASFT) o = cmul(o, E);
         return o;
       };
-      if (fast) {
-        // every position stored: pairs of outputs as 16-byte streaming stores
-        float4* op = reinterpret_cast<float4*>(reinterpret_cast<V*>(P.out) + oo);
+      constexpr bool STAGE = (C::OUT == OUT_MORLET && sizeof(R) == 4 && ITEMS == 16);
+      const int64_t tw = wi.t_a + (int64_t)k * WT;  // first position of the warp-tile
+      if (tw >= t_end || tw + WT <= t_out) continue;  // no output in this warp-tile (warp-uniform)
+      if constexpr (STAGE) {
+        // The warp-tile's 512 outputs go through this warp's shared rows (one padded 144-byte row
+        // per lane, conflict-free both ways) so that every store instruction writes 512 (or 256)
+        // contiguous bytes instead of 32 scattered half-sectors; positions outside [t_out, t_end)
+        // are masked.
+        __shared__ float4 s_out[WARPS * 32 * 9];
+        float4* rows = s_out + (threadIdx.x >> 5) * (32 * 9);
 #pragma unroll
         for (int i = 0; i < ITEMS; i += 2) {
           const V o0 = one(i);
           const V o1 = one(i + 1);
-          __stcs(op + i / 2, make_float4((float)o0.x, (float)o0.y, (float)o1.x, (float)o1.y));
+          rows[lane * 9 + i / 2] = make_float4(o0.x, o0.y, o1.x, o1.y);
         }
-      } else {
-        V prev{};
+        __syncwarp();
+        V* ob = reinterpret_cast<V*>(P.out) + (wi.out_off - D + tw);
+        const int lo_o = (int)(t_out > tw ? t_out - tw : 0);         // stored outputs [lo_o, hi_o)
+        const int hi_o = (int)(t_end < tw + WT ? t_end - tw : WT);
+        if ((reinterpret_cast<uintptr_t>(ob) & 15) == 0) {
 #pragma unroll
-        for (int i = 0; i < ITEMS; ++i) {
-          const V o = one(i);
-          store_item<C>(P, oo, i, o, prev, false, tf + i >= t_out && tf + i < t_end);
-          prev = o;
+          for (int r = 0; r < 8; ++r) {
+            const int c = 32 * r + lane;  // 16-byte chunk: outputs 2c, 2c + 1
+            const float4 v = rows[(c >> 3) * 9 + (c & 7)];
+            const bool in0 = 2 * c >= lo_o && 2 * c < hi_o, in1 = 2 * c + 1 >= lo_o && 2 * c + 1 < hi_o;
+            if (in0 && in1) __stcs(reinterpret_cast<float4*>(ob) + c, v);
+            else if (in0) __stcs(ob + 2 * c, make_float2(v.x, v.y));
+            else if (in1) __stcs(ob + 2 * c + 1, make_float2(v.z, v.w));
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < 16; ++r) {
+            const int o = 32 * r + lane;
+            if (o >= lo_o && o < hi_o) __stcs(ob + o, reinterpret_cast<const float2*>(rows + (o >> 4) * 9)[o & 15]);
+          }
+        }
+        __syncwarp();
+      } else {
+        if (tf >= t_end || tf + ITEMS <= t_out) continue;
+        const int64_t oo = wi.out_off - D + tf;
+        const bool all_in = (tf >= t_out) && (tf + ITEMS <= t_end);
+        bool fast = false;
+        if constexpr (C::OUT == OUT_MORLET && sizeof(R) == 4)
+          fast = all_in && ((reinterpret_cast<uintptr_t>(reinterpret_cast<V*>(P.out) + oo) & 15) == 0);
+        if (fast) {
+          // every position of the lane stored: pairs of outputs as 16-byte streaming stores
+          float4* op = reinterpret_cast<float4*>(reinterpret_cast<V*>(P.out) + oo);
+#pragma unroll
+          for (int i = 0; i < ITEMS; i += 2) {
+            const V o0 = one(i);
+            const V o1 = one(i + 1);
+            __stcs(op + i / 2, make_float4((float)o0.x, (float)o0.y, (float)o1.x, (float)o1.y));
+          }
+        } else {
+          V prev{};
+#pragma unroll
+          for (int i = 0; i < ITEMS; ++i) {
+            const V o = one(i);
+            store_item<C>(P, oo, i, o, prev, false, tf + i >= t_out && tf + i < t_end);
+            prev = o;
+          }
         }
       }
     }
