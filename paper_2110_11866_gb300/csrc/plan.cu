@@ -196,10 +196,9 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
                 long long& slots, Launch& ln, std::vector<WorkItem>& pwork, long long warp_slots) {
   const int S = (int)p->sigmas.size();
   const long long nsig = (long long)p->lengths.size();
-  // Row order. Forward: blocks of signals holding about 16 M input samples (their input stays in
-  // L2 across the scales), scale by scale inside a block, so that consecutive work items share a
-  // scale (a CTA restages its tables only when the scale changes). Adjoint: scale-major (each scale
-  // is one launch that adds into the gradient).
+  // Row order. Forward: blocks of signals holding about 16 M input samples, scale by scale inside a
+  // block, so that a block's samples are mostly served from L2 to its later scales. Adjoint:
+  // scale-major (each scale is one launch that adds into the gradient).
   std::vector<std::pair<long long, int>> order;  // (signal, scale)
   if (adjoint) {
     for (int s = 0; s < S; ++s)

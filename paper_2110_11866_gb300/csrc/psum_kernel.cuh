@@ -35,6 +35,18 @@ __device__ __forceinline__ DFC dfc_rho512(const ScaleTab* tb, int j) {
   return DFC{DF{h.x, l.x}, DF{h.y, l.y}};
 }
 
+// Lane 0 stores the NT values held by lanes 0 .. NT-1 and then releases the status flag, so the
+// values are visible at GPU scope before the flag (one thread, program order + release; no fence).
+template <int NT>
+__device__ __forceinline__ void publish(DFC* dst, uint32_t* flag, uint32_t status, DFC mine, int lane) {
+#pragma unroll
+  for (int v = 0; v < NT; ++v) {
+    const DFC val = CarryOps<DFC>::shfl_idx(mine, v);
+    if (lane == 0) st_cg2(dst + v, val);
+  }
+  if (lane == 0) st_release(flag, status);
+}
+
 // Warp-level decoupled look-back in two-float precision. Lane v < NT holds `mine`, the aggregate of
 // term v over this item; the function publishes it (unless the item is the first of its chain),
 // sums the predecessors' published values back to the first inclusive one, each rotated by
@@ -49,12 +61,7 @@ __device__ __forceinline__ DFC warp_lookback(const KParams& P, int64_t slot, int
   if (slot == slot_first) return carry;
   DFC* aggp = reinterpret_cast<DFC*>(P.agg);
   const DFC* inclp = reinterpret_cast<const DFC*>(P.incl);
-  if (lane < NT) {
-    st_cg2(aggp + slot * NT + lane, mine);
-    __threadfence();
-  }
-  __syncwarp();
-  if (lane == 0) st_release(P.flags + slot, ST_AGG);
+  publish<NT>(aggp + slot * NT, P.flags + slot, ST_AGG, mine, lane);
   DFC rot = CO::one();
   int64_t base = slot - 1;
   long long polls = 0;
@@ -239,7 +246,7 @@ __device__ __forceinline__ void start_state(const KParams& P, const WorkItem& wi
 }
 
 template <class C>
-__global__ void __launch_bounds__(THREADS, C::K <= 6 ? 3 : 2) psum_kernel(const KParams P) {
+__global__ void __launch_bounds__(THREADS, C::K <= 4 ? 3 : 2) psum_kernel(const KParams P) {
   static_assert(std::is_same<typename C::R, float>::value && C::CH == 1 && C::ITEMS == 16,
                 "prefix sums are built for the FP32 real-input kernels");
   constexpr int K = C::K, ITEMS = C::ITEMS;
@@ -276,6 +283,7 @@ __global__ void __launch_bounds__(THREADS, C::K <= 6 ? 3 : 2) psum_kernel(const 
     for (int r = 0; r < TPL; ++r) Gm[r] = make_float2(0.f, 0.f);
 #pragma unroll
     if (lane == 0) prefetch_l2(xs, N, wi.t_a, wi.t_a + (int64_t)n_sub * PS_TILE);  // the chunk, into L2
+#pragma unroll
     for (int k = 0; k < PS_CHUNK; ++k) {
       const int64_t t0 = wi.t_a + (int64_t)k * PS_TILE;
       if (k < n_sub && t0 < N && t0 + PS_TILE > 0) {  // warp-uniform
@@ -319,13 +327,9 @@ __global__ void __launch_bounds__(THREADS, C::K <= 6 ? 3 : 2) psum_kernel(const 
     const DFC carry = warp_lookback<K>(P, wi.slot, wi.slot_first, CarryOps<DFC>::from(acc), tb, lane);
     // inclusive state after a full chunk, published at once for the successors' look-back
     if (n_sub == PS_CHUNK) {
-      if (lane < K) {
-        const DFC inc2 = dfc_add(dfc_mul(dfc_from_f4(__ldg(&tb->c_pw_tile[1][lane])), carry), CarryOps<DFC>::from(acc));
-        st_cg2(reinterpret_cast<DFC*>(P.incl) + wi.slot * K + lane, inc2);
-        __threadfence();
-      }
-      __syncwarp();
-      if (lane == 0) st_release(P.flags + wi.slot, ST_INCL);
+      const DFC inc2 = dfc_add(dfc_mul(dfc_from_f4(__ldg(&tb->c_pw_tile[1][lane < K ? lane : 0])), carry),
+                               CarryOps<DFC>::from(acc));
+      publish<K>(reinterpret_cast<DFC*>(P.incl) + wi.slot * K, P.flags + wi.slot, ST_INCL, inc2, lane);
     }
     // P at the end of each owned tile: rho^{512 (k + 1)} carry + in-chunk prefix, two-float
     const DFC cy = CarryOps<DFC>::shfl_idx(carry, tq);
