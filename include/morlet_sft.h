@@ -49,7 +49,8 @@ enum { MORLET_SFT = 0, MORLET_ASFT = 1 };
 /* precision: arithmetic of the per-sample scan and of the cross-tile carries */
 enum {
   MORLET_FP32_PLAIN = 0,  /* FP32 samples, FP32 scan, FP32 carries, one look-back chain per row */
-  MORLET_FP32_COMP = 1,   /* FP32 samples and scan; FP64 carries; short windows recomputed per tile */
+  MORLET_FP32_COMP = 1,   /* FP32 samples and scan; two-float (FP32 hi + lo) carries and prefix sums;
+                             windows restarted per segment or started from exact prefix-sum states */
   MORLET_FP64 = 2         /* FP64 everywhere */
 };
 /* scan form */
@@ -180,7 +181,7 @@ int morlet_debug_skip_tickets(morlet_plan_t plan, int64_t skip);
  * SFT, compensated FP32, unnormalised Morlet (norm 0), L = ceil(4 sigma); W: device complex64[N],
  * the caller's. Results equal morlet_plan + morlet_forward with the same parameters.
  * All working memory (fit, tables, tile table, look-back status) lives in one fixed device array of
- * about 7.2 MB inside the library; every GPU that loads the library holds it until the process exits.
+ * about 8.1 MB inside the library; every GPU that loads the library holds it until the process exits.
  * Limits: the row may need at most 16384 sub-tiles of 4096 outputs (N up to about 6.7e7 for short
  * windows) and at most 16384 look-back slots; larger sizes return MORLET_ERR_ARG.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that

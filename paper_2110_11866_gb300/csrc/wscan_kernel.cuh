@@ -330,7 +330,14 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
         V* ob = reinterpret_cast<V*>(P.out) + (wi.out_off - D + tw);
         const int lo_o = (int)(t_out > tw ? t_out - tw : 0);         // stored outputs [lo_o, hi_o)
         const int hi_o = (int)(t_end < tw + WT ? t_end - tw : WT);
-        if ((reinterpret_cast<uintptr_t>(ob) & 15) == 0) {
+        const bool aligned = (reinterpret_cast<uintptr_t>(ob) & 15) == 0;
+        if (aligned && lo_o == 0 && hi_o == WT) {  // the common case: every output of the tile
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const int c = 32 * r + lane;
+            __stcs(reinterpret_cast<float4*>(ob) + c, rows[(c >> 3) * 9 + (c & 7)]);
+          }
+        } else if (aligned) {
 #pragma unroll
           for (int r = 0; r < 8; ++r) {
             const int c = 32 * r + lane;  // 16-byte chunk: outputs 2c, 2c + 1
