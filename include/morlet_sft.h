@@ -151,11 +151,12 @@ int morlet_plan_info(morlet_plan_t plan, int32_t s, int64_t* L, int32_t* p0, int
 /*
  * morlet_plan_stats - launch shape and work of the forward, for measurement:
  * out[0] = threads per CTA, out[1] = samples per thread, out[2] = CTAs of the look-back kernel,
- * out[3] = work items of the scan kernels, out[4] = sub-tiles processed (incl. window prologues),
+ * out[3] = work items of the scan kernels, out[4] = 512-position tiles processed (incl. prologues),
  * out[5] = rows in look-back mode, out[6] = rows in window-segment mode, out[7] = kernel launches
- * per forward, out[8] = rows whose work items start from prefix sums, out[9] = prefix-sum work items.
+ * per forward, out[8] = rows whose work items start from prefix sums, out[9] = prefix-sum work items,
+ * out[10] = rows in lane-chunk mode, out[11] = lane-chunk work items.
  */
-int morlet_plan_stats(morlet_plan_t plan, int64_t out[10]);
+int morlet_plan_stats(morlet_plan_t plan, int64_t out[12]);
 
 /*
  * morlet_plan_set_spin_limit - change the bounded-wait limit (polls) of later launches; used to make

@@ -89,6 +89,7 @@ struct ScaleTab {
   double d_lam[KMAX];         // the same in FP64
   float4 c_neg16[32][KMAX];   // rho^{-16 a}, a = 0..31, two-float complex (|rho| = 1)
   float4 c_neg1[16][KMAX];    // rho^{-b}, b = 0..15, two-float complex
+  float2 f_shear[KMAX];       // (tan(beta p / 2), sin(beta p)): rho = e^{-i beta p} as three shears
 };
 
 struct KParams {

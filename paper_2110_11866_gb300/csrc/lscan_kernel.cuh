@@ -1,0 +1,284 @@
+// Single-pass lane-chunk scan for short windows (compensated FP32, SFT, real input, Morlet output).
+//
+// The warp kernel's two passes and warp scan cost about as much as the recursion itself. When the
+// window is short, each lane can instead own a contiguous chunk of C positions of a row and run the
+// recursion through it once, from a zero state a prologue of >= 2L positions before the chunk
+// (samples before chunk start - 2L count as zero, so the state is exact from the chunk's first
+// position on: the window-segment restart of the warp kernel, per lane). The recursion is the SFT's
+// 2L-sample form G <- rho G + (x[t] - x[t - 2L]), V = G + x[t - 2L] (see wscan_kernel.cuh), with the
+// direct-method combine of Sec. III-A; FP32 throughout, its history bounded by prologue + C.
+// Each step multiplies by rho = e^{-i theta} as three shears (x += t y; y -= s x; x += t y with
+// t = tan(theta/2), s = sin(theta)): the same operation count as a complex multiply, but the map has
+// determinant exactly one and its angle error is relative to theta, so the thousands of rotations a
+// lane applies drift far less in magnitude and phase than repeated products with a rounded rho.
+//
+// The 32 chunks of a warp lie C positions apart, so every global access goes through this warp's
+// shared buffers, transposed:
+//  - inputs: per step of 16 positions the warp copies the 32 lanes' runs of x[t] and x[t - 2L] into
+//    shared memory as 16-byte pieces (5 per run, covering a misalignment of up to 3 samples;
+//    consecutive lanes take consecutive pieces) with cp.async, one step ahead into the other of two
+//    buffers, so the copy of step k + 1 overlaps the arithmetic of step k; each lane reads its run
+//    back from a padded 80-byte row and shifts it by the run's misalignment, which is the same for
+//    every lane and step;
+//  - outputs: each lane writes its 16 complex outputs into a padded 144-byte row (over the input
+//    buffer it has just read); the warp stores them as 16-byte pieces, eight lanes per row (128
+//    contiguous bytes per row; the plan starts every row's chunks on an even output element),
+//    masked only in the steps that touch the ends of the row.
+// Every bank access is conflict-free (row strides of 20 and 36 words).
+//
+// Work item fields (see WorkItem): t_a = first position of lane 0's chunk, n_sub = C (multiple of
+// 16), t_dom = prologue (multiple of 16, >= 2L), t_out = D and t_end = D + N bound the stored
+// positions.
+#pragma once
+
+#include "scan_kernel.cuh"
+
+namespace msft {
+
+constexpr int LS_WARPS = 4;                  // warps per CTA (shared memory per warp: 10 KB)
+constexpr int LS_ITEMS = 16;                 // positions per lane per step
+constexpr int LS_PIECES = 5;                 // 16-byte input pieces per lane run (20 samples)
+constexpr int LS_RUN_F4 = 32 * LS_PIECES;    // float4 per input run buffer of a warp (160)
+constexpr int LS_BUF_F4 = 2 * LS_RUN_F4;     // one step's lead + lag buffers (320 float4 = 5120 B); the
+                                             // output rows (32 x 9 float4 = 4608 B) reuse them
+static_assert(32 * 9 <= LS_BUF_F4, "output rows fit in the input buffers");
+
+// v[i] = row[r + i] for the uniform shift r in [0, 3]
+__device__ __forceinline__ void ls_shift(const float (&row)[4 * LS_PIECES], int r, float (&v)[LS_ITEMS]) {
+  if (r == 0) {
+#pragma unroll
+    for (int i = 0; i < LS_ITEMS; ++i) v[i] = row[i];
+  } else if (r == 1) {
+#pragma unroll
+    for (int i = 0; i < LS_ITEMS; ++i) v[i] = row[i + 1];
+  } else if (r == 2) {
+#pragma unroll
+    for (int i = 0; i < LS_ITEMS; ++i) v[i] = row[i + 2];
+  } else {
+#pragma unroll
+    for (int i = 0; i < LS_ITEMS; ++i) v[i] = row[i + 3];
+  }
+}
+
+// 16-byte asynchronous copy global -> shared; `bytes` = 16, or 0 to write zeros (nothing is read).
+__device__ __forceinline__ void ls_cp16(float4* dst, const float* src, int bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void ls_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void ls_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void ls_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Piece of samples [e, e + 4) of the n-sample buffer x into dst: asynchronous when inside the
+// buffer, zeros when outside, element by element (synchronously) when it straddles an end.
+__device__ __forceinline__ void ls_piece(float4* dst, const float* __restrict__ x, int64_t e, int64_t n) {
+  if (e >= 0 && e + 4 <= n) {
+    ls_cp16(dst, x + e, 16);
+  } else if (e + 4 <= 0 || e >= n) {
+    ls_cp16(dst, x, 0);
+  } else {
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (e + i >= 0 && e + i < n) v[i] = __ldg(x + e + i);
+    *dst = make_float4(v[0], v[1], v[2], v[3]);
+  }
+}
+
+__device__ __forceinline__ int64_t ls_floordiv(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+__device__ __forceinline__ int ls_clamp(int64_t v, int hi) { return (int)(v < 0 ? 0 : (v > hi ? hi : v)); }
+
+template <class C>
+__global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel(const KParams P) {
+  static_assert(std::is_same<typename C::R, float>::value && C::CH == 1 && C::OUT == OUT_MORLET && !C::ASFT,
+                "the lane-chunk scan is built for the FP32 SFT Morlet transform");
+  constexpr int K = C::K;
+  const int lane = threadIdx.x & 31;
+  __shared__ __align__(16) float4 s_buf[LS_WARPS][2][LS_BUF_F4];
+  float4 (*const bufs)[LS_BUF_F4] = s_buf[threadIdx.x >> 5];
+  const float* __restrict__ xg = reinterpret_cast<const float*>(P.x);
+  const int64_t b0 = (int64_t)(reinterpret_cast<uintptr_t>(xg) >> 2);
+
+  long long w = 0;
+  if (lane == 0) w = (long long)atomicAdd(P.ticket, 1ull);
+  w = __shfl_sync(0xffffffffu, w, 0);
+  while (w < P.n_work) {
+    const WorkItem wi = P.work[w];
+    long long w2 = 0;  // items are independent: claim the next one now
+    if (lane == 0) w2 = (long long)atomicAdd(P.ticket, 1ull);
+
+    const ScaleTab* tb = P.tabs + wi.scale;
+    const int64_t L2 = 2 * tb->L, D = tb->D;
+    float2 sh[K];  // (tan(theta/2), sin(theta)) per term
+    float cM[K], cL[K], cx = 0.f;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      sh[j] = __ldg(&tb->f_shear[j]);
+      cM[j] = (float)tb->cM[j];
+      cL[j] = (float)tb->cL[j];
+      cx += cM[j];
+    }
+    const int64_t N = wi.n, pro = wi.t_dom;
+    const int Cc = wi.n_sub;
+    const int64_t a0 = wi.t_a - pro;                  // lane 0's first processed position
+    const int64_t s_l = wi.t_a + (int64_t)lane * Cc;  // this lane's first output position
+    const int64_t lo_l = s_l - L2 > 0 ? s_l - L2 : 0;  // samples before lo_l count as zero
+    // misalignment (in samples) of the lead and lagged runs, from their addresses; the same for
+    // every lane and step since C and the step are multiples of 4 samples
+    const int64_t e0 = wi.x_off + a0;
+    const int rl = (int)((b0 + e0) & 3), rg = (int)((b0 + e0 - L2) & 3);
+    const int n_pro = (int)(pro / LS_ITEMS), n_steps = (int)((pro + Cc) / LS_ITEMS);
+    int off[LS_PIECES];  // this lane's input pieces: chunk c = pc / 5, piece q = pc % 5 -> c C + 4 q
+#pragma unroll
+    for (int r = 0; r < LS_PIECES; ++r) {
+      const int pc = lane + 32 * r;
+      off[r] = (pc / LS_PIECES) * Cc + 4 * (pc % LS_PIECES);
+    }
+    // the whole item reads inside the buffer (no per-piece bounds checks)
+    const int64_t span = 31LL * Cc + (int64_t)n_steps * LS_ITEMS + 4 * LS_PIECES;
+    const bool inside = (e0 - L2 - 4 >= 0) && (e0 + span <= P.n_x);
+    // Steps that need no input masks in any lane: the lead run needs lo_l <= p and p + 16 <= N, the
+    // lagged run (output steps) lo_l <= p - 2L and p - 2L + 16 <= N, for p = p0 + 16 k.
+    int kl_a, kh_a, kl_g, kh_g;
+    {
+      const int64_t p0 = a0 + (int64_t)lane * Cc;
+      kl_a = ls_clamp(-ls_floordiv(p0 - lo_l, LS_ITEMS), n_steps);
+      kh_a = ls_clamp(ls_floordiv(N - LS_ITEMS - p0, LS_ITEMS) + 1, n_steps);
+      kl_g = ls_clamp(-ls_floordiv(p0 - lo_l - L2, LS_ITEMS), n_steps);
+      kh_g = ls_clamp(ls_floordiv(N + L2 - LS_ITEMS - p0, LS_ITEMS) + 1, n_steps);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        kl_a = max(kl_a, __shfl_xor_sync(0xffffffffu, kl_a, o));
+        kh_a = min(kh_a, __shfl_xor_sync(0xffffffffu, kh_a, o));
+        kl_g = max(kl_g, __shfl_xor_sync(0xffffffffu, kl_g, o));
+        kh_g = min(kh_g, __shfl_xor_sync(0xffffffffu, kh_g, o));
+      }
+    }
+    // 16-byte output pieces when the row's chunk starts are 16-byte aligned
+    const bool o16 = ((reinterpret_cast<uintptr_t>(reinterpret_cast<float2*>(P.out) + (wi.out_off - D + wi.t_a)) & 15) == 0);
+    float2* const orow = reinterpret_cast<float2*>(P.out) + (wi.out_off - D);
+    const int so = (lane >> 3) * Cc + 2 * (lane & 7);  // this lane's store piece in round 0
+
+    // copies of step k into buffer k & 1
+    auto issue = [&](int k) {
+      float4* bl = bufs[k & 1];
+      const int64_t step0 = a0 + (int64_t)k * LS_ITEMS;
+      const int64_t el = wi.x_off + step0 - rl, eg = wi.x_off + step0 - L2 - rg;
+      const bool lag = k >= n_pro;  // the prologue reads no lagged samples
+      if (inside) {
+#pragma unroll
+        for (int r = 0; r < LS_PIECES; ++r) {
+          ls_cp16(bl + lane + 32 * r, xg + el + off[r], 16);
+          if (lag) ls_cp16(bl + LS_RUN_F4 + lane + 32 * r, xg + eg + off[r], 16);
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < LS_PIECES; ++r) {
+          ls_piece(bl + lane + 32 * r, xg, el + off[r], P.n_x);
+          if (lag) ls_piece(bl + LS_RUN_F4 + lane + 32 * r, xg, eg + off[r], P.n_x);
+        }
+      }
+      ls_commit();
+    };
+
+    float2 S[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) S[j] = make_float2(0.f, 0.f);
+
+    issue(0);
+    for (int k = 0; k < n_steps; ++k) {
+      if (k + 1 < n_steps) {
+        issue(k + 1);
+        ls_wait_prev();
+      } else {
+        ls_wait_all();
+      }
+      __syncwarp();
+      float4* bl = bufs[k & 1];
+      const int64_t step0 = a0 + (int64_t)k * LS_ITEMS;  // lane 0's first position of this step
+      const bool pro_step = k < n_pro;                   // warp-uniform
+      float xa[LS_ITEMS], xl[LS_ITEMS];
+      {
+        float row[4 * LS_PIECES];
+#pragma unroll
+        for (int q = 0; q < LS_PIECES; ++q) reinterpret_cast<float4*>(row)[q] = bl[lane * LS_PIECES + q];
+        ls_shift(row, rl, xa);
+        if (!pro_step) {
+#pragma unroll
+          for (int q = 0; q < LS_PIECES; ++q) reinterpret_cast<float4*>(row)[q] = bl[LS_RUN_F4 + lane * LS_PIECES + q];
+          ls_shift(row, rg, xl);
+        }
+      }
+      __syncwarp();
+      if (k < kl_a || k >= kh_a || (!pro_step && (k < kl_g || k >= kh_g))) {  // warp-uniform
+        const int64_t p = step0 + (int64_t)lane * Cc;
+#pragma unroll
+        for (int i = 0; i < LS_ITEMS; ++i) {
+          const int64_t t = p + i;
+          if (t < lo_l || t >= N) xa[i] = 0.f;
+          if (t - L2 < lo_l || t - L2 >= N) xl[i] = 0.f;
+        }
+      }
+      if (pro_step) {  // x[t - 2L] is before lo_l throughout the prologue: the input is x[t] alone
+#pragma unroll
+        for (int i = 0; i < LS_ITEMS; ++i) {
+#pragma unroll
+          for (int j = 0; j < K; ++j) {
+            const float x1 = fmaf(sh[j].x, S[j].y, S[j].x);
+            S[j].y = fmaf(-sh[j].y, x1, S[j].y);
+            S[j].x = fmaf(sh[j].x, S[j].y, x1 + xa[i]);
+          }
+        }
+        continue;
+      }
+      // ---- output step: recursion, combine, rows in shared memory ----
+#pragma unroll
+      for (int i = 0; i < LS_ITEMS; i += 2) {
+        float2 o[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float d = xa[i + h] - xl[i + h];
+          float ox = 0.f, oy = 0.f;
+#pragma unroll
+          for (int j = 0; j < K; ++j) {
+            const float x1 = fmaf(sh[j].x, S[j].y, S[j].x);
+            S[j].y = fmaf(-sh[j].y, x1, S[j].y);
+            S[j].x = fmaf(sh[j].x, S[j].y, x1 + d);
+            ox = fmaf(cM[j], S[j].x, ox);
+            oy = fmaf(cL[j], S[j].y, oy);
+          }
+          o[h] = make_float2(fmaf(cx, xl[i + h], ox), oy);
+        }
+        bl[lane * 9 + i / 2] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+      }
+      __syncwarp();
+      // ---- cooperative stores: row c's 16-byte piece q holds positions p_c + 2q, p_c + 2q + 1 ----
+      if (o16 && step0 >= wi.t_out && step0 + 31LL * Cc + LS_ITEMS <= wi.t_end) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const int pc = lane + 32 * r;
+          __stcs(reinterpret_cast<float4*>(orow + step0 + so + (int64_t)(4 * r) * Cc), bl[(pc >> 3) * 9 + (pc & 7)]);
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const int pc = lane + 32 * r;
+          const int64_t pos = step0 + so + (int64_t)(4 * r) * Cc;
+          const bool in0 = pos >= wi.t_out && pos < wi.t_end;
+          const bool in1 = pos + 1 >= wi.t_out && pos + 1 < wi.t_end;
+          const float4 v = bl[(pc >> 3) * 9 + (pc & 7)];
+          if (in0 && in1 && o16) {
+            __stcs(reinterpret_cast<float4*>(orow + pos), v);
+          } else {
+            if (in0) __stcs(orow + pos, make_float2(v.x, v.y));
+            if (in1) __stcs(orow + pos + 1, make_float2(v.z, v.w));
+          }
+        }
+      }
+      __syncwarp();
+    }
+    w = __shfl_sync(0xffffffffu, w2, 0);
+  }
+}
+
+}  // namespace msft

@@ -61,12 +61,17 @@ constexpr int ITEMS = 16;
 constexpr long long TILE = (long long)THREADS * ITEMS;
 constexpr long long DEFAULT_SPIN = 1LL << 20;  // polls of ~64 ns sleep + an L2 round trip: about 1 s
 // work counters per launch: look-back kernel, warp kernel (window items), warp kernel (start-state
-// items), prefix-sum kernel
-constexpr int TICKETS = 4;
+// items), prefix-sum kernel, lane-chunk kernel
+constexpr int TICKETS = 5;
 constexpr long long PS_TILE_H = 512, PS_CHUNK_H = 8;  // prefix-sum tile and chunk (psum_kernel.cuh)
 // Rows whose half window exceeds this take their start states from prefix sums: a window segment
 // of such a row (about 16 L positions per warp) would leave too few, too long work items.
 constexpr long long SS_MIN_L = 4096;
+// Rows whose half window is at most this go to the lane-chunk scan (one pass per sample, a
+// prologue of 2L per lane chunk of max(1024, 8 L) positions).
+constexpr long long LS_MAX_L = 128;
+constexpr int LS_STEP_H = 16;     // positions per lane step of the lane-chunk scan (lscan_kernel.cuh)
+constexpr int LS_THREADS_H = 128;  // threads per CTA of the lane-chunk scan (4 warps, lscan_kernel.cuh)
 
 // A launchable transform: kernel, work table, chains and status arrays.
 struct Launch {
@@ -89,6 +94,12 @@ struct Launch {
   long long n_pwork = 0;
   int grid_p = 0;
   long long n_pslots = 0, n_ptiles = 0, rows_ss = 0;
+  // lane-chunk rows (forward, compensated FP32 Morlet, short windows): items d_lwork
+  const void* func_l = nullptr;
+  WorkItem* d_lwork = nullptr;
+  long long n_lwork = 0;
+  int grid_l = 0;
+  long long rows_lane = 0;
 };
 
 }  // namespace
@@ -119,6 +130,7 @@ struct morlet_plan_s {
   void* d_pincl = nullptr;
   void* d_pbuf = nullptr;        // prefix sums at tile ends
   long long ss_min_L = 0;        // rows with L above this use start states (0: none)
+  long long ls_max_L = 0;        // rows with L up to this use the lane-chunk scan (0: none)
   unsigned long long* d_ticket = nullptr;  // TICKETS counters per launch (adjoint: per scale)
   int* h_err = nullptr;                    // host-mapped error word
   int* d_err = nullptr;
@@ -183,6 +195,13 @@ bool ss_row(const morlet_plan_s* p, bool adjoint, const ScaleTab& tb) {
          p->desc.transform == MORLET_SFT && !(p->desc.flags & MORLET_FLAG_NO_HALO) && tb.L > p->ss_min_L;
 }
 
+// Lane-chunk rows: forward, compensated FP32 SFT Morlet in the rotating form, short window.
+bool ls_row(const morlet_plan_s* p, bool adjoint, const ScaleTab& tb) {
+  return !adjoint && p->ls_max_L > 0 && p->form == 2 && p->desc.precision == MORLET_FP32_COMP &&
+         p->desc.transform == MORLET_SFT && p->desc.method == MORLET_DIRECT &&
+         !(p->desc.flags & MORLET_FLAG_NO_HALO) && tb.L <= p->ls_max_L;
+}
+
 // Tiles of a start-state row: tile 0 starts at t_grid (the input element of every tile start is
 // 16-byte aligned); the outputs (positions [D, D + N)) lie in tiles [kD, kE].
 void ss_tiles(long long x_off, long long N, long long D, long long& t_grid, long long& kD, long long& kE) {
@@ -193,7 +212,8 @@ void ss_tiles(long long x_off, long long N, long long D, long long& t_grid, long
 }
 
 void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& work, std::vector<ChainDesc>& chains,
-                long long& slots, Launch& ln, std::vector<WorkItem>& pwork, long long warp_slots) {
+                long long& slots, Launch& ln, std::vector<WorkItem>& pwork, std::vector<WorkItem>& lwork,
+                long long warp_slots) {
   const int S = (int)p->sigmas.size();
   const long long nsig = (long long)p->lengths.size();
   // Row order. Forward: blocks of signals holding about 16 M input samples, scale by scale inside a
@@ -243,6 +263,39 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
     c.scale = s;
     const int ci = (int)chains.size();
     chains.push_back(c);
+    if (ls_row(p, adjoint, tb)) {
+      // 32 lane chunks of C positions per item, each after a prologue of >= 2L positions; chunks
+      // start where the output element is even (16-byte stores), the first one possibly one
+      // position before D (its output there is masked)
+      const long long Cfull = std::min<long long>(4096, std::max<long long>(1024, (8 * tb.L + LS_STEP_H - 1) / LS_STEP_H * LS_STEP_H));
+      const long long pro = (2 * tb.L + LS_STEP_H - 1) / LS_STEP_H * LS_STEP_H;
+      const long long t_first = tb.D, t_last = tb.D + N;
+      long long s0 = t_first - (((c.out_off % 2) + 2) % 2);
+      while (s0 < t_last) {
+        const long long rem = t_last - s0;
+        long long Ci = Cfull;
+        if (rem < 32 * Cfull) Ci = std::max<long long>(LS_STEP_H, ((rem + 31) / 32 + LS_STEP_H - 1) / LS_STEP_H * LS_STEP_H);
+        WorkItem w{};
+        w.x_off = c.x_off;
+        w.n = N;
+        w.out_off = c.out_off;
+        w.scale = s;
+        w.chain = ci;
+        w.n_sub = (int)Ci;
+        w.t_a = s0;
+        w.t_dom = pro;
+        w.t_out = t_first;
+        w.t_end = t_last;
+        w.slot = -1;
+        w.slot_first = -1;
+        w.p_row = -1;
+        lwork.push_back(w);
+        ln.sub_tiles += (32 * (Ci + pro) + 511) / 512;
+        s0 += 32 * Ci;
+      }
+      ln.rows_lane++;
+      continue;
+    }
     if (ss_row(p, adjoint, tb)) {
       long long tg, kD, kE;
       ss_tiles(c.x_off, N, tb.D, tg, kD, kE);
@@ -328,7 +381,7 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
 
 int setup_launch(morlet_plan_s* p, bool adjoint, Launch& ln, long long& slots) {
   int rc = MORLET_OK;
-  std::vector<WorkItem> work, pwork;
+  std::vector<WorkItem> work, pwork, lwork;
   std::vector<ChainDesc> chains;
   ln.func = kernel_for(variant_of(p, adjoint), p->K_kernel, false);
   if (!ln.func) return MORLET_ERR_UNSUPPORTED;
@@ -340,7 +393,7 @@ int setup_launch(morlet_plan_s* p, bool adjoint, Launch& ln, long long& slots) {
     if (occw < 1) occw = 1;
     ln.grid_w = occw * p->sms;
   }
-  build_work(p, adjoint, work, chains, slots, ln, pwork, (long long)ln.grid_w * WARPS);
+  build_work(p, adjoint, work, chains, slots, ln, pwork, lwork, (long long)ln.grid_w * WARPS);
   ln.n_work = (long long)work.size();
   {
     int occ = 0;
@@ -359,6 +412,17 @@ int setup_launch(morlet_plan_s* p, bool adjoint, Launch& ln, long long& slots) {
     CK(cudaMalloc(&ln.d_pwork, sizeof(WorkItem) * pwork.size()));
     CK(cudaMemcpy(ln.d_pwork, pwork.data(), sizeof(WorkItem) * pwork.size(), cudaMemcpyHostToDevice));
   }
+  if (!lwork.empty()) {
+    ln.func_l = kernel_lscan(p->K_kernel);
+    if (!ln.func_l) return MORLET_ERR_UNSUPPORTED;
+    int occl = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occl, ln.func_l, LS_THREADS_H, 0));
+    if (occl < 1) occl = 1;
+    ln.grid_l = occl * p->sms;
+    ln.n_lwork = (long long)lwork.size();
+    CK(cudaMalloc(&ln.d_lwork, sizeof(WorkItem) * lwork.size()));
+    CK(cudaMemcpy(ln.d_lwork, lwork.data(), sizeof(WorkItem) * lwork.size(), cudaMemcpyHostToDevice));
+  }
   CK(cudaMalloc(&ln.d_work, sizeof(WorkItem) * std::max<size_t>(1, work.size())));
   CK(cudaMalloc(&ln.d_chains, sizeof(ChainDesc) * std::max<size_t>(1, chains.size())));
   CK(cudaMemcpy(ln.d_work, work.data(), sizeof(WorkItem) * work.size(), cudaMemcpyHostToDevice));
@@ -372,9 +436,11 @@ void free_launch(Launch& ln) {
   cudaFree(ln.d_work);
   cudaFree(ln.d_chains);
   cudaFree(ln.d_pwork);
+  cudaFree(ln.d_lwork);
   ln.d_work = nullptr;
   ln.d_chains = nullptr;
   ln.d_pwork = nullptr;
+  ln.d_lwork = nullptr;
 }
 
 int check_latched(morlet_plan_s* p) {
@@ -430,19 +496,34 @@ cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out
   kp.n_x = (&ln == &p->adj) ? p->n_in * (long long)p->sigmas.size() : p->n_in;  // adjoint reads the scalogram
   kp.pbuf = p->d_pbuf;
   bool forked = false;
-  if (two && s_beg > c_end) {
-    KParams kw = kp;
-    kw.work = ln.d_work + c_end;
-    kw.n_work = s_beg - c_end;
-    kw.n_chain = 0;
-    kw.ticket = tickets + 1;
+  const bool lane_items = ln.n_lwork > 0 && &ln == &p->fwd;
+  if ((two && s_beg > c_end) || lane_items) {
     e = cudaEventRecord(p->ev_fork, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(p->aux, p->ev_fork, 0);
     if (e != cudaSuccess) return e;
-    void* args[] = {&kw};
-    const int grid = (int)std::min<long long>(ln.grid_w, (kw.n_work + WARPS - 1) / WARPS);
-    e = cudaLaunchKernel(ln.func_w, dim3(grid), dim3(THREADS), args, 0, p->aux);
-    if (e == cudaSuccess) e = cudaEventRecord(p->ev_join, p->aux);
+    if (lane_items) {
+      KParams kl = kp;
+      kl.work = ln.d_lwork;
+      kl.n_work = ln.n_lwork;
+      kl.n_chain = 0;
+      kl.ticket = tickets + 4;
+      void* args[] = {&kl};
+      const int grid = (int)std::min<long long>(ln.grid_l, (kl.n_work + LS_THREADS_H / 32 - 1) / (LS_THREADS_H / 32));
+      e = cudaLaunchKernel(ln.func_l, dim3(grid), dim3(LS_THREADS_H), args, 0, p->aux);
+      if (e != cudaSuccess) return e;
+    }
+    if (two && s_beg > c_end) {
+      KParams kw = kp;
+      kw.work = ln.d_work + c_end;
+      kw.n_work = s_beg - c_end;
+      kw.n_chain = 0;
+      kw.ticket = tickets + 1;
+      void* args[] = {&kw};
+      const int grid = (int)std::min<long long>(ln.grid_w, (kw.n_work + WARPS - 1) / WARPS);
+      e = cudaLaunchKernel(ln.func_w, dim3(grid), dim3(THREADS), args, 0, p->aux);
+      if (e != cudaSuccess) return e;
+    }
+    e = cudaEventRecord(p->ev_join, p->aux);
     if (e != cudaSuccess) return e;
     forked = true;
   }
@@ -648,6 +729,7 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
 
     // work tables and status arrays
     p->ss_min_L = SS_MIN_L;
+    p->ls_max_L = LS_MAX_L;
     long long slots = 0;
     rc = setup_launch(p, false, p->fwd, slots);
     if (rc) goto fail;
@@ -762,7 +844,7 @@ int morlet_plan_info(morlet_plan_t p, int32_t s, int64_t* L, int32_t* p0, int32_
   return MORLET_OK;
 }
 
-int morlet_plan_stats(morlet_plan_t p, int64_t o[10]) {
+int morlet_plan_stats(morlet_plan_t p, int64_t o[12]) {
   if (!p || !o) return MORLET_ERR_ARG;
   const Launch& f = p->fwd;
   const bool two = f.func_w != nullptr;
@@ -775,9 +857,11 @@ int morlet_plan_stats(morlet_plan_t p, int64_t o[10]) {
   o[4] = f.sub_tiles;
   o[5] = f.rows_chain;
   o[6] = f.rows_halo;
-  o[7] = (c_end > 0) + (s_beg > c_end) + (f.n_work > s_beg) + (f.n_pwork > 0 && f.n_work > s_beg);
+  o[7] = (c_end > 0) + (s_beg > c_end) + (f.n_work > s_beg) + (f.n_pwork > 0 && f.n_work > s_beg) + (f.n_lwork > 0);
   o[8] = f.rows_ss;
   o[9] = f.n_pwork;
+  o[10] = f.rows_lane;
+  o[11] = f.n_lwork;
   return MORLET_OK;
 }
 

@@ -57,6 +57,7 @@ constexpr int N_KBUILT = 6;
 __host__ __device__ constexpr int kbuilt(int i) { return i == 0 ? 2 : i == 1 ? 3 : i == 2 ? 4 : i == 3 ? 6 : i == 4 ? 8 : 12; }
 
 const void* kernel_for(int variant, int K, bool warp);
-const void* kernel_psum(int K);  // prefix sums of the start-state rows (k_psum.cu)
+const void* kernel_psum(int K);   // prefix sums of the start-state rows (k_psum.cu)
+const void* kernel_lscan(int K);  // lane-chunk scan of short-window rows (k_lscan.cu)
 
 }  // namespace msft

@@ -256,9 +256,11 @@ __global__ void build_tables(ScaleTab* tabs, const FitJob* jobs, int n_scales, i
     else tb.c_neg1[q - 32][j] = dfc4(harmonic(p, (long long)(q - 32), L));
   }
   for (int j = threadIdx.x; j < KMAX; j += blockDim.x) {
-    const double sh = sinpi((double)(tb.p0 + j) / (double)(2 * L));  // sin(beta p / 2)
+    double sh, ch;
+    sincospi((double)(tb.p0 + j) / (double)(2 * L), &sh, &ch);  // sin, cos of beta p / 2
     tb.d_lam[j] = j < K_kernel ? 4.0 * sh * sh : 0.0;
     tb.f_lam[j] = (float)tb.d_lam[j];
+    tb.f_shear[j] = j < K_kernel ? make_float2((float)(sh / ch), (float)(2.0 * sh * ch)) : make_float2(0.f, 0.f);
   }
   for (int idx = threadIdx.x; idx < K_kernel * 8; idx += blockDim.x) {
     const int j = idx % K_kernel, mm = idx / K_kernel;

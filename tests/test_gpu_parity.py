@@ -47,6 +47,38 @@ def test_c1_fp64_single_signal(form):
     print(f"c1 SFT vs direct +-8 sigma Morlet: {rel_err(ref, true):.3e}")
 
 
+@pytest.mark.parametrize("K", [2, 4, 6])
+@pytest.mark.parametrize("shift", [0, 1, 3])
+def test_lane_chunk_rows_and_unaligned_buffers(K, shift):
+    """Short windows in compensated FP32 go through the lane-chunk scan: rows shorter than a lane
+    chunk, rows spanning several work items, odd and even output offsets, both parities of L, and
+    input / output buffers that start `shift` elements past a 16-byte boundary."""
+    import torch
+    rng = np.random.default_rng(500 + 10 * K + shift)
+    lens = [1, 5, 17, 1000, 33333, 70001, 4096]
+    sigs = [rng.standard_normal(n).astype(np.float32) for n in lens]
+    sigmas = [8.0, 13.25, 64.0]
+    plan = m.morlet_plan(lens, sigmas, K=K, precision=m.MORLET_FP32_COMP)
+    st = m.morlet_plan_stats(plan)
+    assert st["rows_lane_chunk"] == len(lens) * len(sigmas) and st["lane_chunk_items"] > 0
+    S, n_in = len(sigmas), sum(lens)
+    xb = torch.zeros(n_in + 4, dtype=torch.float32, device="cuda")
+    xb[shift:shift + n_in] = torch.from_numpy(np.concatenate(sigs)).cuda()
+    Wb = torch.zeros(n_in * S + 4, dtype=torch.complex64, device="cuda")
+    m.morlet_forward(plan, xb[shift:], Wb[shift:])
+    torch.cuda.synchronize()
+    assert m.morlet_last_device_error(plan) == 0
+    Wh = Wb.cpu().numpy()
+    assert np.all(Wh[:shift] == 0) and np.all(Wh[shift + n_in * S:] == 0)  # nothing written outside
+    off = 0
+    for x, n in zip(sigs, lens):
+        for s, sg in enumerate(sigmas):
+            got = Wh[shift + S * off + s * n: shift + S * off + (s + 1) * n]
+            e = rel_err(got, oracle_forward(x.astype(np.float64), sg, K))
+            assert e < 1e-5, (n, sg, e)
+        off += n
+
+
 @pytest.mark.parametrize("K", [3, 4, 6])
 def test_start_state_rows(K):
     """Long windows in compensated FP32: work items start from the lag-free prefix sums (several
