@@ -3,7 +3,7 @@
 Workload (default): the batched scalogram -- 256 float32 signals with lengths log-uniform in
 [1024, 1048576] (seed 2), 32 scales sigma = 2^(3 + j/3), omega0 = 6/sigma, K = 4, compensated FP32
 (FP32 scan, two-float carries and prefix sums), complex64 outputs, one graph-captured forward per
-step (prefix-sum kernel and two warp-scan launches). A step is one whole transform of the batch (all
+step (lane-chunk kernel, two warp-scan launches, prefix-sum kernel). A step is one whole transform of the batch (all
 hot-path steps: load, rotation, scan, start states, combine, store). Metric: complex output samples per second; the roofline counts the algorithmic
 12 bytes per output (4-byte input read + 8-byte output write) against the measured copy bandwidth.
 
@@ -166,6 +166,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--workload", default="c3", choices=["c3", "c3_small"],
                     help="c3: the full batched scalogram; c3_small: 64 signals clipped to 65536 samples (profiling)")
+    ap.add_argument("--scales", default=None,
+                    help="a:b keeps scales a..b-1 of the workload (profiling one kernel's rows); default all")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
@@ -181,6 +183,11 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     w = WL.c3_scalogram() if args.workload == "c3" else WL.c3_scalogram(n_signals=64, max_len=65536)
+    wname = w.name if args.workload == "c3" else "c3_small_64sig_max65536_32scales_K4"
+    if args.scales:
+        a, b = (int(v) for v in args.scales.split(":"))
+        w = WL.Workload(w.name, w.signals, w.sigmas[a:b], w.K)
+        wname += f"_scales{a}-{b}"
     lens, sigmas = w.lengths, w.sigmas
     n_out = w.n_outputs
     x_host = torch.from_numpy(w.concat()).pin_memory()
@@ -288,7 +295,7 @@ def main():
             "value": value, "unit": "output samples/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": w.name if args.workload == "c3" else "c3_small_64sig_max65536_32scales_K4",
+            "config": {"workload": wname,
                        "signals": len(lens),
                        "samples": int(sum(lens)), "scales": S, "K": w.K, "outputs_per_step": n_out,
                        "precision": "FP32 scan, two-float carries and prefix sums", "form": "rotating" if args.form != 1 else "kernel-integral",
@@ -297,7 +304,7 @@ def main():
                        "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "forward step (prefix-sum kernel + 2 warp-scan launches, one graph)",
+                         "kernel": "forward step (lane-chunk, warp-scan and prefix-sum kernels, one graph)",
                          "algorithmic_bytes_per_output": BYTES_PER_OUTPUT,
                          "strict_floor_bytes_per_output": 8 + 4 / S,
                          "strict_floor_frac": achieved * (8 + 4 / S) / BYTES_PER_OUTPUT / peak},

@@ -108,7 +108,6 @@ __global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel
     if (lane == 0) w2 = (long long)atomicAdd(P.ticket, 1ull);
 
     const ScaleTab* tb = P.tabs + wi.scale;
-    const int64_t L2 = 2 * tb->L, D = tb->D;
     float2 sh[K];  // (tan(theta/2), sin(theta)) per term
     float cM[K], cL[K], cx = 0.f;
 #pragma unroll
@@ -118,16 +117,17 @@ __global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel
       cL[j] = (float)tb->cL[j];
       cx += cM[j];
     }
-    const int64_t N = wi.n, pro = wi.t_dom;
-    const int Cc = wi.n_sub;
-    const int64_t a0 = wi.t_a - pro;                  // lane 0's first processed position
-    const int64_t s_l = wi.t_a + (int64_t)lane * Cc;  // this lane's first output position
-    const int64_t lo_l = s_l - L2 > 0 ? s_l - L2 : 0;  // samples before lo_l count as zero
+    // positions relative to the row fit in 32 bits (the plan keeps rows below 2^30 positions)
+    const int N = (int)wi.n, pro = (int)wi.t_dom, Cc = wi.n_sub, L2 = 2 * (int)tb->L;
+    const int a0 = (int)wi.t_a - pro;             // lane 0's first processed position
+    const int s_l = (int)wi.t_a + lane * Cc;      // this lane's first output position
+    const int lo_l = s_l - L2 > 0 ? s_l - L2 : 0;  // samples before lo_l count as zero
+    const int t_out = (int)wi.t_out, t_end = (int)wi.t_end;
+    const float* __restrict__ xrow = xg + wi.x_off;
     // misalignment (in samples) of the lead and lagged runs, from their addresses; the same for
     // every lane and step since C and the step are multiples of 4 samples
-    const int64_t e0 = wi.x_off + a0;
-    const int rl = (int)((b0 + e0) & 3), rg = (int)((b0 + e0 - L2) & 3);
-    const int n_pro = (int)(pro / LS_ITEMS), n_steps = (int)((pro + Cc) / LS_ITEMS);
+    const int rl = (int)((b0 + wi.x_off + a0) & 3), rg = (int)((b0 + wi.x_off + a0 - L2) & 3);
+    const int n_pro = pro / LS_ITEMS, n_steps = (pro + Cc) / LS_ITEMS;
     int off[LS_PIECES];  // this lane's input pieces: chunk c = pc / 5, piece q = pc % 5 -> c C + 4 q
 #pragma unroll
     for (int r = 0; r < LS_PIECES; ++r) {
@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel
       off[r] = (pc / LS_PIECES) * Cc + 4 * (pc % LS_PIECES);
     }
     // the whole item reads inside the buffer (no per-piece bounds checks)
+    const int64_t e0 = wi.x_off + a0;
     const int64_t span = 31LL * Cc + (int64_t)n_steps * LS_ITEMS + 4 * LS_PIECES;
     const bool inside = (e0 - L2 - 4 >= 0) && (e0 + span <= P.n_x);
     // Steps that need no input masks in any lane: the lead run needs lo_l <= p and p + 16 <= N, the
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel
       kl_a = ls_clamp(-ls_floordiv(p0 - lo_l, LS_ITEMS), n_steps);
       kh_a = ls_clamp(ls_floordiv(N - LS_ITEMS - p0, LS_ITEMS) + 1, n_steps);
       kl_g = ls_clamp(-ls_floordiv(p0 - lo_l - L2, LS_ITEMS), n_steps);
-      kh_g = ls_clamp(ls_floordiv(N + L2 - LS_ITEMS - p0, LS_ITEMS) + 1, n_steps);
+      kh_g = ls_clamp(ls_floordiv((int64_t)N + L2 - LS_ITEMS - p0, LS_ITEMS) + 1, n_steps);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         kl_a = max(kl_a, __shfl_xor_sync(0xffffffffu, kl_a, o));
@@ -155,23 +156,25 @@ __global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel
       }
     }
     // 16-byte output pieces when the row's chunk starts are 16-byte aligned
-    const bool o16 = ((reinterpret_cast<uintptr_t>(reinterpret_cast<float2*>(P.out) + (wi.out_off - D + wi.t_a)) & 15) == 0);
-    float2* const orow = reinterpret_cast<float2*>(P.out) + (wi.out_off - D);
+    float2* const orow = reinterpret_cast<float2*>(P.out) + (wi.out_off - tb->D);
+    const bool o16 = ((reinterpret_cast<uintptr_t>(orow + wi.t_a) & 15) == 0);
     const int so = (lane >> 3) * Cc + 2 * (lane & 7);  // this lane's store piece in round 0
 
     // copies of step k into buffer k & 1
     auto issue = [&](int k) {
       float4* bl = bufs[k & 1];
-      const int64_t step0 = a0 + (int64_t)k * LS_ITEMS;
-      const int64_t el = wi.x_off + step0 - rl, eg = wi.x_off + step0 - L2 - rg;
+      const int step0 = a0 + k * LS_ITEMS;
       const bool lag = k >= n_pro;  // the prologue reads no lagged samples
       if (inside) {
+        const float* pl = xrow + (step0 - rl);
+        const float* pg = xrow + (step0 - L2 - rg);
 #pragma unroll
         for (int r = 0; r < LS_PIECES; ++r) {
-          ls_cp16(bl + lane + 32 * r, xg + el + off[r], 16);
-          if (lag) ls_cp16(bl + LS_RUN_F4 + lane + 32 * r, xg + eg + off[r], 16);
+          ls_cp16(bl + lane + 32 * r, pl + off[r], 16);
+          if (lag) ls_cp16(bl + LS_RUN_F4 + lane + 32 * r, pg + off[r], 16);
         }
       } else {
+        const int64_t el = wi.x_off + step0 - rl, eg = wi.x_off + step0 - L2 - rg;
 #pragma unroll
         for (int r = 0; r < LS_PIECES; ++r) {
           ls_piece(bl + lane + 32 * r, xg, el + off[r], P.n_x);
@@ -195,7 +198,7 @@ __global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel
       }
       __syncwarp();
       float4* bl = bufs[k & 1];
-      const int64_t step0 = a0 + (int64_t)k * LS_ITEMS;  // lane 0's first position of this step
+      const int step0 = a0 + k * LS_ITEMS;  // lane 0's first position of this step
       const bool pro_step = k < n_pro;                   // warp-uniform
       float xa[LS_ITEMS], xl[LS_ITEMS];
       {
@@ -211,10 +214,10 @@ __global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel
       }
       __syncwarp();
       if (k < kl_a || k >= kh_a || (!pro_step && (k < kl_g || k >= kh_g))) {  // warp-uniform
-        const int64_t p = step0 + (int64_t)lane * Cc;
+        const int p = step0 + lane * Cc;
 #pragma unroll
         for (int i = 0; i < LS_ITEMS; ++i) {
-          const int64_t t = p + i;
+          const int t = p + i;
           if (t < lo_l || t >= N) xa[i] = 0.f;
           if (t - L2 < lo_l || t - L2 >= N) xl[i] = 0.f;
         }
@@ -253,19 +256,19 @@ __global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel
       }
       __syncwarp();
       // ---- cooperative stores: row c's 16-byte piece q holds positions p_c + 2q, p_c + 2q + 1 ----
-      if (o16 && step0 >= wi.t_out && step0 + 31LL * Cc + LS_ITEMS <= wi.t_end) {
+      if (o16 && step0 >= t_out && step0 + 31 * Cc + LS_ITEMS <= t_end) {
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
           const int pc = lane + 32 * r;
-          __stcs(reinterpret_cast<float4*>(orow + step0 + so + (int64_t)(4 * r) * Cc), bl[(pc >> 3) * 9 + (pc & 7)]);
+          __stcs(reinterpret_cast<float4*>(orow + (step0 + so + 4 * r * Cc)), bl[(pc >> 3) * 9 + (pc & 7)]);
         }
       } else {
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
           const int pc = lane + 32 * r;
-          const int64_t pos = step0 + so + (int64_t)(4 * r) * Cc;
-          const bool in0 = pos >= wi.t_out && pos < wi.t_end;
-          const bool in1 = pos + 1 >= wi.t_out && pos + 1 < wi.t_end;
+          const int pos = step0 + so + 4 * r * Cc;
+          const bool in0 = pos >= t_out && pos < t_end;
+          const bool in1 = pos + 1 >= t_out && pos + 1 < t_end;
           const float4 v = bl[(pc >> 3) * 9 + (pc & 7)];
           if (in0 && in1 && o16) {
             __stcs(reinterpret_cast<float4*>(orow + pos), v);

@@ -196,10 +196,11 @@ bool ss_row(const morlet_plan_s* p, bool adjoint, const ScaleTab& tb) {
 }
 
 // Lane-chunk rows: forward, compensated FP32 SFT Morlet in the rotating form, short window.
-bool ls_row(const morlet_plan_s* p, bool adjoint, const ScaleTab& tb) {
+// (Positions inside such a row are 32-bit in the kernel: rows stay below 2^30 positions.)
+bool ls_row(const morlet_plan_s* p, bool adjoint, const ScaleTab& tb, long long N) {
   return !adjoint && p->ls_max_L > 0 && p->form == 2 && p->desc.precision == MORLET_FP32_COMP &&
          p->desc.transform == MORLET_SFT && p->desc.method == MORLET_DIRECT &&
-         !(p->desc.flags & MORLET_FLAG_NO_HALO) && tb.L <= p->ls_max_L;
+         !(p->desc.flags & MORLET_FLAG_NO_HALO) && tb.L <= p->ls_max_L && N + 2 * tb.L + (1LL << 20) < (1LL << 30);
 }
 
 // Tiles of a start-state row: tile 0 starts at t_grid (the input element of every tile start is
@@ -263,7 +264,7 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
     c.scale = s;
     const int ci = (int)chains.size();
     chains.push_back(c);
-    if (ls_row(p, adjoint, tb)) {
+    if (ls_row(p, adjoint, tb, N)) {
       // 32 lane chunks of C positions per item, each after a prologue of >= 2L positions; chunks
       // start where the output element is even (16-byte stores), the first one possibly one
       // position before D (its output there is masked)

@@ -57,10 +57,10 @@ def test_lane_chunk_rows_and_unaligned_buffers(K, shift):
     rng = np.random.default_rng(500 + 10 * K + shift)
     lens = [1, 5, 17, 1000, 33333, 70001, 4096]
     sigs = [rng.standard_normal(n).astype(np.float32) for n in lens]
-    sigmas = [8.0, 13.25, 64.0]
+    sigmas = [8.0, 13.25, 32.0, 64.0]   # L = 32, 53, 128 in lane chunks; L = 256 in window segments
     plan = m.morlet_plan(lens, sigmas, K=K, precision=m.MORLET_FP32_COMP)
     st = m.morlet_plan_stats(plan)
-    assert st["rows_lane_chunk"] == len(lens) * len(sigmas) and st["lane_chunk_items"] > 0
+    assert st["rows_lane_chunk"] == len(lens) * 3 and st["lane_chunk_items"] > 0
     S, n_in = len(sigmas), sum(lens)
     xb = torch.zeros(n_in + 4, dtype=torch.float32, device="cuda")
     xb[shift:shift + n_in] = torch.from_numpy(np.concatenate(sigs)).cuda()
