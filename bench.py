@@ -166,6 +166,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--workload", default="c3", choices=["c3", "c3_small"],
                     help="c3: the full batched scalogram; c3_small: 64 signals clipped to 65536 samples (profiling)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default row thresholds instead of timing them at plan time")
     ap.add_argument("--scales", default=None,
                     help="a:b keeps scales a..b-1 of the workload (profiling one kernel's rows); default all")
     args = ap.parse_args()
@@ -192,7 +194,10 @@ def main():
     n_out = w.n_outputs
     x_host = torch.from_numpy(w.concat()).pin_memory()
     x = x_host.to(dev)
-    plan = m.morlet_plan(lens, sigmas, xi=w.xi, K=w.K, precision=m.MORLET_FP32_COMP, form=args.form)
+    t_plan = time.perf_counter()
+    plan = m.morlet_plan(lens, sigmas, xi=w.xi, K=w.K, precision=m.MORLET_FP32_COMP, form=args.form,
+                         flags=0 if args.no_autotune else m.MORLET_FLAG_AUTOTUNE)
+    t_plan = time.perf_counter() - t_plan
     W = torch.empty(n_out, dtype=torch.complex64, device=dev)
     st = torch.cuda.Stream(dev)
 
@@ -301,7 +306,8 @@ def main():
                        "precision": "FP32 scan, two-float carries and prefix sums", "form": "rotating" if args.form != 1 else "kernel-integral",
                        "l2": f"inputs {4 * sum(lens) / 1e6:.0f} MB + outputs {8 * n_out / 1e9:.2f} GB per step "
                              "exceed the 129 MB L2 (no flush between steps)",
-                       "parallelism": f"replicas x{ws}"},
+                       "parallelism": f"replicas x{ws}", "plan_seconds": round(t_plan, 2),
+                       "autotune": not args.no_autotune},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "forward step (lane-chunk, warp-scan and prefix-sum kernels, one graph)",

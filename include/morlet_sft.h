@@ -62,7 +62,9 @@ enum {
 /* flags */
 enum {
   MORLET_FLAG_NO_GRAPH = 1,   /* launch kernels directly instead of replaying a CUDA graph */
-  MORLET_FLAG_AUTOTUNE = 2,   /* time the launch shapes on this plan at plan time and keep the fastest */
+  MORLET_FLAG_AUTOTUNE = 2,   /* compensated FP32 SFT Morlet plans: at plan time, time the forward under a
+                                 few row-to-kernel thresholds (see morlet_plan_stats) on a zero input and
+                                 a scratch output of the batch's size, and keep the fastest */
   MORLET_FLAG_NO_HALO = 4     /* force one look-back chain per row (no per-tile window recompute) */
 };
 
@@ -154,9 +156,11 @@ int morlet_plan_info(morlet_plan_t plan, int32_t s, int64_t* L, int32_t* p0, int
  * out[3] = work items of the scan kernels, out[4] = 512-position tiles processed (incl. prologues),
  * out[5] = rows in look-back mode, out[6] = rows in window-segment mode, out[7] = kernel launches
  * per forward, out[8] = rows whose work items start from prefix sums, out[9] = prefix-sum work items,
- * out[10] = rows in lane-chunk mode, out[11] = lane-chunk work items.
+ * out[10] = rows in lane-chunk mode, out[11] = lane-chunk work items, out[12] / out[13] = the row
+ * thresholds in use (rows with L <= out[12] take the lane-chunk scan, rows with L > out[13] start
+ * from prefix sums).
  */
-int morlet_plan_stats(morlet_plan_t plan, int64_t out[12]);
+int morlet_plan_stats(morlet_plan_t plan, int64_t out[14]);
 
 /*
  * morlet_plan_set_spin_limit - change the bounded-wait limit (polls) of later launches; used to make

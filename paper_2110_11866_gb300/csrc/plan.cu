@@ -569,6 +569,104 @@ cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out
   return e;
 }
 
+// (Re)build the forward launch and its prefix-sum workspace for the plan's current row thresholds
+// (ls_max_L, ss_min_L). `slots` returns the look-back slots the forward needs.
+int build_forward(morlet_plan_s* p, long long& slots) {
+  int rc = MORLET_OK;
+  if (p->gexec) {
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+  }
+  free_launch(p->fwd);
+  p->fwd = Launch{};
+  cudaFree(p->d_pflags);
+  cudaFree(p->d_pagg);
+  cudaFree(p->d_pincl);
+  cudaFree(p->d_pbuf);
+  p->d_pflags = nullptr;
+  p->d_pagg = p->d_pincl = p->d_pbuf = nullptr;
+  slots = 0;
+  rc = setup_launch(p, false, p->fwd, slots);
+  if (rc) return rc;
+  if (p->fwd.n_pwork > 0) {
+    const size_t kb = sizeof(float4) * p->K_kernel;  // K two-float complex values
+    CK(cudaMalloc(&p->d_pflags, sizeof(uint32_t) * p->fwd.n_pslots));
+    CK(cudaMalloc(&p->d_pagg, kb * p->fwd.n_pslots));
+    CK(cudaMalloc(&p->d_pincl, kb * p->fwd.n_pslots));
+    CK(cudaMalloc(&p->d_pbuf, kb * std::max(1LL, p->fwd.n_ptiles)));
+  }
+  return MORLET_OK;
+fail:
+  return rc;
+}
+
+// MORLET_FLAG_AUTOTUNE: time the forward of this plan's batch (zero input, scratch output) under a
+// few choices of which rows take the lane-chunk scan (L <= ls_max_L) and which start from prefix
+// sums (L > ss_min_L), and keep the fastest. Only the compensated rotating-form SFT Morlet plans
+// have these choices; others, or a batch whose scratch output does not fit in memory, keep the
+// defaults.
+int autotune(morlet_plan_s* p, cudaStream_t st) {
+  const morlet_plan_desc& d = p->desc;
+  if (!(p->form == 2 && d.precision == MORLET_FP32_COMP && d.transform == MORLET_SFT && d.method == MORLET_DIRECT))
+    return MORLET_OK;
+  const long long S = (long long)p->sigmas.size();
+  void* x = nullptr;
+  void* W = nullptr;
+  if (cudaMalloc(&x, sizeof(float) * std::max(1LL, p->n_in)) != cudaSuccess ||
+      cudaMalloc(&W, sizeof(float2) * std::max(1LL, p->n_in * S)) != cudaSuccess) {
+    cudaFree(x);
+    cudaFree(W);
+    cudaGetLastError();
+    return MORLET_OK;
+  }
+  int rc = MORLET_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const long long cand[][2] = {{LS_MAX_L, SS_MIN_L}, {0, SS_MIN_L},   {64, SS_MIN_L},
+                               {256, SS_MIN_L},      {LS_MAX_L, 2048}, {LS_MAX_L, 1024}};
+  long long best_ls = LS_MAX_L, best_ss = SS_MIN_L;
+  float best_ms = -1.f;
+  CK(cudaMemsetAsync(x, 0, sizeof(float) * std::max(1LL, p->n_in), st));
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (const auto& c : cand) {
+    p->ls_max_L = c[0];
+    p->ss_min_L = c[1];
+    long long slots = 0;
+    rc = build_forward(p, slots);
+    if (rc) goto fail;
+    if (slots > p->n_slots) continue;  // would need look-back slots the plan does not own
+    const long long ce = p->fwd.chain_end.empty() ? 0 : p->fwd.chain_end[0];
+    CK(enqueue(p, p->fwd, x, W, 0, p->fwd.n_work, ce, p->d_ticket, true, st));  // warm-up
+    CK(cudaEventRecord(e0, st));
+    for (int r = 0; r < 3; ++r) CK(enqueue(p, p->fwd, x, W, 0, p->fwd.n_work, ce, p->d_ticket, true, st));
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (p->h_err && *(volatile int*)p->h_err) {  // a timed-out wait: not a candidate
+      *(volatile int*)p->h_err = 0;
+      continue;
+    }
+    if (best_ms < 0.f || ms < best_ms) {
+      best_ms = ms;
+      best_ls = c[0];
+      best_ss = c[1];
+    }
+  }
+  p->ls_max_L = best_ls;
+  p->ss_min_L = best_ss;
+  {
+    long long slots = 0;
+    rc = build_forward(p, slots);
+  }
+fail:
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(x);
+  cudaFree(W);
+  return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -761,6 +859,10 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
     CK(cudaHostAlloc((void**)&p->h_err, sizeof(int), cudaHostAllocMapped));
     *p->h_err = 0;
     CK(cudaHostGetDevicePointer((void**)&p->d_err, p->h_err, 0));
+    if (d->flags & MORLET_FLAG_AUTOTUNE) {
+      rc = autotune(p, st);
+      if (rc) goto fail;
+    }
   }
   cudaFree(d_partial);
   *out = p;
@@ -845,7 +947,7 @@ int morlet_plan_info(morlet_plan_t p, int32_t s, int64_t* L, int32_t* p0, int32_
   return MORLET_OK;
 }
 
-int morlet_plan_stats(morlet_plan_t p, int64_t o[12]) {
+int morlet_plan_stats(morlet_plan_t p, int64_t o[14]) {
   if (!p || !o) return MORLET_ERR_ARG;
   const Launch& f = p->fwd;
   const bool two = f.func_w != nullptr;
@@ -863,6 +965,8 @@ int morlet_plan_stats(morlet_plan_t p, int64_t o[12]) {
   o[9] = f.n_pwork;
   o[10] = f.rows_lane;
   o[11] = f.n_lwork;
+  o[12] = p->ls_max_L;
+  o[13] = p->ss_min_L;
   return MORLET_OK;
 }
 

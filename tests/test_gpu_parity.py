@@ -151,6 +151,21 @@ def test_c2_chirps_forms(sigma, K):
     assert es < 1e-4
 
 
+def test_autotune_keeps_results():
+    """MORLET_FLAG_AUTOTUNE picks row thresholds by timing; whatever it picks, the transform is the
+    same to within the compensated-FP32 gate."""
+    rng = np.random.default_rng(77)
+    lens = [50000, 120000, 3000]
+    sigs = [rng.standard_normal(n).astype(np.float32) for n in lens]
+    sigmas = [8.0, 40.0, 300.0, 1500.0]
+    plan, out = gpu_forward(sigs, sigmas, K=4, flags=m.MORLET_FLAG_AUTOTUNE)
+    st = m.morlet_plan_stats(plan)
+    assert st["lane_chunk_max_L"] in (0, 64, 128, 256) and st["start_state_min_L"] in (1024, 2048, 4096)
+    for i, x in enumerate(sigs):
+        for s, sg in enumerate(sigmas):
+            assert rel_err(out[i][s], oracle_forward(x.astype(np.float64), sg, 4)) < 1e-5
+
+
 def test_deterministic_replay():
     """Two launches (graph replays) give bit-identical outputs."""
     x = WL.white(3, 300000)
