@@ -281,9 +281,9 @@ __global__ void __launch_bounds__(THREADS, C::K <= 4 ? 3 : 2) psum_kernel(const 
     float2 Gm[TPL];
 #pragma unroll
     for (int r = 0; r < TPL; ++r) Gm[r] = make_float2(0.f, 0.f);
-#pragma unroll
     if (lane == 0) prefetch_l2(xs, N, wi.t_a, wi.t_a + (int64_t)n_sub * PS_TILE);  // the chunk, into L2
-#pragma unroll
+    // (not unrolled: the unrolled chunk overflowed the instruction cache)
+#pragma unroll 1
     for (int k = 0; k < PS_CHUNK; ++k) {
       const int64_t t0 = wi.t_a + (int64_t)k * PS_TILE;
       if (k < n_sub && t0 < N && t0 + PS_TILE > 0) {  // warp-uniform
@@ -292,7 +292,9 @@ __global__ void __launch_bounds__(THREADS, C::K <= 4 ? 3 : 2) psum_kernel(const 
         float2 b[K];
         lane_sums<K, ITEMS>(xa, rho, lam, wl, b);
         const float2 g = warp_sum_scatter<K>(b, lane);
-        if (sl == k / TPL) Gm[k % TPL] = g;
+#pragma unroll
+        for (int r = 0; r < TPL; ++r)
+          if (sl * TPL + r == k) Gm[r] = g;
       }
     }
     // in-chunk prefix at each tile end (FP32): owner-local over its tiles, then a scan over the
