@@ -55,10 +55,14 @@ class Clocks:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.time()  # the sampler is running before the timed region starts
+            while not self.lines and time.time() - t0 < 5.0:
+                time.sleep(0.01)
+            self.lines.clear()
         except Exception:
             self.proc = None
 
@@ -92,34 +96,24 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def cpu_baseline(w, max_seconds=20.0, threads=0):
+def cpu_baseline(w, max_seconds=15.0, threads=0):
     """Time the oracle's O-SFT (double-double kernel integral) on the host cores, on a bounded sample:
-    whole (signal, scale) rows of the same batch, signals taken in order until the estimated CPU work
-    reaches about `max_seconds`."""
+    whole (signal, scale) rows of the same batch, signals taken in order in groups of 8 until about
+    `max_seconds` of wall time have been spent."""
     from oracle import morlet as om
     from oracle import sft_dd
     sft_dd.build()
     fits = [om.fit_direct(s, w.xi, w.K) for s in w.sigmas]
-    # calibrate on one small signal
-    order = np.argsort(w.lengths)
-    probe = [w.signals[int(order[len(order) // 4])]]
-    t = time.perf_counter()
-    _, used = sft_dd.sft_batch(probe, fits, threads)
-    dt = time.perf_counter() - t
-    rate = len(probe[0]) * len(fits) / max(dt, 1e-6)
-    budget = rate * max_seconds
-    sel, tot = [], 0
-    for i in range(len(w.signals)):
-        n = len(w.signals[i]) * len(fits)
-        if tot + n > budget and sel:
-            break
-        sel.append(w.signals[i])
-        tot += n
-    t = time.perf_counter()
-    _, used = sft_dd.sft_batch(sel, fits, threads)
-    dt = time.perf_counter() - t
+    done, tot, used, dt = 0, 0, 1, 0.0
+    while done < len(w.signals) and dt < max_seconds:
+        grp = w.signals[done:done + 8]
+        t = time.perf_counter()
+        _, used = sft_dd.sft_batch(grp, fits, threads)
+        dt += time.perf_counter() - t
+        tot += sum(len(x) for x in grp) * len(fits)
+        done += len(grp)
     return {"value": tot / dt, "unit": "output samples/s", "cores": int(used), "kind": "oracle",
-            "sample": f"first {len(sel)} of {len(w.signals)} signals x {len(fits)} scales "
+            "sample": f"first {done} of {len(w.signals)} signals x {len(fits)} scales "
                       f"({tot} outputs), double-double O-SFT, {dt:.1f} s"}
 
 
@@ -138,15 +132,18 @@ def run_reference(args, ws, rank):
     budget = max(1.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         cpu_baseline(w, max_seconds=min(budget, 5.0))
-    vals = []
+    vals, walls = [], []
     last = None
     for _ in range(args.steps):
+        t = time.perf_counter()
         last = cpu_baseline(w, max_seconds=budget)
+        walls.append(time.perf_counter() - t)
         vals.append(last["value"])
     v = statistics.median(vals)
-    line = {"impl": "reference", "metric": "Morlet output samples/s (scalogram, compensated FP32 path)",
+    line = {"impl": "reference", "metric": "Morlet output samples/s (batched scalogram, compensated FP32, % HBM roofline)",
             "value": v, "unit": "output samples/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(walls), "higher_is_better": True,
+            "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 (double-double)", "data": "synthetic",
             "config": {"workload": "c3_scalogram_256sig_32scales_K4 (bounded host sample per step)"},
             "cpu_baseline": {**last, "value": v},
@@ -157,7 +154,7 @@ def run_reference(args, ws, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", type=int, default=0)
