@@ -90,6 +90,29 @@ struct ScaleTab {
   float4 c_neg16[32][KMAX];   // rho^{-16 a}, a = 0..31, two-float complex (|rho| = 1)
   float4 c_neg1[16][KMAX];    // rho^{-b}, b = 0..15, two-float complex
   float2 f_shear[KMAX];       // (tan(beta p / 2), sin(beta p)): rho = e^{-i beta p} as three shears
+  // FP32 copies of rho, the combine weights, E and kappa (the FP32 kernels never convert from FP64:
+  // conversions run on GB300's narrow FP64 pipe)
+  float2 f_rho[KMAX];
+  float f_cM[KMAX], f_cL[KMAX];
+  float2 f_E;
+  float f_kappa;
+};
+
+// Table reads in the sample precision R (FP32 copies for the FP32 kernels).
+template <typename R> struct TabR;
+template <> struct TabR<float> {
+  __device__ static float2 rho(const ScaleTab* t, int j) { return t->f_rho[j]; }
+  __device__ static float cM(const ScaleTab* t, int j) { return t->f_cM[j]; }
+  __device__ static float cL(const ScaleTab* t, int j) { return t->f_cL[j]; }
+  __device__ static float2 E(const ScaleTab* t) { return t->f_E; }
+  __device__ static float kappa(const ScaleTab* t) { return t->f_kappa; }
+};
+template <> struct TabR<double> {
+  __device__ static double2 rho(const ScaleTab* t, int j) { return t->rho[j]; }
+  __device__ static double cM(const ScaleTab* t, int j) { return t->cM[j]; }
+  __device__ static double cL(const ScaleTab* t, int j) { return t->cL[j]; }
+  __device__ static double2 E(const ScaleTab* t) { return t->E; }
+  __device__ static double kappa(const ScaleTab* t) { return t->kappa; }
 };
 
 struct KParams {

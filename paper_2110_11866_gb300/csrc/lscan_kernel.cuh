@@ -113,8 +113,8 @@ __global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel
 #pragma unroll
     for (int j = 0; j < K; ++j) {
       sh[j] = __ldg(&tb->f_shear[j]);
-      cM[j] = (float)tb->cM[j];
-      cL[j] = (float)tb->cL[j];
+      cM[j] = tb->f_cM[j];
+      cL[j] = tb->f_cL[j];
       cx += cM[j];
     }
     // positions relative to the row fit in 32 bits (the plan keeps rows below 2^30 positions)

@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(THREADS, C::K <= 4 ? 3 : 2) psum_kernel(const 
     float lam[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-      rho[j] = to_f2(tb->rho[j]);
+      rho[j] = tb->f_rho[j];
       wl[j] = __ldg(&tb->f_pw_lane[31 - lane][j]);  // rho^{16 (31 - lane)}
       lam[j] = __ldg(&tb->f_lam[j]);
     }

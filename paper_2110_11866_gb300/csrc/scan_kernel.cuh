@@ -234,9 +234,9 @@ __global__ void __launch_bounds__(THREADS, C::MINB) scan_kernel(const KParams P)
     if (wi.scale != s.cur_scale) {  // stage this scale's constants (uniform branch)
       const ScaleTab* tb = P.tabs + wi.scale;
       for (int i = tid; i < K; i += THREADS) {
-        s.rho[i] = conv2<V>(tb->rho[i]);
-        s.cM[i] = (R)tb->cM[i];
-        s.cL[i] = (C::OUT == OUT_ADJ) ? (R)(-tb->cL[i]) : (R)tb->cL[i];
+        s.rho[i] = TabR<R>::rho(tb, i);
+        s.cM[i] = TabR<R>::cM(tb, i);
+        s.cL[i] = (C::OUT == OUT_ADJ) ? -TabR<R>::cL(tb, i) : TabR<R>::cL(tb, i);
       }
       for (int i = tid; i < 5 * K; i += THREADS) s.pw_thr[i / K][i % K] = conv2<V>(tb->pw_thr[i / K][i % K]);
       for (int i = tid; i < 32 * K; i += THREADS) s.pw_lane[i / K][i % K] = conv2<V>(tb->pw_lane[i / K][i % K]);
@@ -246,8 +246,8 @@ __global__ void __launch_bounds__(THREADS, C::MINB) scan_kernel(const KParams P)
       }
       for (int i = tid; i < 33 * K; i += THREADS) s.pw_tile_c[i / K][i % K] = CO::from_d2(tb->pw_tile[i / K][i % K]);
       if (tid == 0) {
-        s.E = conv2<V>(tb->E);
-        s.kappa = (R)tb->kappa;
+        s.E = TabR<R>::E(tb);
+        s.kappa = TabR<R>::kappa(tb);
         s.L = tb->L;
         s.D = tb->D;
         s.p0 = tb->p0;

@@ -266,6 +266,8 @@ __global__ void build_tables(ScaleTab* tabs, const FitJob* jobs, int n_scales, i
     const int j = idx % K_kernel, mm = idx / K_kernel;
     tb.c_pw_chunk[mm][j] = dfc4(power((long long)tb.p0 + j, (long long)items * 32 * (mm + 1)));
   }
+  for (int j = threadIdx.x; j < KMAX; j += blockDim.x)
+    tb.f_rho[j] = j < K_kernel ? make_float2((float)tb.rho[j].x, (float)tb.rho[j].y) : make_float2(0.f, 0.f);
   for (int idx = threadIdx.x; idx < K_kernel * (5 + 32 + 1); idx += blockDim.x) {
     const int j = idx % K_kernel;
     const int q = idx / K_kernel;
@@ -299,7 +301,11 @@ __global__ void build_tables(ScaleTab* tabs, const FitJob* jobs, int n_scales, i
       const double sg = ((tb.p0 + j) & 1) ? -1.0 : 1.0;  // (-1)^p: c_p - i s_p = (-1)^p V[n + L]
       tb.cM[j] = gain * sg * tb.m[j];
       tb.cL[j] = -gain * sg * tb.l[j];
+      tb.f_cM[j] = (float)tb.cM[j];
+      tb.f_cL[j] = (float)tb.cL[j];
     }
+    tb.f_E = make_float2((float)tb.E.x, (float)tb.E.y);
+    tb.f_kappa = (float)tb.kappa;
   }
 }
 

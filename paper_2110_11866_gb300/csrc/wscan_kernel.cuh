@@ -151,15 +151,15 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
     const ScaleTab* tb = P.tabs + wi.scale;
     const int64_t L = tb->L, D = tb->D;
     const int64_t Wl = GF ? 2 * L : 2 * L + 1;  // lag of the second input stream
-    const R kap = (R)tb->kappa;
+    const R kap = TabR<R>::kappa(tb);
     V rho[K], pn[GF ? K : 1];
     R cM[K], cL[K];
     R cx = 0;
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-      rho[j] = conv2<V>(tb->rho[j]);
-      cM[j] = (R)tb->cM[j];
-      cL[j] = (C::OUT == OUT_ADJ) ? (R)(-tb->cL[j]) : (R)tb->cL[j];
+      rho[j] = TabR<R>::rho(tb, j);
+      cM[j] = TabR<R>::cM(tb, j);
+      cL[j] = (C::OUT == OUT_ADJ) ? -TabR<R>::cL(tb, j) : TabR<R>::cL(tb, j);
       cx += cM[j];
       if constexpr (GF) {  // conj(rho^{ITEMS (lane + 1)}) = rho^{-ITEMS (lane + 1)}
         const V q = cmul(pw_lane<V>(tb, lane, j), pw_thr<V>(tb, 0, j));
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
         pn[j].y = -q.y;
       }
     }
-    const V E = conv2<V>(tb->E);
+    const V E = TabR<R>::E(tb);
     const EIn* __restrict__ xs = reinterpret_cast<const EIn*>(P.x) + wi.x_off;
     const int64_t N = wi.n;
     const int64_t lo = wi.t_dom;
