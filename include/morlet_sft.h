@@ -157,10 +157,11 @@ int morlet_plan_info(morlet_plan_t plan, int32_t s, int64_t* L, int32_t* p0, int
  * out[5] = rows in look-back mode, out[6] = rows in window-segment mode, out[7] = kernel launches
  * per forward, out[8] = rows whose work items start from prefix sums, out[9] = prefix-sum work items,
  * out[10] = rows in lane-chunk mode, out[11] = lane-chunk work items, out[12] / out[13] = the row
- * thresholds in use (rows with L <= out[12] take the lane-chunk scan, rows with L > out[13] start
- * from prefix sums).
+ * thresholds in use (rows with L <= out[12] take the lane-chunk scan, rows with L > out[13] take
+ * start-state items), out[14] = 1 when those start states are window sums of tile sums, 0 when they
+ * come from prefix sums.
  */
-int morlet_plan_stats(morlet_plan_t plan, int64_t out[14]);
+int morlet_plan_stats(morlet_plan_t plan, int64_t out[15]);
 
 /*
  * morlet_plan_set_spin_limit - change the bounded-wait limit (polls) of later launches; used to make
@@ -170,10 +171,10 @@ int morlet_plan_set_spin_limit(morlet_plan_t plan, int64_t polls);
 
 /*
  * morlet_debug_skip_tickets - testing hook: in the next forward, the first kernel that waits on
- * predecessors (the prefix-sum kernel when the plan has start-state rows, else the look-back scan
- * kernel) starts its work-item counter at `skip` instead of 0, so its first `skip` work items are
- * never processed and items that wait on them hit the bounded wait. The outputs of that forward are
- * undefined. Must be followed by morlet_last_device_error.
+ * predecessors (the prefix-sum kernel when the plan's start states come from prefix sums, else the
+ * look-back scan kernel) starts its work-item counter at `skip` instead of 0, so its first `skip`
+ * work items are never processed and items that wait on them hit the bounded wait. The outputs of
+ * that forward are undefined. Must be followed by morlet_last_device_error.
  */
 int morlet_debug_skip_tickets(morlet_plan_t plan, int64_t skip);
 

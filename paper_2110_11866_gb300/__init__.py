@@ -217,11 +217,11 @@ def morlet_plan_info(plan: Plan, s: int) -> dict:
 
 
 def morlet_plan_stats(plan: Plan) -> dict:
-    o = (ctypes.c_int64 * 14)()
+    o = (ctypes.c_int64 * 15)()
     _check(lib().morlet_plan_stats(plan.handle, o), "morlet_plan_stats")
     keys = ["threads", "items", "ctas", "work_items", "sub_tiles", "rows_lookback", "rows_window", "launches",
             "rows_start_state", "prefix_items", "rows_lane_chunk", "lane_chunk_items", "lane_chunk_max_L",
-            "start_state_min_L"]
+            "start_state_min_L", "start_state_window_sums"]
     return dict(zip(keys, list(o)))
 
 

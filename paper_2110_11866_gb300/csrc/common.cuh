@@ -90,6 +90,7 @@ struct ScaleTab {
   float4 c_neg16[32][KMAX];   // rho^{-16 a}, a = 0..31, two-float complex (|rho| = 1)
   float4 c_neg1[16][KMAX];    // rho^{-b}, b = 0..15, two-float complex
   float2 f_shear[KMAX];       // (tan(beta p / 2), sin(beta p)): rho = e^{-i beta p} as three shears
+  float2 f_pw512[17][KMAX];   // rho^{512 m}, m = 0..16, FP32
   // FP32 copies of rho, the combine weights, E and kappa (the FP32 kernels never convert from FP64:
   // conversions run on GB300's narrow FP64 pipe)
   float2 f_rho[KMAX];
@@ -130,7 +131,9 @@ struct KParams {
   long long spin_limit;
   int64_t n_chain;           // work items [0, n_chain) use the look-back; later ones are independent
   int64_t n_x;               // elements of the input buffer (bounds the widened loads)
-  void* pbuf;                // lag-free prefix sums at tile ends: per tile, K two-float complex
+  void* pbuf;                // start-state rows: per 512-position tile, K two-float complex prefix
+                             // sums (ss_window = 0) or K FP32 complex tile sums (ss_window = 1)
+  int ss_window;             // start states from window sums of tile sums instead of prefix sums
   int accumulate;            // adjoint: add to the output instead of overwriting it
 };
 

@@ -1,4 +1,5 @@
-// Prefix-sum kernel instantiations (compensated FP32, real input): `const void* kernel_psum(int K)`.
+// Prefix-sum and tile-sum kernel instantiations (compensated FP32, real input):
+// `const void* kernel_psum(int K)`, `const void* kernel_tsum(int K)`.
 #include "kernels_inst.cuh"
 
 namespace msft {
@@ -10,6 +11,20 @@ const void* kernel_psum(int K) {
     case 6: return (const void*)&psum_kernel<Cfg<float, DFC, 6, FORM_RF, OUT_MORLET, false, 16>>;
     case 8: return (const void*)&psum_kernel<Cfg<float, DFC, 8, FORM_RF, OUT_MORLET, false, 16>>;
     case 12: return (const void*)&psum_kernel<Cfg<float, DFC, 12, FORM_RF, OUT_MORLET, false, 16>>;
+    default: return nullptr;
+  }
+}
+}  // namespace msft
+
+namespace msft {
+const void* kernel_tsum(int K) {
+  switch (K) {
+    case 2: return (const void*)&tsum_kernel<Cfg<float, DFC, 2, FORM_RF, OUT_MORLET, false, 16>>;
+    case 3: return (const void*)&tsum_kernel<Cfg<float, DFC, 3, FORM_RF, OUT_MORLET, false, 16>>;
+    case 4: return (const void*)&tsum_kernel<Cfg<float, DFC, 4, FORM_RF, OUT_MORLET, false, 16>>;
+    case 6: return (const void*)&tsum_kernel<Cfg<float, DFC, 6, FORM_RF, OUT_MORLET, false, 16>>;
+    case 8: return (const void*)&tsum_kernel<Cfg<float, DFC, 8, FORM_RF, OUT_MORLET, false, 16>>;
+    case 12: return (const void*)&tsum_kernel<Cfg<float, DFC, 12, FORM_RF, OUT_MORLET, false, 16>>;
     default: return nullptr;
   }
 }

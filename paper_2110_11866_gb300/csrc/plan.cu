@@ -94,6 +94,7 @@ struct Launch {
   long long n_pwork = 0;
   int grid_p = 0;
   long long n_pslots = 0, n_ptiles = 0, rows_ss = 0;
+  int ss_window = 0;  // start states from window sums of tile sums (tsum kernel) instead of prefix sums
   // lane-chunk rows (forward, compensated FP32 Morlet, short windows): items d_lwork
   const void* func_l = nullptr;
   WorkItem* d_lwork = nullptr;
@@ -245,6 +246,12 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
     ss_total += kE - kD + 1;
   }
   const long long n_ss = std::max(4LL, std::min(32LL, ss_total / std::max(1LL, 4 * warp_slots)));
+  // A start state costs a window sum over its 2L / 512 tiles: cheap next to an item of n_ss tiles
+  // unless the window is much longer; then the prefix sums (one chained pass) are used instead.
+  long long max_win = 0;
+  for (auto& rs : order)
+    if (ss_row(p, adjoint, p->h_tabs[rs.second])) max_win = std::max<long long>(max_win, 2 * p->h_tabs[rs.second].L / PS_TILE_H + 2);
+  ln.ss_window = (max_win <= 16 * n_ss) ? 1 : 0;
   ln.scale_begin.assign(S + 1, 0);
   int prev_scale = -1;
   for (auto& rs : order) {
@@ -403,7 +410,7 @@ int setup_launch(morlet_plan_s* p, bool adjoint, Launch& ln, long long& slots) {
     ln.grid = (int)std::min<long long>((long long)occ * p->sms, std::max<long long>(1, ln.n_work));
   }
   if (!pwork.empty()) {
-    ln.func_p = kernel_psum(p->K_kernel);
+    ln.func_p = ln.ss_window ? kernel_tsum(p->K_kernel) : kernel_psum(p->K_kernel);
     if (!ln.func_p) return MORLET_ERR_UNSUPPORTED;
     int occp = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occp, ln.func_p, THREADS, 0));
@@ -473,7 +480,7 @@ cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out
   if (e == cudaSuccess && p->skip_tickets > 0) {
     // testing hook: skip the first work items of the first look-back kernel of this launch
     const unsigned long long v = (unsigned long long)p->skip_tickets;
-    const int at = (w_end > s_beg && ln.n_pwork > 0) ? 3 : 0;
+    const int at = (w_end > s_beg && ln.n_pwork > 0 && !ln.ss_window) ? 3 : 0;
     e = cudaMemcpyAsync(tickets + at, &v, sizeof(v), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     p->skip_tickets = 0;
@@ -530,8 +537,10 @@ cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out
   }
   if (two && w_end > s_beg) {
     if (ln.n_pwork > 0) {
-      e = cudaMemsetAsync(p->d_pflags, 0, sizeof(uint32_t) * ln.n_pslots, st);
-      if (e != cudaSuccess) return e;
+      if (!ln.ss_window) {
+        e = cudaMemsetAsync(p->d_pflags, 0, sizeof(uint32_t) * ln.n_pslots, st);
+        if (e != cudaSuccess) return e;
+      }
       KParams kq = kp;
       kq.work = ln.d_pwork;
       kq.n_work = ln.n_pwork;
@@ -550,6 +559,7 @@ cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out
     ks.n_work = w_end - s_beg;
     ks.n_chain = 0;
     ks.ticket = tickets + 2;
+    ks.ss_window = ln.ss_window;
     void* args[] = {&ks};
     const int grid = (int)std::min<long long>(ln.grid_w, (ks.n_work + WARPS - 1) / WARPS);
     e = cudaLaunchKernel(ln.func_w, dim3(grid), dim3(THREADS), args, 0, st);
@@ -567,6 +577,25 @@ cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out
   }
   if (forked) e = cudaStreamWaitEvent(st, p->ev_join, 0);
   return e;
+}
+
+// Workspace of the start-state rows: tile sums (K FP32 complex per tile) in window mode; prefix sums
+// (K two-float complex per tile) plus the look-back status, aggregates and inclusive values otherwise.
+int alloc_prefix(morlet_plan_s* p) {
+  int rc = MORLET_OK;
+  const Launch& f = p->fwd;
+  if (f.ss_window) {
+    CK(cudaMalloc(&p->d_pbuf, sizeof(float2) * p->K_kernel * std::max(1LL, f.n_ptiles)));
+  } else {
+    const size_t kb = sizeof(float4) * p->K_kernel;  // K two-float complex values
+    CK(cudaMalloc(&p->d_pflags, sizeof(uint32_t) * f.n_pslots));
+    CK(cudaMalloc(&p->d_pagg, kb * f.n_pslots));
+    CK(cudaMalloc(&p->d_pincl, kb * f.n_pslots));
+    CK(cudaMalloc(&p->d_pbuf, kb * std::max(1LL, f.n_ptiles)));
+  }
+  return MORLET_OK;
+fail:
+  return rc;
 }
 
 // (Re)build the forward launch and its prefix-sum workspace for the plan's current row thresholds
@@ -588,16 +617,8 @@ int build_forward(morlet_plan_s* p, long long& slots) {
   slots = 0;
   rc = setup_launch(p, false, p->fwd, slots);
   if (rc) return rc;
-  if (p->fwd.n_pwork > 0) {
-    const size_t kb = sizeof(float4) * p->K_kernel;  // K two-float complex values
-    CK(cudaMalloc(&p->d_pflags, sizeof(uint32_t) * p->fwd.n_pslots));
-    CK(cudaMalloc(&p->d_pagg, kb * p->fwd.n_pslots));
-    CK(cudaMalloc(&p->d_pincl, kb * p->fwd.n_pslots));
-    CK(cudaMalloc(&p->d_pbuf, kb * std::max(1LL, p->fwd.n_ptiles)));
-  }
+  if (p->fwd.n_pwork > 0) return alloc_prefix(p);
   return MORLET_OK;
-fail:
-  return rc;
 }
 
 // MORLET_FLAG_AUTOTUNE: time the forward of this plan's batch (zero input, scratch output) under a
@@ -846,11 +867,8 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
       CK(cudaMalloc(&p->d_incl, carry_bytes(p) * nt_adj * p->n_slots));
     }
     if (p->fwd.n_pwork > 0) {
-      const size_t kb = sizeof(float4) * p->K_kernel;  // K two-float complex values
-      CK(cudaMalloc(&p->d_pflags, sizeof(uint32_t) * p->fwd.n_pslots));
-      CK(cudaMalloc(&p->d_pagg, kb * p->fwd.n_pslots));
-      CK(cudaMalloc(&p->d_pincl, kb * p->fwd.n_pslots));
-      CK(cudaMalloc(&p->d_pbuf, kb * std::max(1LL, p->fwd.n_ptiles)));
+      rc = alloc_prefix(p);
+      if (rc) goto fail;
     }
     CK(cudaMalloc(&p->d_ticket, sizeof(unsigned long long) * TICKETS * (S + 1)));
     CK(cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking));
@@ -947,7 +965,7 @@ int morlet_plan_info(morlet_plan_t p, int32_t s, int64_t* L, int32_t* p0, int32_
   return MORLET_OK;
 }
 
-int morlet_plan_stats(morlet_plan_t p, int64_t o[14]) {
+int morlet_plan_stats(morlet_plan_t p, int64_t o[15]) {
   if (!p || !o) return MORLET_ERR_ARG;
   const Launch& f = p->fwd;
   const bool two = f.func_w != nullptr;
@@ -967,6 +985,7 @@ int morlet_plan_stats(morlet_plan_t p, int64_t o[14]) {
   o[11] = f.n_lwork;
   o[12] = p->ls_max_L;
   o[13] = p->ss_min_L;
+  o[14] = f.ss_window;
   return MORLET_OK;
 }
 

@@ -245,6 +245,115 @@ __device__ __forceinline__ void start_state(const KParams& P, const WorkItem& wi
   }
 }
 
+// State entering a start-state item from a window sum of stored tile sums (used when the window
+// spans few tiles compared with the item): with b = wi.t_a a tile start and u0 = b - 2L,
+//     G(b - 1) = sum_{k = k0}^{kb - 1} rho^{512 (kb - 1 - k)} G_k,
+// G_k the FP32 tile sums sum_{u in tile k} rho^{e_k - u} x[u] (tsum_kernel), except that the tile
+// k0 holding u0 contributes only its samples from u0 on (a masked tile sum computed here). The lanes
+// of a term's group take the window's tiles in turn with FP32 running powers of rho^{512}.
+template <int K, int ITEMS>
+__device__ __forceinline__ void start_state_window(const KParams& P, const WorkItem& wi, const ScaleTab* tb,
+                                                   const float2 (&rho)[K], int lane, float2 (&Cw)[K]) {
+  constexpr int G = KPad<K>::G;
+  const int tl = lane / G, sl = lane % G, tq = tl < K ? tl : 0;
+  const int64_t L = tb->L;
+  const int64_t kb = (wi.t_a - wi.t_grid) / PS_TILE;
+  const int64_t u0 = wi.t_a - 2 * L;
+  int64_t k0 = 0;
+  float2 gp = make_float2(0.f, 0.f);  // masked sum of tile k0 for this lane's term
+  bool partial = false;
+  if (u0 > wi.t_grid) {  // warp-uniform
+    k0 = (u0 - wi.t_grid) / PS_TILE;
+    const int64_t a0 = wi.t_grid + k0 * PS_TILE;
+    if (u0 > a0) {
+      partial = true;
+      const float* __restrict__ xs = reinterpret_cast<const float*>(P.x) + wi.x_off;
+      float xa[ITEMS];
+      load_run<float, ITEMS>(xs, a0 + (int64_t)lane * ITEMS, u0 > 0 ? u0 : 0, wi.n, xa);
+      float2 wl[K], b[K];
+      float lam[K];
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        wl[j] = __ldg(&tb->f_pw_lane[31 - lane][j]);
+        lam[j] = __ldg(&tb->f_lam[j]);
+      }
+      lane_sums<K, ITEMS>(xa, rho, lam, wl, b);
+      gp = warp_sum_scatter<K>(b, lane);
+    }
+  }
+  const float2* gb = reinterpret_cast<const float2*>(P.pbuf) + wi.p_row * K;
+  const float2 step = __ldg(&tb->f_pw512[G][tq]);  // rho^{512 G}
+  float2 w = __ldg(&tb->f_pw512[sl][tq]);           // rho^{512 m} for m = sl
+  float2 acc = make_float2(0.f, 0.f);
+  const int64_t n_t = kb - k0;  // tiles k0 .. kb - 1
+  for (int64_t m0 = 0; m0 < n_t; m0 += G) {
+    const int64_t m = m0 + sl, k = kb - 1 - m;
+    if (m < n_t && tl < K) {
+      const float2 v = (partial && k == k0) ? gp : gb[k * K + tl];
+      acc = cfma(w, v, acc);
+    }
+    w = cmul(w, step);
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  }
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    Cw[j].x = __shfl_sync(0xffffffffu, acc.x, j * G);
+    Cw[j].y = __shfl_sync(0xffffffffu, acc.y, j * G);
+  }
+}
+
+// Tile sums only: G_k = sum_{u in tile k} rho^{e_k - u} x[u] for the tiles of a chunk, FP32, stored
+// for start_state_window. No look-back, no prefix: chunks are independent.
+template <class C>
+__global__ void __launch_bounds__(THREADS, C::K <= 4 ? 3 : 2) tsum_kernel(const KParams P) {
+  static_assert(std::is_same<typename C::R, float>::value && C::CH == 1 && C::ITEMS == 16,
+                "tile sums are built for the FP32 real-input kernels");
+  constexpr int K = C::K, ITEMS = C::ITEMS;
+  constexpr int G = KPad<K>::G;
+  const int lane = threadIdx.x & 31;
+  const int tl = lane / G, sl = lane % G;
+
+  long long w = 0;
+  if (lane == 0) w = (long long)atomicAdd(P.ticket, 1ull);
+  w = __shfl_sync(0xffffffffu, w, 0);
+  while (w < P.n_work) {
+    const WorkItem wi = P.work[w];
+    long long w2 = 0;  // chunks are independent: claim the next one now
+    if (lane == 0) w2 = (long long)atomicAdd(P.ticket, 1ull);
+    const ScaleTab* tb = P.tabs + wi.scale;
+    float2 rho[K], wl[K];
+    float lam[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      rho[j] = tb->f_rho[j];
+      wl[j] = __ldg(&tb->f_pw_lane[31 - lane][j]);
+      lam[j] = __ldg(&tb->f_lam[j]);
+    }
+    const float* __restrict__ xs = reinterpret_cast<const float*>(P.x) + wi.x_off;
+    const int64_t N = wi.n;
+    float2* gb = reinterpret_cast<float2*>(P.pbuf) + wi.p_row * K;
+    if (lane == 0) prefetch_l2(xs, N, wi.t_a, wi.t_a + (int64_t)wi.n_sub * PS_TILE);
+#pragma unroll 1
+    for (int k = 0; k < wi.n_sub; ++k) {
+      const int64_t t0 = wi.t_a + (int64_t)k * PS_TILE;
+      float2 g = make_float2(0.f, 0.f);
+      if (t0 < N && t0 + PS_TILE > 0) {  // warp-uniform
+        float xa[ITEMS];
+        load_run<float, ITEMS>(xs, t0 + (int64_t)lane * ITEMS, 0, N, xa);
+        float2 b[K];
+        lane_sums<K, ITEMS>(xa, rho, lam, wl, b);
+        g = warp_sum_scatter<K>(b, lane);
+      }
+      if (sl == 0 && tl < K) gb[(int64_t)k * K + tl] = g;
+    }
+    w = __shfl_sync(0xffffffffu, w2, 0);
+  }
+}
+
 template <class C>
 __global__ void __launch_bounds__(THREADS, C::K <= 4 ? 3 : 2) psum_kernel(const KParams P) {
   static_assert(std::is_same<typename C::R, float>::value && C::CH == 1 && C::ITEMS == 16,

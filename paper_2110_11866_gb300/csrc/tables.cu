@@ -268,6 +268,11 @@ __global__ void build_tables(ScaleTab* tabs, const FitJob* jobs, int n_scales, i
   }
   for (int j = threadIdx.x; j < KMAX; j += blockDim.x)
     tb.f_rho[j] = j < K_kernel ? make_float2((float)tb.rho[j].x, (float)tb.rho[j].y) : make_float2(0.f, 0.f);
+  for (int idx = threadIdx.x; idx < K_kernel * 17; idx += blockDim.x) {
+    const int j = idx % K_kernel, mm = idx / K_kernel;
+    const double2 v = power((long long)tb.p0 + j, 512LL * mm);
+    tb.f_pw512[mm][j] = make_float2((float)v.x, (float)v.y);
+  }
   for (int idx = threadIdx.x; idx < K_kernel * (5 + 32 + 1); idx += blockDim.x) {
     const int j = idx % K_kernel;
     const int q = idx / K_kernel;

@@ -178,7 +178,10 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
 #pragma unroll
     for (int v = 0; v < NT; ++v) Cw[v] = V{};
     if constexpr (C::START) {
-      if (wi.p_row >= 0) start_state<K, ITEMS>(P, wi, tb, rho, lane, Cw);
+      if (wi.p_row >= 0) {
+        if (P.ss_window) start_state_window<K, ITEMS>(P, wi, tb, rho, lane, Cw);
+        else start_state<K, ITEMS>(P, wi, tb, rho, lane, Cw);
+      }
     }
 
     for (int k = 0; k < wi.n_sub; ++k) {

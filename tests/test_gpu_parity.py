@@ -80,17 +80,21 @@ def test_lane_chunk_rows_and_unaligned_buffers(K, shift):
 
 
 @pytest.mark.parametrize("K", [3, 4, 6])
-def test_start_state_rows(K):
-    """Long windows in compensated FP32: work items start from the lag-free prefix sums (several
-    chunks per row, every input alignment mod 16 bytes, rows shorter than a tile, shorter than the
-    window, and rows spanning many work items), next to short-window rows of the same plan."""
+@pytest.mark.parametrize("longest", [4000.0, 9000.0])
+def test_start_state_rows(K, longest):
+    """Long windows in compensated FP32: work items start from exact states (several chunks per row,
+    every input alignment mod 16 bytes, rows shorter than a tile, shorter than the window, and rows
+    spanning many work items), next to short-window rows of the same plan. With the longest sigma
+    4000 the states are window sums of tile sums; with 9000 (windows of 141 tiles against items of
+    4 tiles) they come from the chained prefix sums."""
     rng = np.random.default_rng(300 + K)
     lens = [100000, 3, 50001, 262149, 1030, 77777]
     sigs = [rng.standard_normal(n).astype(np.float32) for n in lens]
-    sigmas = [20.0, 255.0, 1030.0, 2000.0, 9000.0]
+    sigmas = [20.0, 255.0, 1030.0, 2000.0, longest]
     plan, out = gpu_forward(sigs, sigmas, K=K, precision=m.MORLET_FP32_COMP)
     st = m.morlet_plan_stats(plan)
     assert st["rows_start_state"] == len(lens) * 3 and st["prefix_items"] > 0
+    assert st["start_state_window_sums"] == (1 if longest < 5000 else 0)
     worst = 0.0
     for i, x in enumerate(sigs):
         for s, sg in enumerate(sigmas):
@@ -203,9 +207,9 @@ def test_prefix_sum_timeout_is_reported_and_context_survives():
     window whose work items start from prefix sums)."""
     import torch
     x = WL.white(5, 300000)
-    plan = m.morlet_plan([len(x)], [3000.0], K=4, precision=m.MORLET_FP32_COMP, flags=m.MORLET_FLAG_NO_GRAPH)
+    plan = m.morlet_plan([len(x)], [6000.0], K=4, precision=m.MORLET_FP32_COMP, flags=m.MORLET_FLAG_NO_GRAPH)
     st = m.morlet_plan_stats(plan)
-    assert st["rows_start_state"] == 1 and st["prefix_items"] > 2
+    assert st["rows_start_state"] == 1 and st["prefix_items"] > 2 and st["start_state_window_sums"] == 0
     m.morlet_plan_set_spin_limit(plan, 2000)
     xt = torch.from_numpy(x).cuda()
     W = torch.empty(len(x), dtype=torch.complex64, device="cuda")
@@ -214,5 +218,5 @@ def test_prefix_sum_timeout_is_reported_and_context_survives():
     assert m.morlet_last_device_error(plan) == m.MORLET_ERR_TIMEOUT
     m.morlet_forward(plan, xt, W)
     assert m.morlet_last_device_error(plan) == 0
-    ref = oracle_forward(x, 3000.0, 4)
+    ref = oracle_forward(x, 6000.0, 4)
     assert rel_err(W.cpu().numpy(), ref) < 1e-5
