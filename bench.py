@@ -165,6 +165,9 @@ def main():
                     help="c3: the full batched scalogram; c3_small: 64 signals clipped to 65536 samples (profiling)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default row thresholds instead of timing them at plan time")
+    ap.add_argument("--thresholds", default=None,
+                    help="LS:SS sets the row thresholds (lane-chunk rows L <= LS, start-state rows L > SS) "
+                         "instead of autotuning them; profiling runs pass the pair the autotuner keeps")
     ap.add_argument("--scales", default=None,
                     help="a:b keeps scales a..b-1 of the workload (profiling one kernel's rows); default all")
     args = ap.parse_args()
@@ -192,9 +195,14 @@ def main():
     x_host = torch.from_numpy(w.concat()).pin_memory()
     x = x_host.to(dev)
     t_plan = time.perf_counter()
+    tune = not args.no_autotune and args.thresholds is None
     plan = m.morlet_plan(lens, sigmas, xi=w.xi, K=w.K, precision=m.MORLET_FP32_COMP, form=args.form,
-                         flags=0 if args.no_autotune else m.MORLET_FLAG_AUTOTUNE)
+                         flags=m.MORLET_FLAG_AUTOTUNE if tune else 0)
+    if args.thresholds:
+        ls_max, ss_min = (int(v) for v in args.thresholds.split(":"))
+        m.morlet_plan_set_row_thresholds(plan, ls_max, ss_min)
     t_plan = time.perf_counter() - t_plan
+    pst = m.morlet_plan_stats(plan)
     W = torch.empty(n_out, dtype=torch.complex64, device=dev)
     st = torch.cuda.Stream(dev)
 
@@ -304,7 +312,9 @@ def main():
                        "l2": f"inputs {4 * sum(lens) / 1e6:.0f} MB + outputs {8 * n_out / 1e9:.2f} GB per step "
                              "exceed the 129 MB L2 (no flush between steps)",
                        "parallelism": f"replicas x{ws}", "plan_seconds": round(t_plan, 2),
-                       "autotune": not args.no_autotune},
+                       "autotune": tune,
+                       "row_thresholds": {"lane_chunk_max_L": pst["lane_chunk_max_L"],
+                                          "start_state_min_L": pst["start_state_min_L"]}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "forward step (lane-chunk, warp-scan and prefix-sum kernels, one graph)",

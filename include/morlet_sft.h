@@ -170,6 +170,19 @@ int morlet_plan_stats(morlet_plan_t plan, int64_t out[15]);
 int morlet_plan_set_spin_limit(morlet_plan_t plan, int64_t polls);
 
 /*
+ * morlet_plan_set_row_thresholds - choose which rows of a compensated-FP32 rotating-form SFT
+ * forward take the lane-chunk scan (L <= lane_chunk_max_L; 0: none) and which take start-state
+ * work items (L > start_state_min_L; 0: none), the two choices MORLET_FLAG_AUTOTUNE makes by
+ * timing; other plans keep their single schedule and ignore the values. The transform is the same
+ * for every choice (each row gate holds); only the schedule changes. Rebuilds the forward's work
+ * tables synchronously (device memory is freed and allocated, so no forward of this plan may be in
+ * flight). Errors: MORLET_ERR_ARG for a negative value; MORLET_ERR_UNSUPPORTED when the choice needs
+ * more look-back slots than the plan allocated (the plan keeps its previous thresholds);
+ * MORLET_ERR_TIMEOUT if an earlier launch timed out and its error word was not read yet.
+ */
+int morlet_plan_set_row_thresholds(morlet_plan_t plan, int64_t lane_chunk_max_L, int64_t start_state_min_L);
+
+/*
  * morlet_debug_skip_tickets - testing hook: in the next forward, the first kernel that waits on
  * predecessors (the prefix-sum kernel when the plan's start states come from prefix sums, else the
  * look-back scan kernel) starts its work-item counter at `skip` instead of 0, so its first `skip`

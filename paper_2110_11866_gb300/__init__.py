@@ -20,7 +20,7 @@ __all__ = [
     "morlet_plan", "morlet_forward", "morlet_backward", "gauss_smooth", "morlet_plan_destroy",
     "morlet_strerror", "morlet_last_device_error", "morlet_plan_info", "morlet_plan_stats",
     "morlet_plan_set_spin_limit", "morlet_debug_skip_tickets", "EXPORTED_SYMBOLS", "source_hash",
-    "morlet_forward_noalloc",
+    "morlet_forward_noalloc", "morlet_plan_set_row_thresholds",
 ]
 
 MORLET_OK, MORLET_ERR_ARG, MORLET_ERR_UNSUPPORTED, MORLET_ERR_CUDA, MORLET_ERR_TIMEOUT, MORLET_ERR_NOMEM = (
@@ -35,6 +35,7 @@ EXPORTED_SYMBOLS = [
     "morlet_plan", "morlet_forward", "morlet_backward", "gauss_smooth", "morlet_plan_destroy",
     "morlet_strerror", "morlet_last_device_error", "morlet_plan_info", "morlet_plan_stats",
     "morlet_plan_set_spin_limit", "morlet_debug_skip_tickets", "morlet_forward_noalloc",
+    "morlet_plan_set_row_thresholds",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -101,10 +102,11 @@ def lib():
     L.morlet_plan_stats.argtypes = [vp, ctypes.POINTER(i64)]
     L.morlet_plan_set_spin_limit.argtypes = [vp, i64]
     L.morlet_debug_skip_tickets.argtypes = [vp, i64]
+    L.morlet_plan_set_row_thresholds.argtypes = [vp, i64, i64]
     L.morlet_forward_noalloc.argtypes = [vp, i64, ctypes.c_double, ctypes.c_double, i32, vp, vp]
     for f in ("morlet_plan", "morlet_forward", "morlet_backward", "gauss_smooth", "morlet_last_device_error",
               "morlet_plan_info", "morlet_plan_stats", "morlet_plan_set_spin_limit", "morlet_debug_skip_tickets",
-              "morlet_forward_noalloc"):
+              "morlet_forward_noalloc", "morlet_plan_set_row_thresholds"):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
@@ -227,6 +229,13 @@ def morlet_plan_stats(plan: Plan) -> dict:
 
 def morlet_plan_set_spin_limit(plan: Plan, polls: int):
     _check(lib().morlet_plan_set_spin_limit(plan.handle, int(polls)), "morlet_plan_set_spin_limit")
+
+
+def morlet_plan_set_row_thresholds(plan: Plan, lane_chunk_max_L: int, start_state_min_L: int):
+    """Rows with L <= lane_chunk_max_L take the lane-chunk scan, rows with L > start_state_min_L
+    start from exact states (0 turns either off); compensated-FP32 rotating-form SFT plans only."""
+    _check(lib().morlet_plan_set_row_thresholds(plan.handle, int(lane_chunk_max_L), int(start_state_min_L)),
+           "morlet_plan_set_row_thresholds")
 
 
 def morlet_debug_skip_tickets(plan: Plan, skip: int):

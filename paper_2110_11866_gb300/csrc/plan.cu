@@ -1018,6 +1018,28 @@ int morlet_plan_set_spin_limit(morlet_plan_t p, int64_t polls) {
   return MORLET_OK;
 }
 
+int morlet_plan_set_row_thresholds(morlet_plan_t p, int64_t lane_chunk_max_L, int64_t start_state_min_L) {
+  if (!p || lane_chunk_max_L < 0 || start_state_min_L < 0) return MORLET_ERR_ARG;
+  if (p->h_err && *(volatile int*)p->h_err) return MORLET_ERR_TIMEOUT;
+  const morlet_plan_desc& d = p->desc;
+  if (!(p->form == 2 && d.precision == MORLET_FP32_COMP && d.transform == MORLET_SFT && d.method == MORLET_DIRECT))
+    return MORLET_OK;  // a single schedule
+  const long long old_ls = p->ls_max_L, old_ss = p->ss_min_L;
+  p->ls_max_L = lane_chunk_max_L;
+  p->ss_min_L = start_state_min_L;
+  long long slots = 0;
+  int rc = build_forward(p, slots);
+  if (rc == MORLET_OK && slots > p->n_slots) rc = MORLET_ERR_UNSUPPORTED;
+  if (rc != MORLET_OK) {  // back to the thresholds the plan had
+    p->ls_max_L = old_ls;
+    p->ss_min_L = old_ss;
+    long long s2 = 0;
+    const int rc2 = build_forward(p, s2);
+    return rc2 != MORLET_OK ? rc2 : rc;
+  }
+  return MORLET_OK;
+}
+
 int morlet_debug_skip_tickets(morlet_plan_t p, int64_t skip) {
   if (!p || skip < 0) return MORLET_ERR_ARG;
   p->skip_tickets = skip;

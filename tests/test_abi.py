@@ -53,3 +53,5 @@ def test_strerror_and_argument_errors_without_gpu(built_lib):
     assert lib.morlet_forward(None, None, None, None) == m.MORLET_ERR_ARG
     assert lib.gauss_smooth(None, 0, 1.0, 3, 0, 0, None, None) == m.MORLET_ERR_ARG
 
+    assert lib.morlet_plan_set_row_thresholds(None, 128, 4096) == m.MORLET_ERR_ARG
+    assert lib.morlet_plan_set_spin_limit(None, 10) == m.MORLET_ERR_ARG

@@ -170,6 +170,51 @@ def test_autotune_keeps_results():
             assert rel_err(out[i][s], oracle_forward(x.astype(np.float64), sg, 4)) < 1e-5
 
 
+@pytest.mark.parametrize("K", [3, 6])
+def test_every_autotune_choice_passes(K):
+    """Each (lane-chunk, start-state) threshold pair the autotuner may keep gives the transform within
+    the compensated-FP32 gate, on rows that move between the scans as the thresholds change
+    (L = 32 ... 4800)."""
+    import torch
+    rng = np.random.default_rng(900 + K)
+    lens = [70001, 3000, 150000]
+    sigs = [rng.standard_normal(n).astype(np.float32) for n in lens]
+    sigmas = [8.0, 16.0, 40.0, 64.0, 100.0, 300.0, 600.0, 1200.0]
+    refs = [[oracle_forward(x.astype(np.float64), sg, K) for sg in sigmas] for x in sigs]
+    plan = m.morlet_plan(lens, sigmas, K=K, precision=m.MORLET_FP32_COMP)
+    S, n_in = len(sigmas), sum(lens)
+    xt = torch.from_numpy(np.concatenate(sigs)).cuda()
+    pairs = [(128, 4096), (256, 4096), (64, 4096), (0, 4096), (128, 2048), (256, 2048), (128, 1024),
+             (256, 1024), (0, 0)]
+    applied = 0
+    for ls, ss in pairs:
+        before = m.morlet_plan_stats(plan)
+        try:
+            m.morlet_plan_set_row_thresholds(plan, ls, ss)
+        except m.MorletError as err:  # needs more look-back slots than the plan owns: plan unchanged
+            assert err.code == m.MORLET_ERR_UNSUPPORTED and (ls, ss) == (0, 0), (ls, ss, err)
+            assert m.morlet_plan_stats(plan) == before
+            continue
+        applied += 1
+        st = m.morlet_plan_stats(plan)
+        assert (st["lane_chunk_max_L"], st["start_state_min_L"]) == (ls, ss)
+        n_lane = sum(int(np.ceil(4 * sg)) <= ls for sg in sigmas) * len(lens)
+        assert st["rows_lane_chunk"] == n_lane, (ls, ss, st)
+        W = torch.full((n_in * S,), float("nan"), dtype=torch.complex64, device="cuda")
+        m.morlet_forward(plan, xt, W)
+        torch.cuda.synchronize()
+        assert m.morlet_last_device_error(plan) == 0
+        Wh = W.cpu().numpy()
+        off = 0
+        for i, n in enumerate(lens):
+            for s in range(S):
+                got = Wh[S * off + s * n: S * off + (s + 1) * n]
+                e = rel_err(got, refs[i][s])
+                assert e < 1e-5, (ls, ss, n, sigmas[s], e)
+            off += n
+    assert applied >= len(pairs) - 1
+
+
 def test_deterministic_replay():
     """Two launches (graph replays) give bit-identical outputs."""
     x = WL.white(3, 300000)
