@@ -198,6 +198,55 @@ __device__ __forceinline__ V shfl_xor2(V v, int o) {
   return r;
 }
 
+// Packed FP32 (sm_100 and later): two independent IEEE single-precision operations per instruction,
+// each rounded exactly like the scalar operation. The FP32 scan loops run the Fourier terms in pairs
+// (2h, 2h + 1) through them; an odd term count is padded with a zero term (rotation 0, weight 0),
+// whose state stays bounded and is never read.
+__device__ __forceinline__ float2 pk_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 pk_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 pk_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pk_dup(float a) { return make_float2(a, a); }
+
+template <int K>
+struct Pairs {
+  static constexpr int H = (K + 1) / 2;
+};
+// (v[2h], v[2h + 1]), zero past the last term
+template <int K>
+__device__ __forceinline__ float2 pk_pair(const float (&v)[K], int h) {
+  return make_float2(v[2 * h], 2 * h + 1 < K ? v[2 * h + 1] : 0.f);
+}
+
+// ITEMS steps of Reinsch's form of the real recurrence of G <- rho G + d from a zero state
+// (lam = 4 sin^2(theta / 2)): e <- e + d_i - lam s, s <- s + e, for every term, two terms per
+// instruction. Returns e and s after the last step.
+template <int K, int ITEMS>
+__device__ __forceinline__ void reinsch_pk(const float (&d)[ITEMS], const float (&lam)[K], float (&e)[K],
+                                           float (&s)[K]) {
+  constexpr int H = Pairs<K>::H;
+  float2 nl[H], e2[H], s2[H];
+#pragma unroll
+  for (int h = 0; h < H; ++h) {
+    const float2 l = pk_pair<K>(lam, h);
+    nl[h] = make_float2(-l.x, -l.y);
+    e2[h] = s2[h] = make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const float2 dd = pk_dup(d[i]);
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      e2[h] = pk_fma(nl[h], s2[h], pk_add(e2[h], dd));
+      s2[h] = pk_add(s2[h], e2[h]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    e[j] = (j & 1) ? e2[j >> 1].y : e2[j >> 1].x;
+    s[j] = (j & 1) ? s2[j >> 1].y : s2[j >> 1].x;
+  }
+}
+
 // ------------------------------------------------------------------------------------------------
 // Memory-ordering helpers for the look-back (flags with acquire/release at GPU scope; the values
 // are read through L2 with ld.global.cg since L1 is not coherent across SMs).

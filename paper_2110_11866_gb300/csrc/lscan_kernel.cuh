@@ -11,6 +11,7 @@
 // t = tan(theta/2), s = sin(theta)): the same operation count as a complex multiply, but the map has
 // determinant exactly one and its angle error is relative to theta, so the thousands of rotations a
 // lane applies drift far less in magnitude and phase than repeated products with a rounded rho.
+// The terms run in pairs through packed FP32 instructions (two terms per instruction).
 //
 // The 32 chunks of a warp lie C positions apart, so every global access goes through this warp's
 // shared buffers, transposed:
@@ -108,15 +109,22 @@ __global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel
     if (lane == 0) w2 = (long long)atomicAdd(P.ticket, 1ull);
 
     const ScaleTab* tb = P.tabs + wi.scale;
-    float2 sh[K];  // (tan(theta/2), sin(theta)) per term
-    float cM[K], cL[K], cx = 0.f;
+    // terms in pairs (packed FP32): tan(theta/2), -sin(theta) and the combine weights per pair
+    constexpr int H = Pairs<K>::H;
+    float2 t2[H], ns2[H], cm2[H], cl2[H];
+    float cx = 0.f;
 #pragma unroll
-    for (int j = 0; j < K; ++j) {
-      sh[j] = __ldg(&tb->f_shear[j]);
-      cM[j] = tb->f_cM[j];
-      cL[j] = tb->f_cL[j];
-      cx += cM[j];
+    for (int h = 0; h < H; ++h) {
+      const bool two = 2 * h + 1 < K;
+      const float2 a = __ldg(&tb->f_shear[2 * h]);
+      const float2 b = two ? __ldg(&tb->f_shear[2 * h + 1]) : make_float2(0.f, 0.f);
+      t2[h] = make_float2(a.x, b.x);
+      ns2[h] = make_float2(-a.y, -b.y);
+      cm2[h] = make_float2(tb->f_cM[2 * h], two ? tb->f_cM[2 * h + 1] : 0.f);
+      cl2[h] = make_float2(tb->f_cL[2 * h], two ? tb->f_cL[2 * h + 1] : 0.f);
     }
+#pragma unroll
+    for (int j = 0; j < K; ++j) cx += tb->f_cM[j];
     // positions relative to the row fit in 32 bits (the plan keeps rows below 2^30 positions)
     const int N = (int)wi.n, pro = (int)wi.t_dom, Cc = wi.n_sub, L2 = 2 * (int)tb->L;
     const int a0 = (int)wi.t_a - pro;             // lane 0's first processed position
@@ -184,9 +192,9 @@ __global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel
       ls_commit();
     };
 
-    float2 S[K];
+    float2 X[H], Y[H];  // (Re, Im) of the states of terms 2h and 2h + 1
 #pragma unroll
-    for (int j = 0; j < K; ++j) S[j] = make_float2(0.f, 0.f);
+    for (int h = 0; h < H; ++h) X[h] = Y[h] = make_float2(0.f, 0.f);
 
     issue(0);
     for (int k = 0; k < n_steps; ++k) {
@@ -225,11 +233,12 @@ __global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel
       if (pro_step) {  // x[t - 2L] is before lo_l throughout the prologue: the input is x[t] alone
 #pragma unroll
         for (int i = 0; i < LS_ITEMS; ++i) {
+          const float2 dd = pk_dup(xa[i]);
 #pragma unroll
-          for (int j = 0; j < K; ++j) {
-            const float x1 = fmaf(sh[j].x, S[j].y, S[j].x);
-            S[j].y = fmaf(-sh[j].y, x1, S[j].y);
-            S[j].x = fmaf(sh[j].x, S[j].y, x1 + xa[i]);
+          for (int h = 0; h < H; ++h) {
+            const float2 x1 = pk_fma(t2[h], Y[h], X[h]);
+            Y[h] = pk_fma(ns2[h], x1, Y[h]);
+            X[h] = pk_fma(t2[h], Y[h], pk_add(x1, dd));
           }
         }
         continue;
@@ -240,17 +249,17 @@ __global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel
         float2 o[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const float d = xa[i + h] - xl[i + h];
-          float ox = 0.f, oy = 0.f;
+          const float2 dd = pk_dup(xa[i + h] - xl[i + h]);
+          float2 ox = make_float2(0.f, 0.f), oy = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int j = 0; j < K; ++j) {
-            const float x1 = fmaf(sh[j].x, S[j].y, S[j].x);
-            S[j].y = fmaf(-sh[j].y, x1, S[j].y);
-            S[j].x = fmaf(sh[j].x, S[j].y, x1 + d);
-            ox = fmaf(cM[j], S[j].x, ox);
-            oy = fmaf(cL[j], S[j].y, oy);
+          for (int q = 0; q < H; ++q) {
+            const float2 x1 = pk_fma(t2[q], Y[q], X[q]);
+            Y[q] = pk_fma(ns2[q], x1, Y[q]);
+            X[q] = pk_fma(t2[q], Y[q], pk_add(x1, dd));
+            ox = pk_fma(cm2[q], X[q], ox);
+            oy = pk_fma(cl2[q], Y[q], oy);
           }
-          o[h] = make_float2(fmaf(cx, xl[i + h], ox), oy);
+          o[h] = make_float2(fmaf(cx, xl[i + h], ox.x + ox.y), oy.x + oy.y);
         }
         bl[lane * 9 + i / 2] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
       }

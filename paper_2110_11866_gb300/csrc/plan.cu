@@ -205,9 +205,9 @@ bool ls_row(const morlet_plan_s* p, bool adjoint, const ScaleTab& tb, long long 
 }
 
 // Tiles of a start-state row: tile 0 starts at t_grid (the input element of every tile start is
-// 16-byte aligned); the outputs (positions [D, D + N)) lie in tiles [kD, kE].
+// 32-byte aligned); the outputs (positions [D, D + N)) lie in tiles [kD, kE].
 void ss_tiles(long long x_off, long long N, long long D, long long& t_grid, long long& kD, long long& kE) {
-  const long long g = (4 - (x_off % 4)) % 4;
+  const long long g = (8 - (x_off % 8)) % 8;
   t_grid = g - PS_TILE_H;
   kD = (D - t_grid) / PS_TILE_H;
   kE = (D + N - 1 - t_grid) / PS_TILE_H;
@@ -353,7 +353,7 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
       continue;
     }
     const bool warp_window = (p->form != 1);
-    RowSpec r{N, tb.L, tb.D, c.x_off, c.out_off, s, 16 / esz, seg_policy(p), ci,
+    RowSpec r{N, tb.L, tb.D, c.x_off, c.out_off, s, 32 / esz, seg_policy(p), ci,
               warp_window ? (long long)32 * ITEMS : TILE, warp_window ? 1 : 0};
     long long sl = slots, st = 0;
     bool chained = false;

@@ -12,7 +12,7 @@
 // state, with neither a look-back nor a 2L-sample prologue.
 //
 // Tiles are 512 positions (32 lanes x 16 samples), tile 0 of a row starting at the position t_grid
-// whose input element is 16-byte aligned. A work item is a chunk of up to 8 tiles (4096 positions,
+// whose input element is 32-byte aligned. A work item is a chunk of up to 8 tiles (4096 positions,
 // the unit of the pw_tile powers) of one row, taken by one warp:
 //   per tile: lane-serial Horner sum of its 16 samples, a warp reduction weighted by
 //             rho^{16 (31 - lane)} -> the tile sum G (FP32), and the chunk aggregate in FP32;
@@ -117,21 +117,13 @@ __device__ __forceinline__ DFC warp_lookback(const KParams& P, int64_t slot, int
 // Reinsch's form, which stays accurate for small theta: with lam = 4 sin^2(theta / 2),
 //     d_i = d_{i-1} + x_i - lam s_{i-1},  s_i = s_{i-1} + d_i,
 // and at the end sum_i rho^{15-i} x_i = (d_15 + (lam / 2) s_14) - i sin(theta) s_14 with
-// s_14 = s_15 - d_15. Three operations per sample and term instead of a complex rotation's five.
+// s_14 = s_15 - d_15. Three operations per sample and term instead of a complex rotation's five,
+// issued for two terms at a time (packed FP32).
 template <int K, int ITEMS>
 __device__ __forceinline__ void lane_sums(const float (&xa)[ITEMS], const float2 (&rho)[K], const float (&lam)[K],
                                           const float2 (&w)[K], float2 (&b)[K]) {
   float s[K], d[K];
-#pragma unroll
-  for (int j = 0; j < K; ++j) s[j] = d[j] = 0.f;
-#pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-      d[j] = fmaf(-lam[j], s[j], d[j] + xa[i]);
-      s[j] += d[j];
-    }
-  }
+  reinsch_pk<K, ITEMS>(xa, lam, d, s);
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     const float s14 = s[j] - d[j];

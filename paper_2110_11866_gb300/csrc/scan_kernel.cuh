@@ -158,6 +158,51 @@ __device__ __forceinline__ void load_run(const E* __restrict__ p, int64_t t, int
   }
 }
 
+// 32 bytes of read-only FP32 input in one 256-bit load (sm_100 and later; q 32-byte aligned).
+__device__ __forceinline__ void ld_nc_v8(const float* q, float* v) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+      : "l"(q));
+}
+
+// load_run for FP32 runs with 256-bit loads: a run of N (a multiple of 8) samples that is in range
+// and 32-byte aligned takes N / 8 loads; misaligned by r samples (uniform across a warp in this
+// library's layouts), the aligned 32-byte chunks covering it plus one, shifted by r in registers,
+// provided that superset lies inside [0, cap). Otherwise as load_run. A lane's run is 64 bytes
+// that the warp's 32 lanes read at a 64-byte stride: 32-byte pieces halve the L1 wavefronts of
+// 16-byte ones.
+template <int N>
+__device__ __forceinline__ void load_run_v8(const float* __restrict__ p, int64_t t, int64_t lo, int64_t hi,
+                                            float (&v)[N], int64_t cap) {
+  static_assert(N % 8 == 0, "runs of whole 32-byte pieces");
+  if (t >= lo && t + N <= hi) {
+    const float* q = p + t;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(q);
+    const int r = (int)((a & 31) >> 2);
+    if ((a & 31) == 0) {
+#pragma unroll
+      for (int i = 0; i < N; i += 8) ld_nc_v8(q + i, v + i);
+      return;
+    }
+    if ((a & 3) == 0 && t - r >= 0 && t - r + N + 8 <= cap) {
+      float c[N + 8];
+#pragma unroll
+      for (int i = 0; i < N + 8; i += 8) ld_nc_v8(q - r + i, c + i);
+      switch (r) {
+        case 1: shift_copy<float, N, 1>(c, v); break;
+        case 2: shift_copy<float, N, 2>(c, v); break;
+        case 3: shift_copy<float, N, 3>(c, v); break;
+        case 4: shift_copy<float, N, 4>(c, v); break;
+        case 5: shift_copy<float, N, 5>(c, v); break;
+        case 6: shift_copy<float, N, 6>(c, v); break;
+        default: shift_copy<float, N, 7>(c, v); break;
+      }
+      return;
+    }
+  }
+  load_run<float, N>(p, t, lo, hi, v, cap);
+}
+
 // Hint: bring elements [a, b) of the n-element buffer at base into L2 with one bulk prefetch (the
 // range is shrunk to whole 16-byte granules inside the buffer; nothing is read into registers).
 template <typename E>

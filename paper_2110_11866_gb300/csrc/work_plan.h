@@ -26,7 +26,7 @@ struct RowSpec {
   long long x_off;     // first input element of the row
   long long out_off;   // first output element of the row
   int scale;
-  int align;           // input elements per 16 bytes (segment starts are aligned to it)
+  int align;           // input elements per 32 bytes (segment starts are aligned to it)
   int policy;
   int chain;           // row index stored in the work items
   long long wt;        // positions per step of a window segment: a CTA sub-tile, or one warp-tile
@@ -51,7 +51,7 @@ __host__ __device__ inline long long row_work(const RowSpec& r, long long T, Wor
     // i.e. a prologue of at most about an eighth of the segment
     long long sub = r.warp_window ? (16 * r.L + r.wt - 1) / r.wt : (10 * r.L + r.wt - 1) / r.wt;
     if (sub < (r.warp_window ? 2 : 1)) sub = r.warp_window ? 2 : 1;
-    R = sub * r.wt - 2 * r.L - (r.align - 1);  // room for rounding the segment start down to 16 bytes
+    R = sub * r.wt - 2 * r.L - (r.align - 1);  // room for rounding the segment start down to 32 bytes
   } else if (r.policy == SEG_RESTART) {
     R = 4 * T > 4 * r.L ? 4 * T : 4 * r.L;
   } else {
@@ -61,7 +61,7 @@ __host__ __device__ inline long long row_work(const RowSpec& r, long long T, Wor
   for (long long ts = t_first_out; ts < t_last_out; ts += R) {
     const long long te = (ts + R < t_last_out) ? ts + R : t_last_out;
     const long long t_dom = (ts - 2 * r.L > 0) ? ts - 2 * r.L : 0;
-    // first processed position: t_dom rounded down so that the lead loads start 16-byte aligned
+    // first processed position: t_dom rounded down so that the lead loads start 32-byte aligned
     long long t_a = t_dom - ((((r.x_off + t_dom) % r.align) + r.align) % r.align);
     const long long step = *chained ? T : r.wt;
     const long long n_tiles = (te - t_a + step - 1) / step;

@@ -128,6 +128,11 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
   // where combining two lanes is a plain sum. The damped ASFT keeps the V recursion and the
   // multiplicative scan (rho^{-n} would amplify).
   constexpr bool GF = !C::ASFT;
+  // FP32 real input: the per-position loops run the terms in pairs (packed FP32)
+  constexpr bool PK = GF && std::is_same<R, float>::value && CH == 1;
+  constexpr bool PKM = PK && C::OUT == OUT_MORLET;
+  constexpr bool V8 = PK;  // 256-bit loads of the FP32 input runs
+  constexpr int H = Pairs<K>::H;
   using EIn = typename std::conditional<CH == 2, V, R>::type;
   const int lane = threadIdx.x & 31;
 
@@ -167,6 +172,20 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
         pn[j].y = -q.y;
       }
     }
+    // packed constants of the FP32 Morlet loops (term pairs; a padded term has rho = 0, weight 0)
+    float2 rx2[H], ry2[H], nry2[H], cm2[H], cl2[H];
+    if constexpr (PKM) {
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        const bool two = 2 * h + 1 < K;
+        const V r0 = rho[2 * h], r1 = two ? rho[2 * h + 1] : V{};
+        rx2[h] = make_float2(r0.x, r1.x);
+        ry2[h] = make_float2(r0.y, r1.y);
+        nry2[h] = make_float2(-r0.y, -r1.y);
+        cm2[h] = make_float2(cM[2 * h], two ? cM[2 * h + 1] : 0.f);
+        cl2[h] = make_float2(cL[2 * h], two ? cL[2 * h + 1] : 0.f);
+      }
+    }
     const V E = TabR<R>::E(tb);
     const EIn* __restrict__ xs = reinterpret_cast<const EIn*>(P.x) + wi.x_off;
     const int64_t N = wi.n;
@@ -194,8 +213,13 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
       EIn xa[ITEMS], xl[ITEMS];
       const bool live = (tf + ITEMS > lo && tf < N) || (tf - Wl + ITEMS > lo && tf - Wl < N);
       if (live) {
-        load_run<EIn, ITEMS>(xs, tf, lo, N, xa);
-        load_run<EIn, ITEMS>(xs, tf - Wl, lo, N, xl, P.n_x - wi.x_off);
+        if constexpr (V8) {
+          load_run_v8<ITEMS>(xs, tf, lo, N, xa, P.n_x - wi.x_off);
+          load_run_v8<ITEMS>(xs, tf - Wl, lo, N, xl, P.n_x - wi.x_off);
+        } else {
+          load_run<EIn, ITEMS>(xs, tf, lo, N, xa);
+          load_run<EIn, ITEMS>(xs, tf - Wl, lo, N, xl, P.n_x - wi.x_off);
+        }
       } else {
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) xa[i] = xl[i] = EIn{};
@@ -216,20 +240,27 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
             if constexpr (sizeof(R) == 4) lam[j] = __ldg(&tb->f_lam[j]);
             else lam[j] = tb->d_lam[j];
           }
+          if constexpr (PK) {
+            float d[ITEMS];
 #pragma unroll
-          for (int v = 0; v < NT; ++v) sv[v] = ev[v] = R(0);
+            for (int i = 0; i < ITEMS; ++i) d[i] = xa[i] - xl[i];
+            reinsch_pk<K, ITEMS>(d, lam, ev, sv);
+          } else {
 #pragma unroll
-          for (int i = 0; i < ITEMS; ++i) {
-            R xv[CH], xgv[CH];
-            split_in<C>(xa[i], xl[i], xv, xgv);
+            for (int v = 0; v < NT; ++v) sv[v] = ev[v] = R(0);
 #pragma unroll
-            for (int c = 0; c < CH; ++c) {
-              const R dd = xv[c] - xgv[c];
+            for (int i = 0; i < ITEMS; ++i) {
+              R xv[CH], xgv[CH];
+              split_in<C>(xa[i], xl[i], xv, xgv);
 #pragma unroll
-              for (int j = 0; j < K; ++j) {
-                const int v = c * K + j;
-                ev[v] = fma(-lam[j], sv[v], ev[v] + dd);
-                sv[v] += ev[v];
+              for (int c = 0; c < CH; ++c) {
+                const R dd = xv[c] - xgv[c];
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                  const int v = c * K + j;
+                  ev[v] = fma(-lam[j], sv[v], ev[v] + dd);
+                  sv[v] += ev[v];
+                }
               }
             }
           }
@@ -237,7 +268,8 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
           for (int v = 0; v < NT; ++v) {
             const R s14 = sv[v] - ev[v];
             B[v].x = fma(R(0.5) * lam[v % K], s14, ev[v]);
-            B[v].y = rho[v % K].y * s14;
+            if constexpr (PKM) B[v].y = ((v & 1) ? ry2[v >> 1].y : ry2[v >> 1].x) * s14;
+            else B[v].y = rho[v % K].y * s14;
           }
         } else {
 #pragma unroll
@@ -298,7 +330,32 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
         }
       }
       // pass 2: outputs for positions in [t_out, t_end)
+      // packed state (Morlet output): X = (Re G_2h, Re G_2h+1), Y likewise
+      float2 X2[H], Y2[H];
+      if constexpr (PKM) {
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+          const V s0 = S[2 * h], s1 = 2 * h + 1 < K ? S[2 * h + 1] : V{};
+          X2[h] = make_float2(s0.x, s1.x);
+          Y2[h] = make_float2(s0.y, s1.y);
+        }
+      }
       auto one = [&](int i) -> V {
+        if constexpr (PKM) {
+          // G <- rho G + d and the combine, two terms per instruction
+          const float2 dd = pk_dup(xa[i] - xl[i]);
+          float2 ox = make_float2(0.f, 0.f), oy = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int h = 0; h < H; ++h) {
+            const float2 vr = pk_fma(rx2[h], X2[h], pk_fma(nry2[h], Y2[h], dd));
+            const float2 vi = pk_fma(ry2[h], X2[h], pk_mul(rx2[h], Y2[h]));
+            X2[h] = vr;
+            Y2[h] = vi;
+            ox = pk_fma(cm2[h], vr, ox);
+            oy = pk_fma(cl2[h], vi, oy);
+          }
+          return cmake<R>(fma(cx, xl[i], ox.x + ox.y), oy.x + oy.y);
+        }
         R xv[CH], xlv[CH];
         split_in<C>(xa[i], xl[i], xv, xlv);
         V o;
