@@ -11,7 +11,6 @@
 // t = tan(theta/2), s = sin(theta)): the same operation count as a complex multiply, but the map has
 // determinant exactly one and its angle error is relative to theta, so the thousands of rotations a
 // lane applies drift far less in magnitude and phase than repeated products with a rounded rho.
-// The terms run in pairs through packed FP32 instructions (two terms per instruction).
 //
 // The 32 chunks of a warp lie C positions apart, so every global access goes through this warp's
 // shared buffers, transposed:
@@ -21,10 +20,12 @@
 //    buffers, so the copy of step k + 1 overlaps the arithmetic of step k; each lane reads its run
 //    back from a padded 80-byte row and shifts it by the run's misalignment, which is the same for
 //    every lane and step;
-//  - outputs: each lane writes its 16 complex outputs into a padded 144-byte row (over the input
-//    buffer it has just read); the warp stores them as 16-byte pieces, eight lanes per row (128
-//    contiguous bytes per row; the plan starts every row's chunks on an even output element),
-//    masked only in the steps that touch the ends of the row.
+//  - outputs: a lane's 16 complex outputs of a step are 128 contiguous bytes. When every lane's
+//    outputs of the step are in range and 32-byte aligned (the plan starts every row's chunks on an
+//    output element that is a multiple of 4), each lane writes them as four 256-bit stores of whole
+//    sectors. Otherwise (the steps that touch the ends of the row, or a misaligned output buffer)
+//    each lane writes them into a padded 144-byte row (over the input buffer it has just read) and
+//    the warp stores them as masked 16-byte pieces, eight lanes per row.
 // Every bank access is conflict-free (row strides of 20 and 36 words).
 //
 // Work item fields (see WorkItem): t_a = first position of lane 0's chunk, n_sub = C (multiple of
@@ -109,22 +110,15 @@ __global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel
     if (lane == 0) w2 = (long long)atomicAdd(P.ticket, 1ull);
 
     const ScaleTab* tb = P.tabs + wi.scale;
-    // terms in pairs (packed FP32): tan(theta/2), -sin(theta) and the combine weights per pair
-    constexpr int H = Pairs<K>::H;
-    float2 t2[H], ns2[H], cm2[H], cl2[H];
-    float cx = 0.f;
+    float2 sh[K];  // (tan(theta/2), sin(theta)) per term
+    float cM[K], cL[K], cx = 0.f;
 #pragma unroll
-    for (int h = 0; h < H; ++h) {
-      const bool two = 2 * h + 1 < K;
-      const float2 a = __ldg(&tb->f_shear[2 * h]);
-      const float2 b = two ? __ldg(&tb->f_shear[2 * h + 1]) : make_float2(0.f, 0.f);
-      t2[h] = make_float2(a.x, b.x);
-      ns2[h] = make_float2(-a.y, -b.y);
-      cm2[h] = make_float2(tb->f_cM[2 * h], two ? tb->f_cM[2 * h + 1] : 0.f);
-      cl2[h] = make_float2(tb->f_cL[2 * h], two ? tb->f_cL[2 * h + 1] : 0.f);
+    for (int j = 0; j < K; ++j) {
+      sh[j] = __ldg(&tb->f_shear[j]);
+      cM[j] = tb->f_cM[j];
+      cL[j] = tb->f_cL[j];
+      cx += cM[j];
     }
-#pragma unroll
-    for (int j = 0; j < K; ++j) cx += tb->f_cM[j];
     // positions relative to the row fit in 32 bits (the plan keeps rows below 2^30 positions)
     const int N = (int)wi.n, pro = (int)wi.t_dom, Cc = wi.n_sub, L2 = 2 * (int)tb->L;
     const int a0 = (int)wi.t_a - pro;             // lane 0's first processed position
@@ -166,6 +160,7 @@ __global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel
     // 16-byte output pieces when the row's chunk starts are 16-byte aligned
     float2* const orow = reinterpret_cast<float2*>(P.out) + (wi.out_off - tb->D);
     const bool o16 = ((reinterpret_cast<uintptr_t>(orow + wi.t_a) & 15) == 0);
+    const bool o32 = ((reinterpret_cast<uintptr_t>(orow + wi.t_a) & 31) == 0);
     const int so = (lane >> 3) * Cc + 2 * (lane & 7);  // this lane's store piece in round 0
 
     // copies of step k into buffer k & 1
@@ -192,9 +187,9 @@ __global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel
       ls_commit();
     };
 
-    float2 X[H], Y[H];  // (Re, Im) of the states of terms 2h and 2h + 1
+    float2 S[K];
 #pragma unroll
-    for (int h = 0; h < H; ++h) X[h] = Y[h] = make_float2(0.f, 0.f);
+    for (int j = 0; j < K; ++j) S[j] = make_float2(0.f, 0.f);
 
     issue(0);
     for (int k = 0; k < n_steps; ++k) {
@@ -233,35 +228,45 @@ __global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel
       if (pro_step) {  // x[t - 2L] is before lo_l throughout the prologue: the input is x[t] alone
 #pragma unroll
         for (int i = 0; i < LS_ITEMS; ++i) {
-          const float2 dd = pk_dup(xa[i]);
 #pragma unroll
-          for (int h = 0; h < H; ++h) {
-            const float2 x1 = pk_fma(t2[h], Y[h], X[h]);
-            Y[h] = pk_fma(ns2[h], x1, Y[h]);
-            X[h] = pk_fma(t2[h], Y[h], pk_add(x1, dd));
+          for (int j = 0; j < K; ++j) {
+            const float x1 = fmaf(sh[j].x, S[j].y, S[j].x);
+            S[j].y = fmaf(-sh[j].y, x1, S[j].y);
+            S[j].x = fmaf(sh[j].x, S[j].y, x1 + xa[i]);
           }
         }
         continue;
       }
-      // ---- output step: recursion, combine, rows in shared memory ----
+      // ---- output step: recursion and combine ----
+      auto one = [&](int i) -> float2 {
+        const float d = xa[i] - xl[i];
+        float ox = 0.f, oy = 0.f;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+          const float x1 = fmaf(sh[j].x, S[j].y, S[j].x);
+          S[j].y = fmaf(-sh[j].y, x1, S[j].y);
+          S[j].x = fmaf(sh[j].x, S[j].y, x1 + d);
+          ox = fmaf(cM[j], S[j].x, ox);
+          oy = fmaf(cL[j], S[j].y, oy);
+        }
+        return make_float2(fmaf(cx, xl[i], ox), oy);
+      };
+      if (o32 && step0 >= t_out && step0 + 31 * Cc + LS_ITEMS <= t_end) {  // warp-uniform
+        // every lane's 16 outputs are in range: four 32-byte stores of whole sectors per lane
+        float2* op = orow + (step0 + lane * Cc);
+#pragma unroll
+        for (int i = 0; i < LS_ITEMS; i += 4) {
+          const float2 o0 = one(i), o1 = one(i + 1), o2 = one(i + 2), o3 = one(i + 3);
+          asm volatile("st.global.cs.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(op + i),
+                       "f"(o0.x), "f"(o0.y), "f"(o1.x), "f"(o1.y), "f"(o2.x), "f"(o2.y), "f"(o3.x), "f"(o3.y)
+                       : "memory");
+        }
+        continue;
+      }
 #pragma unroll
       for (int i = 0; i < LS_ITEMS; i += 2) {
-        float2 o[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const float2 dd = pk_dup(xa[i + h] - xl[i + h]);
-          float2 ox = make_float2(0.f, 0.f), oy = make_float2(0.f, 0.f);
-#pragma unroll
-          for (int q = 0; q < H; ++q) {
-            const float2 x1 = pk_fma(t2[q], Y[q], X[q]);
-            Y[q] = pk_fma(ns2[q], x1, Y[q]);
-            X[q] = pk_fma(t2[q], Y[q], pk_add(x1, dd));
-            ox = pk_fma(cm2[q], X[q], ox);
-            oy = pk_fma(cl2[q], Y[q], oy);
-          }
-          o[h] = make_float2(fmaf(cx, xl[i + h], ox.x + ox.y), oy.x + oy.y);
-        }
-        bl[lane * 9 + i / 2] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+        const float2 o0 = one(i), o1 = one(i + 1);
+        bl[lane * 9 + i / 2] = make_float4(o0.x, o0.y, o1.x, o1.y);
       }
       __syncwarp();
       // ---- cooperative stores: row c's 16-byte piece q holds positions p_c + 2q, p_c + 2q + 1 ----

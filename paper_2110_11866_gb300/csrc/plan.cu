@@ -273,12 +273,12 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
     chains.push_back(c);
     if (ls_row(p, adjoint, tb, N)) {
       // 32 lane chunks of C positions per item, each after a prologue of >= 2L positions; chunks
-      // start where the output element is even (16-byte stores), the first one possibly one
-      // position before D (its output there is masked)
+      // start where the output element is a multiple of 4 (32-byte stores), the first one possibly
+      // up to three positions before D (its outputs there are masked)
       const long long Cfull = std::min<long long>(4096, std::max<long long>(1024, (8 * tb.L + LS_STEP_H - 1) / LS_STEP_H * LS_STEP_H));
       const long long pro = (2 * tb.L + LS_STEP_H - 1) / LS_STEP_H * LS_STEP_H;
       const long long t_first = tb.D, t_last = tb.D + N;
-      long long s0 = t_first - (((c.out_off % 2) + 2) % 2);
+      long long s0 = t_first - (((c.out_off % 4) + 4) % 4);
       while (s0 < t_last) {
         const long long rem = t_last - s0;
         long long Ci = Cfull;

@@ -374,10 +374,26 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
       const int64_t tw = wi.t_a + (int64_t)k * WT;  // first position of the warp-tile
       if (tw >= t_end || tw + WT <= t_out) continue;  // no output in this warp-tile (warp-uniform)
       if constexpr (STAGE) {
-        // The warp-tile's 512 outputs go through this warp's shared rows (one padded 144-byte row
-        // per lane, conflict-free both ways) so that every store instruction writes 512 (or 256)
-        // contiguous bytes instead of 32 scattered half-sectors; positions outside [t_out, t_end)
-        // are masked.
+        {
+          V* obd = reinterpret_cast<V*>(P.out) + (wi.out_off - D + tw);
+          if (tw >= t_out && tw + WT <= t_end && (reinterpret_cast<uintptr_t>(obd) & 31) == 0) {
+            // every output of the tile, 32-byte aligned: each lane writes its 128 bytes as four
+            // whole-sector 256-bit stores
+            float* op = reinterpret_cast<float*>(obd + lane * ITEMS);
+#pragma unroll
+            for (int i = 0; i < ITEMS; i += 4) {
+              const V o0 = one(i), o1 = one(i + 1), o2 = one(i + 2), o3 = one(i + 3);
+              asm volatile("st.global.cs.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(op + 2 * i),
+                           "f"(o0.x), "f"(o0.y), "f"(o1.x), "f"(o1.y), "f"(o2.x), "f"(o2.y), "f"(o3.x), "f"(o3.y)
+                           : "memory");
+            }
+            continue;
+          }
+        }
+        // Otherwise the warp-tile's 512 outputs go through this warp's shared rows (one padded
+        // 144-byte row per lane, conflict-free both ways) so that every store instruction writes
+        // 512 (or 256) contiguous bytes instead of 32 scattered half-sectors; positions outside
+        // [t_out, t_end) are masked.
         __shared__ float4 s_out[WARPS * 32 * 9];
         float4* rows = s_out + (threadIdx.x >> 5) * (32 * 9);
 #pragma unroll
