@@ -64,7 +64,8 @@ enum {
   MORLET_FLAG_NO_GRAPH = 1,   /* launch kernels directly instead of replaying a CUDA graph */
   MORLET_FLAG_AUTOTUNE = 2,   /* compensated FP32 SFT Morlet plans: at plan time, time the forward under a
                                  few row-to-kernel thresholds (see morlet_plan_stats) on a zero input and
-                                 a scratch output of the batch's size, and keep the fastest */
+                                 a scratch output of the batch's size, and keep the fastest (the
+                                 defaults unless another choice is at least 1 % faster) */
   MORLET_FLAG_NO_HALO = 4     /* force one look-back chain per row (no per-tile window recompute) */
 };
 

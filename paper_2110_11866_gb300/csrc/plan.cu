@@ -706,9 +706,10 @@ int autotune(morlet_plan_s* p, cudaStream_t st) {
     }
   }
   {
+    // the defaults (candidate 0) stay unless another pair is at least 1 % faster
     float best_ms = -1.f;
     for (int i = 0; i < NC; ++i)
-      if (tmin[i] >= 0.f && (best_ms < 0.f || tmin[i] < best_ms)) {
+      if (tmin[i] >= 0.f && (best_ms < 0.f || tmin[i] < 0.99f * best_ms)) {
         best_ms = tmin[i];
         best_ls = cand[i][0];
         best_ss = cand[i][1];

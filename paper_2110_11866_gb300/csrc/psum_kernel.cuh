@@ -214,7 +214,7 @@ __device__ __forceinline__ void start_state(const KParams& P, const WorkItem& wi
     const int m = (int)(a0 + PS_TILE - 1 - q);  // e - q, 0 .. 511
     const float* __restrict__ xs = reinterpret_cast<const float*>(P.x) + wi.x_off;
     float xa[ITEMS];
-    load_run<float, ITEMS>(xs, a0 + (int64_t)lane * ITEMS, 0, wi.n < q + 1 ? wi.n : q + 1, xa);
+    load_run_v8<ITEMS>(xs, a0 + (int64_t)lane * ITEMS, 0, wi.n < q + 1 ? wi.n : q + 1, xa, P.n_x - wi.x_off);
     float2 wl[K], b[K];
     float lam[K];
 #pragma unroll
@@ -261,7 +261,7 @@ __device__ __forceinline__ void start_state_window(const KParams& P, const WorkI
       partial = true;
       const float* __restrict__ xs = reinterpret_cast<const float*>(P.x) + wi.x_off;
       float xa[ITEMS];
-      load_run<float, ITEMS>(xs, a0 + (int64_t)lane * ITEMS, u0 > 0 ? u0 : 0, wi.n, xa);
+      load_run_v8<ITEMS>(xs, a0 + (int64_t)lane * ITEMS, u0 > 0 ? u0 : 0, wi.n, xa, P.n_x - wi.x_off);
       float2 wl[K], b[K];
       float lam[K];
 #pragma unroll
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(THREADS, C::K <= 4 ? 3 : 2) tsum_kernel(const 
       float2 g = make_float2(0.f, 0.f);
       if (t0 < N && t0 + PS_TILE > 0) {  // warp-uniform
         float xa[ITEMS];
-        load_run<float, ITEMS>(xs, t0 + (int64_t)lane * ITEMS, 0, N, xa);
+        load_run_v8<ITEMS>(xs, t0 + (int64_t)lane * ITEMS, 0, N, xa, P.n_x - wi.x_off);
         float2 b[K];
         lane_sums<K, ITEMS>(xa, rho, lam, wl, b);
         g = warp_sum_scatter<K>(b, lane);
@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(THREADS, C::K <= 4 ? 3 : 2) psum_kernel(const 
       const int64_t t0 = wi.t_a + (int64_t)k * PS_TILE;
       if (k < n_sub && t0 < N && t0 + PS_TILE > 0) {  // warp-uniform
         float xa[ITEMS];
-        load_run<float, ITEMS>(xs, t0 + (int64_t)lane * ITEMS, 0, N, xa);
+        load_run_v8<ITEMS>(xs, t0 + (int64_t)lane * ITEMS, 0, N, xa, P.n_x - wi.x_off);
         float2 b[K];
         lane_sums<K, ITEMS>(xa, rho, lam, wl, b);
         const float2 g = warp_sum_scatter<K>(b, lane);
