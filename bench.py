@@ -308,7 +308,7 @@ def main():
             "config": {"workload": wname,
                        "signals": len(lens),
                        "samples": int(sum(lens)), "scales": S, "K": w.K, "outputs_per_step": n_out,
-                       "precision": "FP32 scan, two-float carries and prefix sums", "form": "rotating" if args.form != 1 else "kernel-integral",
+                       "precision": "FP32 scan (packed term pairs), two-float carries", "form": "rotating" if args.form != 1 else "kernel-integral",
                        "l2": f"inputs {4 * sum(lens) / 1e6:.0f} MB + outputs {8 * n_out / 1e9:.2f} GB per step "
                              "exceed the 129 MB L2 (no flush between steps)",
                        "parallelism": f"replicas x{ws}", "plan_seconds": round(t_plan, 2),
@@ -317,7 +317,7 @@ def main():
                                           "start_state_min_L": pst["start_state_min_L"]}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "forward step (lane-chunk, warp-scan and prefix-sum kernels, one graph)",
+                         "kernel": "forward step (lane-chunk, warp-scan and tile-sum kernels, one graph)",
                          "algorithmic_bytes_per_output": BYTES_PER_OUTPUT,
                          "strict_floor_bytes_per_output": 8 + 4 / S,
                          "strict_floor_frac": achieved * (8 + 4 / S) / BYTES_PER_OUTPUT / peak},
