@@ -298,6 +298,8 @@ __device__ __forceinline__ void start_state_window(const KParams& P, const WorkI
   }
 }
 
+constexpr bool TS_PF = true;  // a tile-sum chunk prefetched into L2 when claimed
+
 // Tile sums only: G_k = sum_{u in tile k} rho^{e_k - u} x[u] for the tiles of a chunk, FP32, stored
 // for start_state_window. No look-back, no prefix: chunks are independent.
 template <class C>
@@ -328,7 +330,7 @@ __global__ void __launch_bounds__(THREADS, C::K <= 4 ? 3 : 2) tsum_kernel(const 
     const float* __restrict__ xs = reinterpret_cast<const float*>(P.x) + wi.x_off;
     const int64_t N = wi.n;
     float2* gb = reinterpret_cast<float2*>(P.pbuf) + wi.p_row * K;
-    if (lane == 0) prefetch_l2(xs, N, wi.t_a, wi.t_a + (int64_t)wi.n_sub * PS_TILE);
+    if (TS_PF && lane == 0) prefetch_l2(xs, N, wi.t_a, wi.t_a + (int64_t)wi.n_sub * PS_TILE);
 #pragma unroll 1
     for (int k = 0; k < wi.n_sub; ++k) {
       const int64_t t0 = wi.t_a + (int64_t)k * PS_TILE;

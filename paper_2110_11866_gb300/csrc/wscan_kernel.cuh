@@ -205,11 +205,6 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
 
     for (int k = 0; k < wi.n_sub; ++k) {
       const int64_t tf = wi.t_a + (int64_t)k * WT + (int64_t)lane * ITEMS;
-      if (lane == 0 && k + 1 < wi.n_sub) {  // the next warp-tile's two input runs, into L2
-        const int64_t t1 = wi.t_a + (int64_t)(k + 1) * WT;
-        prefetch_l2(xs, N, t1 < lo ? lo : t1, t1 + WT);
-        prefetch_l2(xs, N, t1 - Wl < lo ? lo : t1 - Wl, t1 - Wl + WT);
-      }
       EIn xa[ITEMS], xl[ITEMS];
       const bool live = (tf + ITEMS > lo && tf < N) || (tf - Wl + ITEMS > lo && tf - Wl < N);
       if (live) {
