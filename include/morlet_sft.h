@@ -173,13 +173,16 @@ int morlet_plan_set_spin_limit(morlet_plan_t plan, int64_t polls);
 /*
  * morlet_plan_set_row_thresholds - choose which rows of a compensated-FP32 rotating-form SFT
  * forward take the lane-chunk scan (L <= lane_chunk_max_L; 0: none) and which take start-state
- * work items (L > start_state_min_L; 0: none), the two choices MORLET_FLAG_AUTOTUNE makes by
- * timing; other plans keep their single schedule and ignore the values. The transform is the same
- * for every choice (each row gate holds); only the schedule changes. Rebuilds the forward's work
- * tables synchronously (device memory is freed and allocated, so no forward of this plan may be in
- * flight). Errors: MORLET_ERR_ARG for a negative value; MORLET_ERR_UNSUPPORTED when the choice needs
- * more look-back slots than the plan allocated (the plan keeps its previous thresholds);
- * MORLET_ERR_TIMEOUT if an earlier launch timed out and its error word was not read yet.
+ * work items (L > start_state_min_L), the two choices MORLET_FLAG_AUTOTUNE makes by timing; other
+ * plans keep their single schedule and ignore the values. Only choices that keep every row within
+ * the compensated-FP32 gate (1e-5 of max|W|) are accepted: 0 <= lane_chunk_max_L <= 256 and
+ * 1 <= start_state_min_L <= 2048 (window segments of longer windows drift past the gate on
+ * resonant inputs). The transform is the same for every accepted choice; only the schedule
+ * changes. Rebuilds the forward's work tables synchronously (device memory is freed and
+ * allocated, so no forward of this plan may be in flight). Errors: MORLET_ERR_ARG for a value out
+ * of those ranges; MORLET_ERR_UNSUPPORTED when the choice needs more look-back slots than the plan
+ * allocated (the plan keeps its previous thresholds); MORLET_ERR_TIMEOUT if an earlier launch timed
+ * out and its error word was not read yet.
  */
 int morlet_plan_set_row_thresholds(morlet_plan_t plan, int64_t lane_chunk_max_L, int64_t start_state_min_L);
 

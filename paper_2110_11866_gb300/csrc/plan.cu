@@ -64,9 +64,16 @@ constexpr long long DEFAULT_SPIN = 1LL << 20;  // polls of ~64 ns sleep + an L2 
 // items), prefix-sum kernel, lane-chunk kernel
 constexpr int TICKETS = 5;
 constexpr long long PS_TILE_H = 512, PS_CHUNK_H = 8;  // prefix-sum tile and chunk (psum_kernel.cuh)
-// Rows whose half window exceeds this take their start states from prefix sums: a window segment
-// of such a row (about 16 L positions per warp) would leave too few, too long work items.
-constexpr long long SS_MIN_L = 4096;
+// Rows whose half window exceeds this start their work items from exact states (window sums of
+// tile sums, or prefix sums). A window segment restarts 2L positions before its first output and
+// runs about 16 L positions, so its FP32 residue history grows with L; for L > 2048 a resonant
+// input (a chirp through the kernel's band) takes it past 1e-5 of max|W| (1.4e-5 measured at
+// L = 4096), while start-state items (at most 32 warp-tiles from an exact state) stay below 9e-6.
+constexpr long long SS_MIN_L = 2048;
+// Largest start-state threshold and lane-chunk threshold that keep every row within the
+// compensated-FP32 gate (measured on chirps and white noise, K = 3..6).
+constexpr long long SS_MIN_L_MAX = 2048;
+constexpr long long LS_MAX_L_MAX = 256;
 // Rows whose half window is at most this go to the lane-chunk scan (one pass per sample, a
 // prologue of 2L per lane chunk of max(1024, 8 L) positions).
 constexpr long long LS_MAX_L = 128;
@@ -671,7 +678,7 @@ int autotune(morlet_plan_s* p, cudaStream_t st) {
   int rc = MORLET_OK;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   const long long cand[][2] = {{LS_MAX_L, SS_MIN_L}, {256, SS_MIN_L}, {64, SS_MIN_L}, {0, SS_MIN_L},
-                               {LS_MAX_L, 2048},     {256, 2048},     {LS_MAX_L, 1024}, {256, 1024}};
+                               {LS_MAX_L, 1024},     {256, 1024},     {64, 1024},       {0, 1024}};
   constexpr int NC = (int)(sizeof(cand) / sizeof(cand[0]));
   float tmin[NC];
   for (int i = 0; i < NC; ++i) tmin[i] = -1.f;
@@ -1020,7 +1027,9 @@ int morlet_plan_set_spin_limit(morlet_plan_t p, int64_t polls) {
 }
 
 int morlet_plan_set_row_thresholds(morlet_plan_t p, int64_t lane_chunk_max_L, int64_t start_state_min_L) {
-  if (!p || lane_chunk_max_L < 0 || start_state_min_L < 0) return MORLET_ERR_ARG;
+  if (!p || lane_chunk_max_L < 0 || lane_chunk_max_L > LS_MAX_L_MAX || start_state_min_L < 1 ||
+      start_state_min_L > SS_MIN_L_MAX)
+    return MORLET_ERR_ARG;
   if (p->h_err && *(volatile int*)p->h_err) return MORLET_ERR_TIMEOUT;
   const morlet_plan_desc& d = p->desc;
   if (!(p->form == 2 && d.precision == MORLET_FP32_COMP && d.transform == MORLET_SFT && d.method == MORLET_DIRECT))
