@@ -227,6 +227,25 @@ def test_chirp_sigma_sweep(K):
             assert e < 1e-5, (sg, K, e)
 
 
+@pytest.mark.parametrize("K", [4, 6])
+def test_chirp_sigma_sweep_other_forms(K):
+    """The chirp sweep for the kernel-integral form (compensated FP32), plain FP32, FP64 and the
+    ASFT, each against its own gate."""
+    x = WL.c2_chirps()
+    sigmas = [128.0, 512.0, 1024.0, 2048.0, 2896.0, 4096.0, 10321.0]
+    refs = [oracle_forward(x, sg, K) for sg in sigmas]
+    cases = [(dict(precision=m.MORLET_FP32_COMP, form=m.MORLET_FORM_KERNEL), refs, 1e-5),
+             (dict(precision=m.MORLET_FP32_PLAIN), refs, 1e-3),
+             (dict(precision=m.MORLET_FP64), refs, 1e-12),
+             (dict(precision=m.MORLET_FP32_PLAIN, transform=m.MORLET_ASFT),
+              [oracle_forward(x, sg, K, transform=m.MORLET_ASFT) for sg in sigmas], 1e-4)]
+    for kw, rr, tol in cases:
+        _, out = gpu_forward([x], sigmas, K=K, **kw)
+        for s, sg in enumerate(sigmas):
+            e = rel_err(out[0][s], rr[s])
+            assert e < tol, (kw, sg, e)
+
+
 def test_chirp_long_windows_from_tile_sums():
     """Window sums of tile sums at the longest windows (a batch large enough that start-state items
     are long, so the plan takes window sums): the chirp stays within the gate."""
