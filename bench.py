@@ -160,7 +160,7 @@ def main():
     ap.add_argument("--form", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--workload", default="c3", choices=["c3", "c3_small"],
                     help="c3: the full batched scalogram; c3_small: 64 signals clipped to 65536 samples (profiling)")
     ap.add_argument("--no-autotune", action="store_true",
