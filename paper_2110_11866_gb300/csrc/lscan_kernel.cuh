@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel
     float2* const orow = reinterpret_cast<float2*>(P.out) + (wi.out_off - tb->D);
     const bool o16 = ((reinterpret_cast<uintptr_t>(orow + wi.t_a) & 15) == 0);
     const bool o32 = ((reinterpret_cast<uintptr_t>(orow + wi.t_a) & 31) == 0);
-    const int so = (lane >> 3) * Cc + 2 * (lane & 7);  // this lane's store piece in store pass 0
+    const int so = (lane >> 3) * Cc + 2 * (lane & 7);  // this lane's store piece in round 0
 
     // copies of step k into buffer k & 1
     auto issue = [&](int k) {
