@@ -55,3 +55,28 @@ def test_strerror_and_argument_errors_without_gpu(built_lib):
 
     assert lib.morlet_plan_set_row_thresholds(None, 128, 4096) == m.MORLET_ERR_ARG
     assert lib.morlet_plan_set_spin_limit(None, 10) == m.MORLET_ERR_ARG
+
+
+def test_plan_descriptor_errors_without_gpu(built_lib):
+    """Descriptor validation happens before any device call: invalid batches, scales, term counts
+    and option combinations are refused with the documented status on a machine without a GPU."""
+    import paper_2110_11866_gb300 as m
+    bad = [
+        (dict(lengths=[], sigmas=[8.0]), m.MORLET_ERR_ARG),                 # no signals
+        (dict(lengths=[100, 0], sigmas=[8.0]), m.MORLET_ERR_ARG),           # an empty signal
+        (dict(lengths=[100], sigmas=[]), m.MORLET_ERR_ARG),                 # no scales
+        (dict(lengths=[100], sigmas=[0.25]), m.MORLET_ERR_ARG),             # sigma below 0.5
+        (dict(lengths=[100], sigmas=[float("nan")]), m.MORLET_ERR_ARG),     # NaN sigma
+        (dict(lengths=[100], sigmas=[8.0], K=13), m.MORLET_ERR_UNSUPPORTED),  # more terms than built
+        (dict(lengths=[100], sigmas=[8.0], K=-1), m.MORLET_ERR_ARG),
+        (dict(lengths=[100], sigmas=[8.0], K=0), m.MORLET_ERR_ARG),         # automatic K needs fit_tol
+        (dict(lengths=[100], sigmas=[8.0], precision=3), m.MORLET_ERR_ARG),
+        (dict(lengths=[100], sigmas=[8.0], transform=m.MORLET_ASFT, precision=m.MORLET_FP64),
+         m.MORLET_ERR_UNSUPPORTED),                                         # ASFT is FP32 only
+        (dict(lengths=[100], sigmas=[8.0], xi=float("inf")), m.MORLET_ERR_ARG),
+        (dict(lengths=[100], sigmas=[8.0], norm=2), m.MORLET_ERR_ARG),
+    ]
+    for kw, code in bad:
+        with pytest.raises(m.MorletError) as err:
+            m.morlet_plan(**kw)
+        assert err.value.code == code, (kw, err.value.code)
