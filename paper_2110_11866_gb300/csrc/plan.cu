@@ -64,6 +64,7 @@ constexpr long long DEFAULT_SPIN = 1LL << 20;  // polls of ~64 ns sleep + an L2 
 // items), prefix-sum kernel, lane-chunk kernel
 constexpr int TICKETS = 5;
 constexpr long long PS_TILE_H = 512, PS_CHUNK_H = 8;  // prefix-sum tile and chunk (psum_kernel.cuh)
+constexpr long long TS_CHUNK_H = 8;                    // tiles per tile-sum work item
 // Rows whose half window exceeds this start their work items from exact states (window sums of
 // tile sums, or prefix sums). A window segment restarts 2L positions before its first output and
 // runs about 16 L positions, so its FP32 residue history grows with L; for L > 2048 a resonant
@@ -337,17 +338,18 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
         ln.sub_tiles += nsub;
         k_last = k;
       }
-      // prefix sums at the ends of tiles 0 .. k_last - 1, in chunks of PS_CHUNK_H tiles
+      // tile sums (window mode) or prefix sums at the ends of tiles 0 .. k_last - 1, in chunks
       const long long n_t = k_last;
       const long long first = ln.n_pslots;
-      for (long long k = 0; k < n_t; k += PS_CHUNK_H) {
+      const long long chunk = ln.ss_window ? TS_CHUNK_H : PS_CHUNK_H;
+      for (long long k = 0; k < n_t; k += chunk) {
         WorkItem w{};
         w.x_off = c.x_off;
         w.n = N;
         w.out_off = c.out_off;
         w.scale = s;
         w.chain = ci;
-        w.n_sub = (int)std::min(PS_CHUNK_H, n_t - k);
+        w.n_sub = (int)std::min(chunk, n_t - k);
         w.t_a = tg + PS_TILE_H * k;
         w.slot = ln.n_pslots++;
         w.slot_first = first;

@@ -303,7 +303,7 @@ constexpr bool TS_PF = true;  // a tile-sum chunk prefetched into L2 when claime
 // Tile sums only: G_k = sum_{u in tile k} rho^{e_k - u} x[u] for the tiles of a chunk, FP32, stored
 // for start_state_window. No look-back, no prefix: chunks are independent.
 template <class C>
-__global__ void __launch_bounds__(THREADS, C::K <= 4 ? 3 : 2) tsum_kernel(const KParams P) {
+__global__ void __launch_bounds__(THREADS, C::K <= 4 ? 4 : 2) tsum_kernel(const KParams P) {
   static_assert(std::is_same<typename C::R, float>::value && C::CH == 1 && C::ITEMS == 16,
                 "tile sums are built for the FP32 real-input kernels");
   constexpr int K = C::K, ITEMS = C::ITEMS;
