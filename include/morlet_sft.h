@@ -94,7 +94,11 @@ typedef struct {
  * Defines: per scale, L = ceil(window_mult * sigma), beta = pi / L, harmonics p = P_S .. P_S + K - 1
  * with P_S the least-residual start (direct method, Sec. III-A), coefficients m_p (cos) and l_p
  * (sin) minimising eq. mmse over k in [-L, L], fitted on the GPU in FP64. For MORLET_GAUSS:
- * harmonics 0..K-1 fitted to G, G_D or G_DD (eq. aproGauss).
+ * harmonics 0..K-1 fitted to G, G_D or G_DD (eq. aproGauss). MORLET_GAUSS with MORLET_ASFT (eqs.
+ * GsASFT, gddAsft): with alpha = n0 / sigma^2 and the shift identity eq. siftGauss, the fitted
+ * target is G, G_D - alpha G or G_DD - 2 alpha G_D + alpha^2 G (cos terms for the even part, sin
+ * terms for the odd part); the damped window sums then give G_X[n] at output n.
+ * The ASFT runs in FP32 (either FP32 precision); MORLET_FP64 with MORLET_ASFT is unsupported.
  * Allocates the plan's device workspace (tile table, cross-tile status, tables) and a host-mapped
  * error word; no allocation happens in forward/backward. Synchronises `stream`.
  * Errors: MORLET_ERR_ARG (bad sizes/options), MORLET_ERR_NOMEM, MORLET_ERR_CUDA.

@@ -168,6 +168,60 @@ def fit_gauss(sigma: float, P: int, deriv: int, L: int | None = None):
     raise ValueError("deriv must be 0, 1 or 2")
 
 
+def fit_gauss_asft(sigma: float, P: int, deriv: int, n0: int, L: int | None = None):
+    """Fits for Gaussian smoothing by the ASFT (eqs. GsASFT and gddAsft).
+
+    The ASFT window weights x[n - k] by e^{-alpha k}, alpha = n0 / sigma^2. By the shift identity
+    eq. siftGauss, e^{-alpha k} G[k] = e^{alpha^2/(4 gamma)} G[k + n0], so with
+    C = e^{-alpha^2/(4 gamma)} and the derivative rule d/dk applied to k + n0:
+        G[k + n0]    = C e^{-alpha k} G[k],
+        G_D[k + n0]  = C e^{-alpha k} (G_D[k] - alpha G[k]),
+        G_DD[k + n0] = C e^{-alpha k} (G_DD[k] - 2 alpha G_D[k] + alpha^2 G[k]).
+    The printed eq. gddAsft carries these terms with misplaced factors and tildes; this is the
+    reading taken. The bracket h is fitted on [-L, L] as in eq. mmse: its even part by
+    cos(beta p k), its odd part by sin(beta p k), p = 0 .. P. Returns dict(L, n0, alpha, cos, sin).
+    """
+    L = window_half(sigma) if L is None else L
+    alpha = asft_alpha(sigma, n0)
+    ps = range(0, P + 1)
+    if deriv == 0:
+        even, odd = (lambda k: gaussian(k, sigma)), None
+    elif deriv == 1:
+        even, odd = (lambda k: -alpha * gaussian(k, sigma)), (lambda k: gaussian_d(k, sigma))
+    elif deriv == 2:
+        even = lambda k: gaussian_dd(k, sigma) + alpha * alpha * gaussian(k, sigma)
+        odd = lambda k: -2.0 * alpha * gaussian_d(k, sigma)
+    else:
+        raise ValueError("deriv must be 0, 1 or 2")
+    c, r1 = _ls_fit(np.cos, even, L, ps)
+    if odd is None:
+        sn, r2 = np.zeros(len(ps)), 0.0
+    else:
+        sn, r2 = _ls_fit(np.sin, odd, L, ps)
+    return dict(L=L, n0=int(n0), alpha=alpha, sigma=float(sigma), cos=c, sin=sn, rss=r1 + r2)
+
+
+def kernel_gauss_asft(gf):
+    """Effective kernel of the ASFT Gaussian fit, on k' in [n0 - L, n0 + L]:
+    C e^{-alpha (k' - n0)} h_hat[k' - n0], h_hat[k] = sum_p cos_p cos(beta p k) + sin_p sin(beta p k).
+    Equal to G_X[k'] up to the fit residual. Returns (k', kernel)."""
+    L, n0, alpha, sigma = gf["L"], gf["n0"], gf["alpha"], gf["sigma"]
+    g = 1.0 / (2.0 * sigma * sigma)
+    C = math.exp(-alpha * alpha / (4.0 * g))
+    kk = np.arange(-L, L + 1, dtype=np.int64)
+    h = np.zeros(kk.shape, np.float64)
+    for p, (a, b) in enumerate(zip(gf["cos"], gf["sin"])):
+        ang = harmonic_angle(p, kk, L)
+        h += a * np.cos(ang) + b * np.sin(ang)
+    return kk + n0, C * np.exp(-alpha * kk.astype(np.float64)) * h
+
+
+def gauss_asft_direct(x, gf, n_idx=None):
+    """Gaussian smoothing (or a derivative) by the ASFT fit: sum_{k'} kernel[k'] x[n - k']."""
+    kp, ker = kernel_gauss_asft(gf)
+    return conv_direct(x, ker, int(kp[0]), n_idx)
+
+
 # ----------------------------------------------------------------------------------------------
 # Effective kernels: what each method computes exactly (up to rounding)
 # ----------------------------------------------------------------------------------------------

@@ -102,6 +102,25 @@ def asft_direct_method(x, fit, sigma: float, xi: float, n0: int):
     return W[0::2] + 1j * W[1::2]
 
 
+def asft_gauss(x, gf):
+    """Gaussian smoothing (or a derivative) by the attenuated recursion (Sec. II-D, eq. GsASFT):
+    the damped window sums of the cos part and of the sin part of the fit, shifted by n0 and scaled
+    by C = e^{-alpha^2/(4 gamma)} (see morlet.fit_gauss_asft); real output."""
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    K = len(gf["cos"])
+    c = np.ascontiguousarray(gf["cos"], np.float64)
+    sn = np.ascontiguousarray(gf["sin"], np.float64)
+    sigma, alpha, n0 = gf["sigma"], gf["alpha"], gf["n0"]
+    C = math.exp(-alpha * alpha * sigma * sigma / 2.0)
+    W = np.zeros(2 * x.shape[0], np.float64)
+    rc = lib.oracle_asft_dd(_ptr(x), x.shape[0], int(gf["L"]), 0, K, float(alpha), int(n0), _ptr(c), _ptr(sn),
+                            C, 0.0, _ptr(W))
+    if rc != 0:
+        raise RuntimeError("oracle_asft_dd failed")
+    return W[0::2] + W[1::2]
+
+
 def sft_batch(signals, fits, n_threads: int = 0):
     """All (signal, scale) chains of a ragged batch, OpenMP over chains. Returns (W, threads used).
 

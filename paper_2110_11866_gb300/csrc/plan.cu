@@ -19,6 +19,7 @@ namespace msft {
 MSFT_DECL(kernel_rf_f32c_morlet)
 MSFT_DECL(kernel_rf_f32p_morlet)
 MSFT_DECL(kernel_rf_f32p_asft)
+MSFT_DECL(kernel_rf_f32p_asft_real)
 MSFT_DECL(kernel_rf_f64_morlet)
 MSFT_DECL(kernel_rf_f32c_real)
 MSFT_DECL(kernel_rf_f32p_real)
@@ -38,6 +39,7 @@ const void* kernel_for(int variant, int K, bool warp) {
     case V_RF_F32C_MORLET: return warp ? kernel_rf_f32c_morlet_w(K) : kernel_rf_f32c_morlet(K);
     case V_RF_F32P_MORLET: return warp ? kernel_rf_f32p_morlet_w(K) : kernel_rf_f32p_morlet(K);
     case V_RF_F32P_ASFT: return warp ? kernel_rf_f32p_asft_w(K) : kernel_rf_f32p_asft(K);
+    case V_RF_F32P_ASFT_REAL: return warp ? kernel_rf_f32p_asft_real_w(K) : kernel_rf_f32p_asft_real(K);
     case V_RF_F64_MORLET: return warp ? kernel_rf_f64_morlet_w(K) : kernel_rf_f64_morlet(K);
     case V_KI_F32C_MORLET: return warp ? nullptr : kernel_ki_f32c_morlet(K);
     case V_KI_F32P_MORLET: return warp ? nullptr : kernel_ki_f32p_morlet(K);
@@ -180,8 +182,10 @@ int round_k(int K) {
 int variant_of(const morlet_plan_s* p, bool adjoint) {
   const int prec = p->desc.precision;
   if (adjoint) return prec == MORLET_FP64 ? V_RF_F64_ADJ : prec == MORLET_FP32_COMP ? V_RF_F32C_ADJ : V_RF_F32P_ADJ;
-  if (p->desc.method == MORLET_GAUSS)
+  if (p->desc.method == MORLET_GAUSS) {
+    if (p->desc.transform == MORLET_ASFT) return V_RF_F32P_ASFT_REAL;
     return prec == MORLET_FP64 ? V_RF_F64_REAL : prec == MORLET_FP32_COMP ? V_RF_F32C_REAL : V_RF_F32P_REAL;
+  }
   if (p->desc.transform == MORLET_ASFT) return V_RF_F32P_ASFT;
   if (p->form == 1)
     return prec == MORLET_FP64 ? V_KI_F64_MORLET : prec == MORLET_FP32_COMP ? V_KI_F32C_MORLET : V_KI_F32P_MORLET;
@@ -791,8 +795,7 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
   if (d->norm != 0 && d->norm != 1) return MORLET_ERR_ARG;
   if (d->form < 0 || d->form > 2) return MORLET_ERR_ARG;
   if (d->method == MORLET_GAUSS && (d->deriv < 0 || d->deriv > 2)) return MORLET_ERR_ARG;
-  if (d->transform == MORLET_ASFT && (d->method != MORLET_DIRECT || d->precision == MORLET_FP64 || d->form == 1))
-    return MORLET_ERR_UNSUPPORTED;
+  if (d->transform == MORLET_ASFT && (d->precision == MORLET_FP64 || d->form == 1)) return MORLET_ERR_UNSUPPORTED;
   if (d->n0 < 0 || d->window_mult < 0 || d->spin_limit < 0) return MORLET_ERR_ARG;
   for (int64_t i = 0; i < d->n_signals; ++i)
     if (d->lengths[i] < 1) return MORLET_ERR_ARG;
@@ -836,7 +839,7 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
       const double sg = p->sigmas[s];
       J.sigma = sg;
       J.xi = d->xi;
-      J.omega0 = d->xi / sg;
+      J.omega0 = d->method == MORLET_GAUSS ? 0.0 : d->xi / sg;  // no carrier for the Gaussian
       J.L = (long long)ceil(wm * sg);
       J.amp = d->norm ? Cxi * pow(M_PI, -0.25) / sqrt(sg) : 1.0;
       J.kappa_xi = d->norm ? kxi : 0.0;

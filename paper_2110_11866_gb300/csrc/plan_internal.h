@@ -49,6 +49,7 @@ enum Variant {
   V_RF_F32C_ADJ,         // adjoint
   V_RF_F32P_ADJ,
   V_RF_F64_ADJ,
+  V_RF_F32P_ASFT_REAL,   // ASFT Gaussian smoothing, FP32
   V_COUNT
 };
 

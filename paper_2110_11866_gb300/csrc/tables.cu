@@ -39,11 +39,25 @@ __device__ void fit_target(const FitJob& J, long long k, double* tc, double* ts)
   } else {  // Gaussian and its derivatives (Sec. II)
     const double g = 1.0 / (2.0 * J.sigma * J.sigma);
     const double G = sqrt(g / M_PI) * exp(-g * kk * kk);
-    *tc = 0.0;
-    *ts = 0.0;
-    if (J.deriv == 0) *tc = G;
-    else if (J.deriv == 1) *ts = -2.0 * g * kk * G;
-    else *tc = (4.0 * g * g * kk * kk - 2.0 * g) * G;
+    const double GD = -2.0 * g * kk * G, GDD = (4.0 * g * g * kk * kk - 2.0 * g) * G;
+    // ASFT (Sec. II-E): the damped window weights x[n - k] by e^{-alpha k}, and the shift identity
+    // e^{-alpha k} G[k] = e^{alpha^2/(4 gamma)} G[k + n0] (n0 = alpha / (2 gamma)) turns the
+    // derivatives into fixed mixtures: with C = e^{-alpha^2/(4 gamma)},
+    //   G_D[k + n0]  = C e^{-alpha k} (G_D - alpha G)[k],
+    //   G_DD[k + n0] = C e^{-alpha k} (G_DD - 2 alpha G_D + alpha^2 G)[k].
+    // The fitted target is that mixture: its even part goes to the cos terms, its odd part to the
+    // sin terms (alpha = 0 gives the SFT targets).
+    const double a = J.alpha;
+    if (J.deriv == 0) {
+      *tc = G;
+      *ts = 0.0;
+    } else if (J.deriv == 1) {
+      *tc = -a * G;
+      *ts = GD;
+    } else {
+      *tc = GDD + a * a * G;
+      *ts = -2.0 * a * GD;
+    }
   }
 }
 
@@ -177,6 +191,10 @@ __global__ void fit_solve(const FitJob* jobs, const double* partial, int nblk, i
         const double r1 = ls_solve(ps, K, J.L, false, bcs, 0.0, m);
         const double r2 = ls_solve(ps, K, J.L, true, bss, 0.0, l);
         r = yy + r1 + r2;  // yy - c.b over both parts
+      } else if (J.alpha > 0.0 && J.deriv > 0) {  // ASFT derivative: both parts
+        const double r1 = ls_solve(ps, K, J.L, false, bcs, 0.0, m);
+        const double r2 = ls_solve(ps, K, J.L, true, bss, 0.0, l);
+        r = yy + r1 + r2;
       } else if (J.deriv == 1) {
         r = yy + ls_solve(ps, K, J.L, true, bss, 0.0, l);
         for (int j = 0; j < K; ++j) m[j] = 0.0;

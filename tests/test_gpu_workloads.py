@@ -205,3 +205,35 @@ def test_gauss_smooth(deriv, precision):
         e = rel_err(y.cpu().numpy(), ref)
         print(f"gauss deriv={deriv} sigma={sigma} P={P} precision={precision}: {e:.2e}")
         assert e < (1e-12 if precision == m.MORLET_FP64 else 1e-5)
+
+
+@pytest.mark.parametrize("deriv", [0, 1, 2])
+def test_gauss_smooth_asft(deriv):
+    """Gaussian smoothing and its derivatives by the ASFT (eqs. GsASFT, gddAsft, FP32 attenuated
+    recursion): a batch of ragged signals at several scales against the oracle's double-double
+    recursion with the oracle's own fit; the ASFT gate 1e-4 of max|y|."""
+    import torch
+    rng = np.random.default_rng(20 + deriv)
+    lens = [70000, 5, 4097, 30000]
+    sigs = [rng.standard_normal(n).astype(np.float32) for n in lens]
+    sigmas = [5.0, 24.0, 40.0, 700.0]
+    P = 6
+    plan = m.morlet_plan(lens, sigmas, K=P + 1, method=m.MORLET_GAUSS, transform=m.MORLET_ASFT,
+                         deriv=deriv, precision=m.MORLET_FP32_PLAIN)
+    S, n_in = len(sigmas), sum(lens)
+    xt = torch.from_numpy(np.concatenate(sigs)).cuda()
+    y = torch.full((n_in * S,), float("nan"), dtype=torch.float32, device="cuda")
+    m.morlet_forward(plan, xt, y)
+    torch.cuda.synchronize()
+    assert m.morlet_last_device_error(plan) == 0
+    yh = y.cpu().numpy()
+    off = 0
+    for x, n in zip(sigs, lens):
+        for s, sigma in enumerate(sigmas):
+            gf = om.fit_gauss_asft(sigma, P, deriv, om.default_n0(sigma))
+            ref = sft_dd.asft_gauss(x.astype(np.float64), gf)
+            got = yh[S * off + s * n: S * off + (s + 1) * n]
+            e = rel_err(got, ref)
+            print(f"gauss asft deriv={deriv} n={n} sigma={sigma}: {e:.2e}")
+            assert e < 1e-4, (n, sigma, e)
+        off += n

@@ -399,3 +399,69 @@ def test_adjoint_finite_differences_log_power_loss():
         e[t] = 1e-6
         fd = (loss(x + e) - loss(x - e)) / 2e-6
         assert abs(fd - dx[t]) < 1e-5 * (abs(dx[t]) + 1e-3)
+
+
+# ---- Gaussian smoothing by the ASFT (eqs. GsASFT, gddAsft through eq. siftGauss) ----
+
+_TRUE_G = {0: M.gaussian, 1: M.gaussian_d, 2: M.gaussian_dd}
+
+
+@pytest.mark.parametrize("deriv", [0, 1, 2])
+@pytest.mark.parametrize("sigma,P", [(16.0, 6), (24.0, 8), (64.0, 10)])
+def test_gauss_asft_kernel_is_the_true_derivative(sigma, P, deriv):
+    """The ASFT Gaussian fit's effective kernel C e^{-alpha (k'-n0)} h_hat[k'-n0] equals the true
+    G, G_D or G_DD (closed forms of Sec. II) on [n0 - L, n0 + L] up to the fit residual, which the
+    damping amplifies by at most e^{alpha L} C (about e^{1/2} here). A slip in the mixture (a sign
+    of alpha, a missing alpha or alpha^2 term) costs O(n0 / sigma), far above it."""
+    n0 = M.default_n0(sigma)
+    gf = M.fit_gauss_asft(sigma, P, deriv, n0)
+    kp, ker = M.kernel_gauss_asft(gf)
+    true = _TRUE_G[deriv](kp, sigma)
+    err = np.abs(ker - true).max() / np.abs(true).max()
+    # the same-P SFT fit of the undamped derivative, for scale
+    sf = M.fit_gauss(sigma, P, deriv)
+    ks = np.arange(-sf["L"], sf["L"] + 1)
+    ts = _TRUE_G[deriv](ks, sigma)
+    e_sft = np.abs(M.kernel_gauss(sf) - ts).max() / np.abs(ts).max()
+    assert err <= 3.0 * e_sft, (err, e_sft)
+    # the wrong mixtures are far off
+    alpha = gf["alpha"]
+    if deriv == 1:
+        wrong = dict(gf, cos=-gf["cos"])                      # + alpha G instead of - alpha G
+    elif deriv == 2:
+        wrong = dict(gf, sin=-gf["sin"])                      # + 2 alpha G_D instead of - 2 alpha G_D
+    else:
+        wrong = dict(gf, alpha=-alpha)                        # growing instead of decaying window
+    _, kw = M.kernel_gauss_asft(wrong)
+    assert np.abs(kw - true).max() / np.abs(true).max() > 10.0 * err
+
+
+@pytest.mark.parametrize("deriv", [0, 1, 2])
+def test_gauss_asft_sinusoid_closed_form(deriv):
+    """A sinusoid through the ASFT Gaussian smoothing: (G_X * cos(nu .))[n] is A cos(nu n),
+    -nu A sin(nu n) or -nu^2 A cos(nu n) with A = e^{-sigma^2 nu^2 / 2} (the normalised Gaussian's
+    transform; the sampled sums equal it up to exponentially small aliasing). Checked away from
+    the ends of the signal; the shift n0 and the factor C are what this pins for deriv 0."""
+    sigma, P, nu = 24.0, 8, 0.05
+    n0 = M.default_n0(sigma)
+    gf = M.fit_gauss_asft(sigma, P, deriv, n0)
+    N = 4000
+    n = np.arange(N)
+    x = np.cos(nu * n)
+    y = D.asft_gauss(x, gf)
+    A = math.exp(-0.5 * sigma * sigma * nu * nu)
+    ref = {0: A * np.cos(nu * n), 1: -nu * A * np.sin(nu * n), 2: -nu * nu * A * np.cos(nu * n)}[deriv]
+    inner = slice(gf["L"] + n0 + 1, N - gf["L"] - n0 - 1)
+    err = np.abs(y[inner] - ref[inner]).max() / np.abs(ref[inner]).max()
+    assert err < (2e-3 if deriv == 0 else 1e-2), err
+
+
+def test_gauss_asft_recursion_equals_its_kernel():
+    """The double-double attenuated recursion equals the direct convolution with the effective
+    kernel (the definition it must reach up to rounding)."""
+    x = np.random.default_rng(3).standard_normal(3000)
+    for deriv in (0, 1, 2):
+        gf = M.fit_gauss_asft(24.0, 8, deriv, 3)
+        a = D.asft_gauss(x, gf)
+        b = M.gauss_asft_direct(x, gf)
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max(), deriv
