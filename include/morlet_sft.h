@@ -43,7 +43,7 @@ typedef enum {
 } morlet_status;
 
 /* method */
-enum { MORLET_DIRECT = 0, MORLET_GAUSS = 1 };
+enum { MORLET_DIRECT = 0, MORLET_GAUSS = 1, MORLET_MULTIPLY = 2 };
 /* transform */
 enum { MORLET_SFT = 0, MORLET_ASFT = 1 };
 /* precision: arithmetic of the per-sample scan and of the cross-tile carries */
@@ -77,7 +77,8 @@ typedef struct {
   double xi;                /* Morlet centre parameter; omega0 = xi / sigma (Sec. III) */
   int32_t K;                /* Fourier terms, 1..12; 0 = smallest K whose relative fit RMSE <= fit_tol */
   double fit_tol;           /* used only when K == 0 */
-  int32_t method;           /* MORLET_DIRECT (Morlet, direct method of Sec. III-A) | MORLET_GAUSS */
+  int32_t method;           /* MORLET_DIRECT (Morlet, direct method of Sec. III-A) | MORLET_GAUSS |
+                               MORLET_MULTIPLY (Morlet, multiplication method of Sec. III-B) */
   int32_t transform;        /* MORLET_SFT | MORLET_ASFT */
   int32_t precision;        /* MORLET_FP32_PLAIN | MORLET_FP32_COMP | MORLET_FP64 */
   int32_t norm;             /* 0: e^{-k^2/2sigma^2} e^{i omega0 k}; 1: C_xi pi^{-1/4} sigma^{-1/2} (...)(e^{i xi k/sigma} - kappa_xi) */
@@ -99,6 +100,11 @@ typedef struct {
  * target is G, G_D - alpha G or G_DD - 2 alpha G_D + alpha^2 G (cos terms for the even part, sin
  * terms for the odd part); the damped window sums then give G_X[n] at output n.
  * The ASFT runs in FP32 (either FP32 precision); MORLET_FP64 with MORLET_ASFT is unsupported.
+ * MORLET_MULTIPLY (Sec. III-B): the envelope e^{-k^2/(2 sigma^2)} is fitted by K cos terms a_p
+ * (p = 0 .. K-1) and the Morlet becomes sum_{p=-(K-1)}^{K-1} a'_p e^{i (omega0 + beta p) k}
+ * (a'_0 = a_0, a'_{+-p} = a_p / 2): 2K - 1 non-harmonic window sums combined with complex weights.
+ * Built for the SFT, norm = 0, FP32 (either FP32 precision runs the FP32 scan), 2K - 1 <= 12 and
+ * L <= 4096; other cases return MORLET_ERR_UNSUPPORTED.
  * Allocates the plan's device workspace (tile table, cross-tile status, tables) and a host-mapped
  * error word; no allocation happens in forward/backward. Synchronises `stream`.
  * Errors: MORLET_ERR_ARG (bad sizes/options), MORLET_ERR_NOMEM, MORLET_ERR_CUDA.

@@ -222,6 +222,39 @@ def gauss_asft_direct(x, gf, n_idx=None):
     return conv_direct(x, ker, int(kp[0]), n_idx)
 
 
+def fit_multiply(sigma: float, xi: float, K: int, L: int | None = None):
+    """Multiplication method (Sec. III-B) for the unnormalised Morlet (norm = 0).
+
+    The envelope e^{-k^2/(2 sigma^2)} is fitted on [-L, L] by sum_{p=0}^{K-1} a_p cos(beta p k)
+    (eq. mmse); then psi[k] ~ sum_{p=-(K-1)}^{K-1} a'_p e^{i (omega0 + beta p) k} with a'_0 = a_0 and
+    a'_{+-p} = a_p / 2 (the two-sided form of the cosine series). The kappa terms of the normalised
+    Morlet are not part of this build. Returns dict(L, sigma, xi, omega0, a, rss).
+    """
+    L = window_half(sigma) if L is None else L
+    a, r = _ls_fit(np.cos, lambda k: np.exp(-k.astype(np.float64) ** 2 / (2.0 * sigma * sigma)), L, range(K))
+    return dict(L=L, sigma=float(sigma), xi=float(xi), omega0=float(xi) / sigma, a=a, rss=r)
+
+
+def kernel_multiply(mf, k=None):
+    """psi_mult[k] = sum_{p=-P}^{P} a'_p e^{i (omega0 + beta p) k}, P = K - 1, on k in [-L, L], summed
+    term by term over the 2P + 1 non-harmonic frequencies omega0 + beta p."""
+    L = mf["L"]
+    k = np.arange(-L, L + 1, dtype=np.int64) if k is None else np.asarray(k, np.int64)
+    a = mf["a"]
+    P = len(a) - 1
+    carrier = np.exp(1j * mf["omega0"] * k.astype(np.float64))
+    out = np.zeros(k.shape, np.complex128)
+    for p in range(-P, P + 1):
+        ap = a[0] if p == 0 else 0.5 * a[abs(p)]
+        out += ap * carrier * np.exp(1j * harmonic_angle(p, k, L))
+    return out
+
+
+def morlet_multiply_direct(x, mf, n_idx=None):
+    """Oracle for the multiplication method: sum_{k=-L}^{L} psi_mult[k] x[n-k]."""
+    return conv_direct(x, kernel_multiply(mf), -mf["L"], n_idx)
+
+
 # ----------------------------------------------------------------------------------------------
 # Effective kernels: what each method computes exactly (up to rounding)
 # ----------------------------------------------------------------------------------------------

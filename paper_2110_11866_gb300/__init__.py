@@ -14,7 +14,7 @@ import os
 
 __all__ = [
     "MORLET_OK", "MORLET_ERR_ARG", "MORLET_ERR_UNSUPPORTED", "MORLET_ERR_CUDA", "MORLET_ERR_TIMEOUT",
-    "MORLET_ERR_NOMEM", "MORLET_DIRECT", "MORLET_GAUSS", "MORLET_SFT", "MORLET_ASFT", "MORLET_FP32_PLAIN",
+    "MORLET_ERR_NOMEM", "MORLET_DIRECT", "MORLET_GAUSS", "MORLET_MULTIPLY", "MORLET_SFT", "MORLET_ASFT", "MORLET_FP32_PLAIN",
     "MORLET_FP32_COMP", "MORLET_FP64", "MORLET_FORM_AUTO", "MORLET_FORM_KERNEL", "MORLET_FORM_ROTATING",
     "MORLET_FLAG_NO_GRAPH", "MORLET_FLAG_AUTOTUNE", "MORLET_FLAG_NO_HALO", "MorletError", "lib", "lib_path",
     "morlet_plan", "morlet_forward", "morlet_backward", "gauss_smooth", "morlet_plan_destroy",
@@ -25,7 +25,7 @@ __all__ = [
 
 MORLET_OK, MORLET_ERR_ARG, MORLET_ERR_UNSUPPORTED, MORLET_ERR_CUDA, MORLET_ERR_TIMEOUT, MORLET_ERR_NOMEM = (
     0, -1, -2, -3, -4, -5)
-MORLET_DIRECT, MORLET_GAUSS = 0, 1
+MORLET_DIRECT, MORLET_GAUSS, MORLET_MULTIPLY = 0, 1, 2
 MORLET_SFT, MORLET_ASFT = 0, 1
 MORLET_FP32_PLAIN, MORLET_FP32_COMP, MORLET_FP64 = 0, 1, 2
 MORLET_FORM_AUTO, MORLET_FORM_KERNEL, MORLET_FORM_ROTATING = 0, 1, 2

@@ -97,6 +97,7 @@ struct ScaleTab {
   float f_cM[KMAX], f_cL[KMAX];
   float2 f_E;
   float f_kappa;
+  float2 f_kapc[KMAX];  // multiplication method: rho_j^{2L} per term (non-harmonic, complex)
 };
 
 // Table reads in the sample precision R (FP32 copies for the FP32 kernels).

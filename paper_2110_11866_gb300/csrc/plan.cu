@@ -20,6 +20,7 @@ MSFT_DECL(kernel_rf_f32c_morlet)
 MSFT_DECL(kernel_rf_f32p_morlet)
 MSFT_DECL(kernel_rf_f32p_asft)
 MSFT_DECL(kernel_rf_f32p_asft_real)
+MSFT_DECL(kernel_rf_f32p_mult)
 MSFT_DECL(kernel_rf_f64_morlet)
 MSFT_DECL(kernel_rf_f32c_real)
 MSFT_DECL(kernel_rf_f32p_real)
@@ -40,6 +41,7 @@ const void* kernel_for(int variant, int K, bool warp) {
     case V_RF_F32P_MORLET: return warp ? kernel_rf_f32p_morlet_w(K) : kernel_rf_f32p_morlet(K);
     case V_RF_F32P_ASFT: return warp ? kernel_rf_f32p_asft_w(K) : kernel_rf_f32p_asft(K);
     case V_RF_F32P_ASFT_REAL: return warp ? kernel_rf_f32p_asft_real_w(K) : kernel_rf_f32p_asft_real(K);
+    case V_RF_F32P_MULT: return warp ? kernel_rf_f32p_mult_w(K) : kernel_rf_f32p_mult(K);
     case V_RF_F64_MORLET: return warp ? kernel_rf_f64_morlet_w(K) : kernel_rf_f64_morlet(K);
     case V_KI_F32C_MORLET: return warp ? nullptr : kernel_ki_f32c_morlet(K);
     case V_KI_F32P_MORLET: return warp ? nullptr : kernel_ki_f32p_morlet(K);
@@ -182,6 +184,7 @@ int round_k(int K) {
 int variant_of(const morlet_plan_s* p, bool adjoint) {
   const int prec = p->desc.precision;
   if (adjoint) return prec == MORLET_FP64 ? V_RF_F64_ADJ : prec == MORLET_FP32_COMP ? V_RF_F32C_ADJ : V_RF_F32P_ADJ;
+  if (p->desc.method == MORLET_MULTIPLY) return V_RF_F32P_MULT;
   if (p->desc.method == MORLET_GAUSS) {
     if (p->desc.transform == MORLET_ASFT) return V_RF_F32P_ASFT_REAL;
     return prec == MORLET_FP64 ? V_RF_F64_REAL : prec == MORLET_FP32_COMP ? V_RF_F32C_REAL : V_RF_F32P_REAL;
@@ -197,6 +200,7 @@ long long floordiv(long long a, long long b) { return (a >= 0) ? a / b : -((-a +
 // Work table of one transform. Rows are (signal, scale) pairs taken in `order`; each row is cut
 // into segments by row_work (work_plan.h), which explains the precision policies.
 int seg_policy(const morlet_plan_s* p) {
+  if (p->desc.method == MORLET_MULTIPLY) return SEG_RESTART;  // window segments only (L <= 4096)
   if (p->desc.precision == MORLET_FP32_PLAIN || (p->desc.flags & MORLET_FLAG_NO_HALO)) return SEG_PLAIN;
   if (p->desc.precision == MORLET_FP32_COMP && p->desc.transform == MORLET_SFT) return SEG_RESTART;
   return SEG_ROW;
@@ -205,7 +209,8 @@ int seg_policy(const morlet_plan_s* p) {
 // Start-state rows: forward, compensated FP32 SFT in the rotating form, real input, long window.
 bool ss_row(const morlet_plan_s* p, bool adjoint, const ScaleTab& tb) {
   return !adjoint && p->ss_min_L > 0 && p->form == 2 && p->desc.precision == MORLET_FP32_COMP &&
-         p->desc.transform == MORLET_SFT && !(p->desc.flags & MORLET_FLAG_NO_HALO) && tb.L > p->ss_min_L;
+         p->desc.transform == MORLET_SFT && p->desc.method == MORLET_DIRECT &&
+         !(p->desc.flags & MORLET_FLAG_NO_HALO) && tb.L > p->ss_min_L;
 }
 
 // Lane-chunk rows: forward, compensated FP32 SFT Morlet in the rotating form, short window.
@@ -789,7 +794,13 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
   if (!d || d->n_signals < 1 || !d->lengths || d->n_scales < 1 || !d->sigmas) return MORLET_ERR_ARG;
   if (d->K < 0 || d->K > KMAX) return d->K > KMAX ? MORLET_ERR_UNSUPPORTED : MORLET_ERR_ARG;
   if (d->K == 0 && !(d->fit_tol > 0)) return MORLET_ERR_ARG;
-  if (d->method != MORLET_DIRECT && d->method != MORLET_GAUSS) return MORLET_ERR_ARG;
+  if (d->method != MORLET_DIRECT && d->method != MORLET_GAUSS && d->method != MORLET_MULTIPLY) return MORLET_ERR_ARG;
+  // multiplication method: FP32, rotating form, the unnormalised Morlet (no kappa terms), 2K - 1
+  // non-harmonic terms (K Gaussian terms given), windows up to L = 4096 (window segments)
+  if (d->method == MORLET_MULTIPLY &&
+      (d->transform != MORLET_SFT || d->precision == MORLET_FP64 || d->form == 1 || d->norm != 0 || d->K < 1 ||
+       2 * d->K - 1 > KMAX || (d->flags & MORLET_FLAG_NO_HALO)))
+    return MORLET_ERR_UNSUPPORTED;
   if (d->transform != MORLET_SFT && d->transform != MORLET_ASFT) return MORLET_ERR_ARG;
   if (d->precision < MORLET_FP32_PLAIN || d->precision > MORLET_FP64) return MORLET_ERR_ARG;
   if (d->norm != 0 && d->norm != 1) return MORLET_ERR_ARG;
@@ -843,7 +854,7 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
       J.L = (long long)ceil(wm * sg);
       J.amp = d->norm ? Cxi * pow(M_PI, -0.25) / sqrt(sg) : 1.0;
       J.kappa_xi = d->norm ? kxi : 0.0;
-      J.method = d->method == MORLET_GAUSS ? 1 : 0;
+      J.method = d->method == MORLET_GAUSS ? 1 : d->method == MORLET_MULTIPLY ? 2 : 0;
       J.deriv = d->deriv;
       J.K = d->K;
       J.fit_tol = d->fit_tol;
@@ -858,6 +869,10 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
         J.nh = kmax_fit;
       }
       if (J.ph_lo + J.nh > J.L) { rc = MORLET_ERR_ARG; goto fail; }  // harmonics must stay below beta p < pi
+      if (J.method == 2) {
+        J.deriv = 0;
+        if (J.L > 4096) { rc = MORLET_ERR_UNSUPPORTED; goto fail; }  // only window segments are built
+      }
       if (d->transform == MORLET_ASFT) {
         J.n0 = d->n0 > 0 ? d->n0 : std::max(1, (int)floor(sg / 8.0 + 0.5));
         if (J.n0 > J.L) { rc = MORLET_ERR_ARG; goto fail; }
@@ -879,7 +894,7 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
     CK(cudaStreamSynchronize(st));
     p->K_fit = 0;
     for (int s = 0; s < S; ++s) p->K_fit = std::max(p->K_fit, (int)p->h_tabs[s].K);
-    p->K_kernel = round_k(std::max(p->K_fit, 2));
+    p->K_kernel = round_k(std::max(d->method == MORLET_MULTIPLY ? 2 * p->K_fit - 1 : p->K_fit, 2));
     if (p->K_kernel < 0) { rc = MORLET_ERR_UNSUPPORTED; goto fail; }
     for (int s = 0; s < S; ++s)
       if (p->h_tabs[s].p0 + p->K_kernel > jobs[s].L) { rc = MORLET_ERR_ARG; goto fail; }

@@ -50,6 +50,7 @@ enum Variant {
   V_RF_F32P_ADJ,
   V_RF_F64_ADJ,
   V_RF_F32P_ASFT_REAL,   // ASFT Gaussian smoothing, FP32
+  V_RF_F32P_MULT,        // multiplication method, FP32
   V_COUNT
 };
 

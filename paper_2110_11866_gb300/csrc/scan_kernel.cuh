@@ -40,7 +40,10 @@
 namespace msft {
 
 enum { FORM_KI = 1, FORM_RF = 2 };
-enum { OUT_MORLET = 0, OUT_REAL = 1, OUT_ADJ = 2 };
+// Output of a position: Morlet direct method W = sum_j cM_j Re V_j + i cL_j Im V_j (complex);
+// real (Gaussian smoothing: sum_j cM_j Re V_j + cL_j Im V_j); adjoint; or a complex combine
+// W = sum_j w_j V_j with w_j = cM_j + i cL_j (multiplication method, non-harmonic terms).
+enum { OUT_MORLET = 0, OUT_REAL = 1, OUT_ADJ = 2, OUT_CPLX = 3 };
 
 template <typename R_, typename CV_, int K_, int FORM_, int OUT_, bool ASFT_, int ITEMS_>
 struct Cfg {
@@ -224,7 +227,7 @@ __device__ __forceinline__ void store_item(const KParams& P, int64_t oo, int i, 
                                            bool all_in, bool in) {
   using R = typename C::R;
   using V = typename C::V;
-  if constexpr (C::OUT == OUT_MORLET) {
+  if constexpr (C::OUT == OUT_MORLET || C::OUT == OUT_CPLX) {
     V* op = reinterpret_cast<V*>(P.out) + oo;
     if constexpr (sizeof(R) == 4) {
       if (all_in && ((reinterpret_cast<uintptr_t>(op) & 15) == 0)) {

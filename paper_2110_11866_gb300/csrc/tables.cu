@@ -36,6 +36,9 @@ __device__ void fit_target(const FitJob& J, long long k, double* tc, double* ts)
     sincos(J.omega0 * kk, &s, &c);
     *tc = J.amp * env * (c - J.kappa_xi);
     *ts = J.amp * env * s;
+  } else if (J.method == 2) {  // multiplication method (Sec. III-B): the Morlet envelope alone
+    *tc = J.amp * exp(-kk * kk / (2.0 * J.sigma * J.sigma));
+    *ts = 0.0;
   } else {  // Gaussian and its derivatives (Sec. II)
     const double g = 1.0 / (2.0 * J.sigma * J.sigma);
     const double G = sqrt(g / M_PI) * exp(-g * kk * kk);
@@ -242,7 +245,18 @@ __global__ void build_tables(ScaleTab* tabs, const FitJob* jobs, int n_scales, i
   const long long L = J.L;
   const double alpha = J.alpha;
   const bool rot = (form == 2);
+  // multiplication method: term j has the non-harmonic frequency omega_j = omega0 + beta (j - P),
+  // P = (Gaussian terms) - 1, and rho_j = e^{i omega_j}; its powers are e^{i omega0 n} (FP64 angle)
+  // times the exact harmonic e^{i beta (j - P) n}
+  const bool mult = (J.method == 2);
+  const long long Pm = mult ? (long long)tb.K - 1 : 0;
   auto power = [&](long long p, long long n) -> double2 {
+    if (mult) {
+      double sn, cs;
+      sincos(fmod(J.omega0 * (double)n, 2.0 * M_PI), &sn, &cs);
+      const double2 h = harmonic(p - tb.p0 - Pm, n, L);
+      return make_double2(cs * h.x - sn * h.y, cs * h.y + sn * h.x);
+    }
     const double2 e = harmonic(p, n, L);
     if (!rot) return e;
     const double a = exp(-alpha * (double)n);
@@ -326,6 +340,26 @@ __global__ void build_tables(ScaleTab* tabs, const FitJob* jobs, int n_scales, i
       tb.cL[j] = -gain * sg * tb.l[j];
       tb.f_cM[j] = (float)tb.cM[j];
       tb.f_cL[j] = (float)tb.cL[j];
+    }
+    if (mult) {
+      // V_j(t) = sum_{u = t - 2L}^{t} rho_j^{t - u} x[u] with the lag factor kappa_j = rho_j^{2L};
+      // c(omega) + i s(omega) at n (Sec. III-B) is e^{-i omega L} V(n + L), and the Morlet output
+      // sum_{p = -P}^{P} a'_p (c + i s)(omega_p) has the complex weights w_j = a'_j e^{-i omega_j L}
+      // (a'_0 = a_0, a'_{+-p} = a_p / 2), held as cM_j + i cL_j.
+      tb.E = make_double2(1.0, 0.0);
+      tb.kappa = 0.0;
+      for (int j = 0; j < KMAX; ++j) {
+        const long long q = j - Pm;
+        const long long aq = q < 0 ? -q : q;
+        const double ap = (j < K_kernel && aq <= Pm) ? (aq == 0 ? tb.m[0] : 0.5 * tb.m[aq]) : 0.0;
+        const double2 eL = power(tb.p0 + j, L);
+        tb.cM[j] = ap * eL.x;
+        tb.cL[j] = -ap * eL.y;
+        tb.f_cM[j] = (float)tb.cM[j];
+        tb.f_cL[j] = (float)tb.cL[j];
+        const double2 k2 = power(tb.p0 + j, 2 * L);
+        tb.f_kapc[j] = j < K_kernel ? make_float2((float)k2.x, (float)k2.y) : make_float2(0.f, 0.f);
+      }
     }
     tb.f_E = make_float2((float)tb.E.x, (float)tb.E.y);
     tb.f_kappa = (float)tb.kappa;

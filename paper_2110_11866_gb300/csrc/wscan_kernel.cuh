@@ -35,7 +35,8 @@ template <class C, bool OUT>
 __device__ __forceinline__ typename C::V step(typename C::V (&S)[C::NT], const typename C::V (&rho)[C::K],
                                               const typename C::R (&cM)[C::K], const typename C::R (&cL)[C::K],
                                               typename C::R kap, const typename C::R (&xv)[C::CH],
-                                              const typename C::R (&xlv)[C::CH]) {
+                                              const typename C::R (&xlv)[C::CH],
+                                              const typename C::V (&kapc)[C::OUT == OUT_CPLX ? C::K : 1]) {
   using R = typename C::R;
   using V = typename C::V;
   V o = V{};
@@ -44,13 +45,25 @@ __device__ __forceinline__ typename C::V step(typename C::V (&S)[C::NT], const t
 #pragma unroll
     for (int j = 0; j < C::K; ++j) {
       V& b = S[c * C::K + j];
-      const R tt = fma(-kap, xlv[c], b.x);
-      const R vr = fma(rho[j].x, tt, fma(-rho[j].y, b.y, xv[c]));
-      const R vi = fma(rho[j].y, tt, rho[j].x * b.y);
+      R vr, vi;
+      if constexpr (C::OUT == OUT_CPLX) {
+        // V <- rho (V - kappa_j x_lag) + x with the complex kappa_j = rho_j^{2L} (non-harmonic)
+        const R tr = fma(-kapc[j].x, xlv[c], b.x);
+        const R ti = fma(-kapc[j].y, xlv[c], b.y);
+        vr = fma(rho[j].x, tr, fma(-rho[j].y, ti, xv[c]));
+        vi = fma(rho[j].y, tr, rho[j].x * ti);
+      } else {
+        const R tt = fma(-kap, xlv[c], b.x);
+        vr = fma(rho[j].x, tt, fma(-rho[j].y, b.y, xv[c]));
+        vi = fma(rho[j].y, tt, rho[j].x * b.y);
+      }
       b.x = vr;
       b.y = vi;
       if constexpr (OUT) {
-        if constexpr (C::OUT == OUT_MORLET) {
+        if constexpr (C::OUT == OUT_CPLX) {
+          o.x = fma(cM[j], vr, fma(-cL[j], vi, o.x));
+          o.y = fma(cM[j], vi, fma(cL[j], vr, o.y));
+        } else if constexpr (C::OUT == OUT_MORLET) {
           o.x = fma(cM[j], vr, o.x);
           o.y = fma(cL[j], vi, o.y);
         } else if constexpr (C::OUT == OUT_REAL) {
@@ -157,6 +170,10 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
     const int64_t L = tb->L, D = tb->D;
     const int64_t Wl = GF ? 2 * L : 2 * L + 1;  // lag of the second input stream
     const R kap = TabR<R>::kappa(tb);
+    V kapc[C::OUT == OUT_CPLX ? K : 1];  // multiplication method: complex lag factor per term
+#pragma unroll
+    for (int j = 0; j < (C::OUT == OUT_CPLX ? K : 1); ++j)
+      kapc[j] = (C::OUT == OUT_CPLX) ? cmake<R>((R)tb->f_kapc[j].x, (R)tb->f_kapc[j].y) : V{};
     V rho[K], pn[GF ? K : 1];
     R cM[K], cL[K];
     R cx = 0;
@@ -271,7 +288,7 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
           for (int i = 0; i < ITEMS; ++i) {
             R xv[CH], xlv[CH];
             split_in<C>(xa[i], xl[i], xv, xlv);
-            step<C, false>(B, rho, cM, cL, kap, xv, xlv);
+            step<C, false>(B, rho, cM, cL, kap, xv, xlv, kapc);
           }
         }
       }
@@ -360,12 +377,12 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
           for (int c = 0; c < CH; ++c) dd[c] = xv[c] - xlv[c];
           o = step_g<C, true>(S, rho, cM, cL, cx, dd, xlv[0]);
         } else {
-          o = step<C, true>(S, rho, cM, cL, kap, xv, xlv);
+          o = step<C, true>(S, rho, cM, cL, kap, xv, xlv, kapc);
         }
         if constexpr (C::ASFT) o = cmul(o, E);
         return o;
       };
-      constexpr bool STAGE = (C::OUT == OUT_MORLET && sizeof(R) == 4 && ITEMS == 16);
+      constexpr bool STAGE = ((C::OUT == OUT_MORLET || C::OUT == OUT_CPLX) && sizeof(R) == 4 && ITEMS == 16);
       const int64_t tw = wi.t_a + (int64_t)k * WT;  // first position of the warp-tile
       if (tw >= t_end || tw + WT <= t_out) continue;  // no output in this warp-tile (warp-uniform)
       if constexpr (STAGE) {
@@ -431,7 +448,7 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
         const int64_t oo = wi.out_off - D + tf;
         const bool all_in = (tf >= t_out) && (tf + ITEMS <= t_end);
         bool fast = false;
-        if constexpr (C::OUT == OUT_MORLET && sizeof(R) == 4)
+        if constexpr ((C::OUT == OUT_MORLET || C::OUT == OUT_CPLX) && sizeof(R) == 4)
           fast = all_in && ((reinterpret_cast<uintptr_t>(reinterpret_cast<V*>(P.out) + oo) & 15) == 0);
         if (fast) {
           // every position of the lane stored: pairs of outputs as 16-byte streaming stores

@@ -75,6 +75,16 @@ def test_plan_descriptor_errors_without_gpu(built_lib):
          m.MORLET_ERR_UNSUPPORTED),                                         # ASFT is FP32 only
         (dict(lengths=[100], sigmas=[8.0], xi=float("inf")), m.MORLET_ERR_ARG),
         (dict(lengths=[100], sigmas=[8.0], norm=2), m.MORLET_ERR_ARG),
+        (dict(lengths=[100], sigmas=[8.0], method=3), m.MORLET_ERR_ARG),
+        # multiplication method: only the SFT, FP32, rotating form, norm = 0, 2K - 1 <= 12
+        (dict(lengths=[100], sigmas=[8.0], method=m.MORLET_MULTIPLY, transform=m.MORLET_ASFT),
+         m.MORLET_ERR_UNSUPPORTED),
+        (dict(lengths=[100], sigmas=[8.0], method=m.MORLET_MULTIPLY, precision=m.MORLET_FP64),
+         m.MORLET_ERR_UNSUPPORTED),
+        (dict(lengths=[100], sigmas=[8.0], method=m.MORLET_MULTIPLY, norm=1), m.MORLET_ERR_UNSUPPORTED),
+        (dict(lengths=[100], sigmas=[8.0], method=m.MORLET_MULTIPLY, K=7), m.MORLET_ERR_UNSUPPORTED),
+        (dict(lengths=[100], sigmas=[8.0], method=m.MORLET_MULTIPLY, form=m.MORLET_FORM_KERNEL),
+         m.MORLET_ERR_UNSUPPORTED),
     ]
     for kw, code in bad:
         with pytest.raises(m.MorletError) as err:

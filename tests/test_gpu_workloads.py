@@ -237,3 +237,35 @@ def test_gauss_smooth_asft(deriv):
             print(f"gauss asft deriv={deriv} n={n} sigma={sigma}: {e:.2e}")
             assert e < 1e-4, (n, sigma, e)
         off += n
+
+
+@pytest.mark.parametrize("K", [3, 4, 6])
+def test_multiply_method(K):
+    """The multiplication method (Sec. III-B: 2K - 1 non-harmonic window sums, complex combine) on a
+    ragged batch against the direct convolution with the oracle's own kernel; FP32 recursion, gate
+    1e-4 of max|W| like the other uncompensated form. Windows beyond L = 4096 are refused."""
+    import torch
+    rng = np.random.default_rng(40 + K)
+    lens = [30000, 7, 4097, 12000]
+    sigs = [rng.standard_normal(n).astype(np.float32) for n in lens]
+    sigmas = [8.0, 40.0, 300.0, 1000.0]
+    plan = m.morlet_plan(lens, sigmas, K=K, method=m.MORLET_MULTIPLY, precision=m.MORLET_FP32_PLAIN)
+    S, n_in = len(sigmas), sum(lens)
+    xt = torch.from_numpy(np.concatenate(sigs)).cuda()
+    W = torch.full((n_in * S,), float("nan"), dtype=torch.complex64, device="cuda")
+    m.morlet_forward(plan, xt, W)
+    torch.cuda.synchronize()
+    assert m.morlet_last_device_error(plan) == 0
+    Wh = W.cpu().numpy()
+    off = 0
+    for x, n in zip(sigs, lens):
+        for s, sigma in enumerate(sigmas):
+            ref = om.morlet_multiply_direct(x.astype(np.float64), om.fit_multiply(sigma, 6.0, K))
+            got = Wh[S * off + s * n: S * off + (s + 1) * n]
+            e = rel_err(got, ref)
+            print(f"multiply K={K} n={n} sigma={sigma}: {e:.2e}")
+            assert e < 1e-4, (n, sigma, e)
+        off += n
+    with pytest.raises(m.MorletError) as err:
+        m.morlet_plan([5000], [2000.0], K=K, method=m.MORLET_MULTIPLY)
+    assert err.value.code == m.MORLET_ERR_UNSUPPORTED

@@ -465,3 +465,52 @@ def test_gauss_asft_recursion_equals_its_kernel():
         a = D.asft_gauss(x, gf)
         b = M.gauss_asft_direct(x, gf)
         assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max(), deriv
+
+
+# ---- Multiplication method (Sec. III-B) ----
+
+def test_multiply_kernel_two_sided_series():
+    """The 2P + 1 non-harmonic terms with a'_0 = a_0, a'_{+-p} = a_p / 2 sum to the carrier times the
+    fitted cosine series of the envelope, e^{i omega0 k} sum_p a_p cos(beta p k): the two-sided form
+    the method rests on (a slip in a' or in the sign of beta p breaks it at O(a_p))."""
+    mf = M.fit_multiply(32.0, 6.0, 5)
+    L = mf["L"]
+    k = np.arange(-L, L + 1)
+    series = sum(a * np.cos(M.harmonic_angle(p, k, L)) for p, a in enumerate(mf["a"]))
+    want = np.exp(1j * mf["omega0"] * k) * series
+    got = M.kernel_multiply(mf)
+    assert np.abs(got - want).max() <= 1e-13 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("sigma,K", [(16.0, 4), (32.0, 5), (100.0, 6)])
+def test_multiply_kernel_approximates_morlet(sigma, K):
+    """|psi_mult - psi| is the envelope's fit error (|e^{i omega0 k}| = 1): the multiplication kernel
+    approximates the Morlet of Sec. III to the accuracy of the Gaussian fit, and more terms help."""
+    mf = M.fit_multiply(sigma, 6.0, K)
+    L = mf["L"]
+    k = np.arange(-L, L + 1)
+    psi = M.morlet(k, sigma, 6.0, 0)
+    env = np.exp(-k.astype(np.float64) ** 2 / (2 * sigma * sigma))
+    env_hat = sum(a * np.cos(M.harmonic_angle(p, k, L)) for p, a in enumerate(mf["a"]))
+    err = np.abs(M.kernel_multiply(mf) - psi).max()
+    assert abs(err - np.abs(env_hat - env).max()) <= 1e-12
+    assert err < 5e-3
+    worse = M.fit_multiply(sigma, 6.0, K - 1)
+    assert np.abs(M.kernel_multiply(worse) - psi).max() > err
+
+
+def test_multiply_sinusoid_closed_form():
+    """cos(nu n) through the multiplication method: W[n] is (sqrt(2 pi) sigma / 2) times
+    (e^{-sigma^2 (nu - omega0)^2 / 2} e^{i nu n} + e^{-sigma^2 (nu + omega0)^2 / 2} e^{-i nu n})
+    (the Morlet's transform at +-nu), up to the envelope's fit error, away from the ends."""
+    sigma, xi, K, nu = 32.0, 6.0, 5, 0.17
+    mf = M.fit_multiply(sigma, xi, K)
+    N = 3000
+    n = np.arange(N)
+    W = M.morlet_multiply_direct(np.cos(nu * n), mf)
+    w0 = xi / sigma
+    c = math.sqrt(2 * math.pi) * sigma / 2
+    ref = c * (math.exp(-0.5 * sigma ** 2 * (nu - w0) ** 2) * np.exp(1j * nu * n)
+               + math.exp(-0.5 * sigma ** 2 * (nu + w0) ** 2) * np.exp(-1j * nu * n))
+    inner = slice(mf["L"], N - mf["L"])
+    assert np.abs(W[inner] - ref[inner]).max() <= 5e-3 * np.abs(ref[inner]).max()
