@@ -335,8 +335,8 @@ def main():
 
 def secondary(m, torch, dev, st):
     """Context numbers on the same GPU: the plain FP64 and compensated FP32 single-signal forms (one
-    2^24-sample signal, sigma = 8192, K = 6) at their stated accuracy, and Gaussian smoothing by the
-    SFT and by the ASFT on the 64 x 65536 batch."""
+    2^24-sample signal, sigma = 8192, K = 6) at their stated accuracy, Gaussian smoothing by the SFT
+    and by the ASFT on the 64 x 65536 batch, and the multiplication method beside the direct method."""
     out = {}
     try:
         x5 = WL.c5_pink()
@@ -388,6 +388,32 @@ def secondary(m, torch, dev, st):
                          "hbm_frac_at_8B_per_output": 8.0 * n4 / (t * 1e-3) / 1e9 / peak}
             del p
         del y4, x4
+        # the multiplication method (Sec. III-B, K = 4 Gaussian terms: 7 non-harmonic terms) beside the
+        # direct method (K = 4) on the scalogram's scales with L <= 4096 (22 scales)
+        w3 = WL.c3_scalogram()
+        sig3 = [v for v in w3.sigmas if 4 * v <= 4096]
+        n3 = sum(w3.lengths) * len(sig3)
+        x3 = torch.from_numpy(w3.concat()).to(dev)
+        W3 = torch.empty(n3, dtype=torch.complex64, device=dev)
+        for name, meth, prec in (("multiply_K4_c3_L4096", m.MORLET_MULTIPLY, m.MORLET_FP32_PLAIN),
+                                 ("direct_K4_c3_L4096", m.MORLET_DIRECT, m.MORLET_FP32_COMP)):
+            p = m.morlet_plan(w3.lengths, sig3, K=4, method=meth, precision=prec)
+            for _ in range(2):
+                m.morlet_forward(p, x3, W3, st)
+            st.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            for _ in range(5):
+                m.morlet_forward(p, x3, W3, st)
+            b.record(st)
+            st.synchronize()
+            t = a.elapsed_time(b) / 5
+            out[name] = {"workload": f"c3 signals, the {len(sig3)} scales with L <= 4096, K = 4", "ms": t,
+                         "value": n3 / (t * 1e-3), "unit": "output samples/s",
+                         "hbm_frac_at_12B_per_output": 12.0 * n3 / (t * 1e-3) / 1e9 / peak}
+            del p
+        del W3, x3
     except Exception as e:  # context only; never hides the headline
         out["secondary_error"] = str(e)
     return out

@@ -209,7 +209,7 @@ int seg_policy(const morlet_plan_s* p) {
 // Start-state rows: forward, compensated FP32 SFT in the rotating form, real input, long window.
 bool ss_row(const morlet_plan_s* p, bool adjoint, const ScaleTab& tb) {
   return !adjoint && p->ss_min_L > 0 && p->form == 2 && p->desc.precision == MORLET_FP32_COMP &&
-         p->desc.transform == MORLET_SFT && p->desc.method == MORLET_DIRECT &&
+         p->desc.transform == MORLET_SFT && p->desc.method != MORLET_MULTIPLY &&
          !(p->desc.flags & MORLET_FLAG_NO_HALO) && tb.L > p->ss_min_L;
 }
 
