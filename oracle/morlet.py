@@ -222,17 +222,19 @@ def gauss_asft_direct(x, gf, n_idx=None):
     return conv_direct(x, ker, int(kp[0]), n_idx)
 
 
-def fit_multiply(sigma: float, xi: float, K: int, L: int | None = None):
+def fit_multiply(sigma: float, xi: float, K: int, L: int | None = None, norm: int = 0):
     """Multiplication method (Sec. III-B) for the unnormalised Morlet (norm = 0).
 
     The envelope e^{-k^2/(2 sigma^2)} is fitted on [-L, L] by sum_{p=0}^{K-1} a_p cos(beta p k)
     (eq. mmse); then psi[k] ~ sum_{p=-(K-1)}^{K-1} a'_p e^{i (omega0 + beta p) k} with a'_0 = a_0 and
     a'_{+-p} = a_p / 2 (the two-sided form of the cosine series). The kappa terms of the normalised
-    Morlet are not part of this build. Returns dict(L, sigma, xi, omega0, a, rss).
+    Morlet are not part of the GPU build; with norm = 1 the oracle kernel includes them:
+    C_xi pi^{-1/4} sigma^{-1/2} G_hat[k] (e^{i omega0 k} - kappa_xi), the kappa part being the
+    harmonic series itself. Returns dict(L, sigma, xi, omega0, a, rss, norm).
     """
     L = window_half(sigma) if L is None else L
     a, r = _ls_fit(np.cos, lambda k: np.exp(-k.astype(np.float64) ** 2 / (2.0 * sigma * sigma)), L, range(K))
-    return dict(L=L, sigma=float(sigma), xi=float(xi), omega0=float(xi) / sigma, a=a, rss=r)
+    return dict(L=L, sigma=float(sigma), xi=float(xi), omega0=float(xi) / sigma, a=a, rss=r, norm=norm)
 
 
 def kernel_multiply(mf, k=None):
@@ -247,12 +249,73 @@ def kernel_multiply(mf, k=None):
     for p in range(-P, P + 1):
         ap = a[0] if p == 0 else 0.5 * a[abs(p)]
         out += ap * carrier * np.exp(1j * harmonic_angle(p, k, L))
+    if mf.get("norm", 0):
+        C, kappa = morlet_constants(mf["xi"])
+        env_hat = sum(c * np.cos(harmonic_angle(p, k, L)) for p, c in enumerate(a))
+        out = C * math.pi ** -0.25 / math.sqrt(mf["sigma"]) * (out - kappa * env_hat)
     return out
 
 
 def morlet_multiply_direct(x, mf, n_idx=None):
     """Oracle for the multiplication method: sum_{k=-L}^{L} psi_mult[k] x[n-k]."""
     return conv_direct(x, kernel_multiply(mf), -mf["L"], n_idx)
+
+
+# ----------------------------------------------------------------------------------------------
+# Approximation error of the Morlet wavelet (Sec. IV, "Approximation error of the Morlet wavelet")
+# ----------------------------------------------------------------------------------------------
+
+
+def morlet_relative_rmse(kernel_hat, L: int, sigma: float, xi: float, norm: int = 1) -> float:
+    """Relative RMSE of an approximated Morlet given on [-L, L] (zero outside) against the true
+    psi_{sigma,xi}, both summed over n in [-5L, 5L] (the paper's definition)."""
+    n = np.arange(-5 * L, 5 * L + 1)
+    psi = morlet(n, sigma, xi, norm)
+    hat = np.zeros(n.shape, np.complex128)
+    hat[4 * L: 6 * L + 1] = kernel_hat
+    return float(np.sqrt(np.sum(np.abs(hat - psi) ** 2) / np.sum(np.abs(psi) ** 2)))
+
+
+def approx_error(method: str, sigma: float, xi: float, P: int, L: int, norm: int = 1):
+    """Relative RMSE of one approximation at one window: method "direct" (P terms, least-residual
+    P_S), "multiply" (2P + 1 non-harmonic terms from P + 1 envelope terms) or "truncated" (the
+    true Morlet cut to [-L, L]). Returns (rmse, P_S or None)."""
+    k = np.arange(-L, L + 1)
+    if method == "direct":
+        fit = fit_direct(sigma, xi, P, L, norm)
+        return morlet_relative_rmse(kernel_direct(fit), L, sigma, xi, norm), fit["p0"]
+    if method == "multiply":
+        mf = fit_multiply(sigma, xi, P + 1, L, norm)
+        return morlet_relative_rmse(kernel_multiply(mf), L, sigma, xi, norm), None
+    if method == "truncated":
+        return morlet_relative_rmse(morlet(k, sigma, xi, norm), L, sigma, xi, norm), None
+    raise ValueError(method)
+
+
+def best_window(method: str, sigma: float, xi: float, P: int, norm: int = 1,
+                lo_mult: float = 2.0, hi_mult: float = 6.0, coarse: int = 8):
+    """The window L in [lo_mult sigma, hi_mult sigma] with the smallest relative RMSE (the paper
+    chooses the window that way): a scan with step `coarse`, refined by single steps around the best
+    coarse point. The truncated Morlet keeps the paper's fixed interval [-3 sigma, 3 sigma].
+    Returns dict(L, rmse, p0)."""
+    if method == "truncated":
+        L = int(round(3.0 * sigma))
+        r, _ = approx_error(method, sigma, xi, P, L, norm)
+        return dict(L=L, rmse=r, p0=None)
+    lo, hi = int(math.ceil(lo_mult * sigma)), int(math.floor(hi_mult * sigma))
+    best = None
+    def visit(L):
+        nonlocal best
+        r, p0 = approx_error(method, sigma, xi, P, L, norm)
+        if best is None or r < best["rmse"]:
+            best = dict(L=L, rmse=r, p0=p0)
+    for L in range(lo, hi + 1, coarse):
+        visit(L)
+    c = best["L"]
+    for L in range(max(lo, c - coarse + 1), min(hi, c + coarse - 1) + 1):
+        if L != c:
+            visit(L)
+    return best
 
 
 # ----------------------------------------------------------------------------------------------

@@ -514,3 +514,47 @@ def test_multiply_sinusoid_closed_form():
                + math.exp(-0.5 * sigma ** 2 * (nu + w0) ** 2) * np.exp(-1j * nu * n))
     inner = slice(mf["L"], N - mf["L"])
     assert np.abs(W[inner] - ref[inner]).max() <= 5e-3 * np.abs(ref[inner]).max()
+
+
+# ---- Approximation error of the Morlet wavelet (Sec. IV, Figs. MSE1 and MSE2) ----
+
+def _sweep():
+    return _gold("morlet_approx_sweep.json")
+
+
+def test_approx_sweep_shape_matches_the_text():
+    """The stored sweep (sigma = 60, xi = 1..20, windows chosen for the least relative RMSE) has the
+    shape the paper states: with P_D = 2 P_M + 1 the direct and multiplication methods are almost
+    the same for xi >= 6; for small xi the multiplication method is worse; the optimum P_S
+    increases with xi; the direct method with P_D = 6 is about as accurate as the Morlet truncated
+    to [-3 sigma, 3 sigma]."""
+    d = _sweep()
+    rows = {r["xi"]: r for r in d["rows"]}
+    for pm in (1, 2, 3):
+        pd = 2 * pm + 1
+        for xi, r in rows.items():
+            ratio = r[f"direct_{pd}"]["rmse"] / r[f"multiply_{pm}"]["rmse"]
+            if xi >= 6:
+                assert 0.5 < ratio < 2.0, (xi, pm, ratio)
+            if xi <= 2:
+                assert ratio < 1.0, (xi, pm, ratio)
+    ps = [rows[x]["direct_6"]["p_start"] for x in sorted(rows)]
+    assert all(b >= a for a, b in zip(ps, ps[1:])) and ps[-1] > ps[0] + 10
+    trunc = _gold("truncation_3sigma.json")["relative_rmse_percent"] / 100
+    for xi, r in rows.items():
+        if xi >= 4:
+            assert abs(r["truncated_0"]["rmse"] - trunc) < 0.05 * trunc
+            assert 0.5 < r["direct_6"]["rmse"] / r["truncated_0"]["rmse"] < 2.0, xi
+
+
+@pytest.mark.parametrize("xi", [1.0, 6.0, 20.0])
+def test_approx_sweep_table_reproduces(xi):
+    """The stored values are what the oracle computes (the table is written by
+    tests/golden/make_morlet_approx_sweep.py, which calls only oracle/)."""
+    d = _sweep()
+    row = next(r for r in d["rows"] if r["xi"] == xi)
+    for case in ("direct_6", "multiply_2", "truncated_0"):
+        meth, P = case.rsplit("_", 1)
+        b = M.best_window(meth, d["sigma"], xi, int(P))
+        assert b["L"] == row[case]["L"] and b["p0"] == row[case]["p_start"]
+        assert abs(b["rmse"] - row[case]["rmse"]) <= 1e-9 * row[case]["rmse"]
