@@ -141,6 +141,23 @@ int morlet_backward(morlet_plan_t plan, const void* gW, void* gx, void* stream);
 int gauss_smooth(const void* x, int64_t N, double sigma, int32_t P, int32_t deriv, int32_t precision,
                  void* y, void* stream);
 
+/*
+ * gauss_filter_2d - separable Gaussian filtering of an image: out = (G_{deriv_y} along y) (G_{deriv_x}
+ * along x) * img. The rows and the columns of an image are independent 1-D signals (Sec. IV,
+ * opening paragraph), so this is one batched 1-D transform of eq. GsSFT (or a derivative form) over
+ * the ny rows, a transpose, one over the nx columns, and a transpose back.
+ * img, out: device arrays [ny][nx], row-major, FP32 (FP64 if precision == MORLET_FP64); they may not
+ * overlap. deriv_x, deriv_y in 0..2 (G, G_D, G_DD along that axis); harmonics p = 0..P; L =
+ * ceil(4 sigma); zero extension outside the image.
+ * Builds (first call) and caches, per (device, ny, nx, sigma, P, deriv_y, deriv_x, precision), the
+ * two 1-D plans and a workspace of 2 ny nx elements; later calls with the same key allocate nothing
+ * and are asynchronous on `stream`.
+ * Errors: MORLET_ERR_ARG (sizes, derivatives, precision; ny or nx above 2^21), MORLET_ERR_NOMEM,
+ * MORLET_ERR_CUDA, and those of morlet_plan / morlet_forward.
+ */
+int gauss_filter_2d(const void* img, int64_t ny, int64_t nx, double sigma, int32_t P, int32_t deriv_y,
+                    int32_t deriv_x, int32_t precision, void* out, void* stream);
+
 /* Release a plan and everything it owns. Synchronises the device. NULL is ignored. */
 void morlet_plan_destroy(morlet_plan_t plan);
 

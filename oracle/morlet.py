@@ -447,6 +447,16 @@ def gauss_sft_direct(x, gfit, n_idx=None):
     return conv_direct(x, kernel_gauss(gfit), -gfit["L"], n_idx)
 
 
+def gauss_filter_2d_direct(img, sigma: float, P: int, deriv_y: int, deriv_x: int):
+    """Separable 2-D Gaussian filtering (Sec. IV, 2-D signals as independent rows and columns): the
+    fitted 1-D kernel of eq. GsSFT (or its derivative form) convolved along every row (deriv_x),
+    then along every column (deriv_y); zero extension outside the image."""
+    img = np.asarray(img, dtype=np.float64)
+    gx, gy = fit_gauss(sigma, P, deriv_x), fit_gauss(sigma, P, deriv_y)
+    rows = np.stack([gauss_sft_direct(r, gx) for r in img])
+    return np.stack([gauss_sft_direct(c, gy) for c in rows.T]).T
+
+
 def adjoint_direct(g, fit, n_idx=None):
     """Transpose of x -> W = sum_k psi_hat[k] x[n-k] for real x and a real loss.
 

@@ -20,7 +20,7 @@ __all__ = [
     "morlet_plan", "morlet_forward", "morlet_backward", "gauss_smooth", "morlet_plan_destroy",
     "morlet_strerror", "morlet_last_device_error", "morlet_plan_info", "morlet_plan_stats",
     "morlet_plan_set_spin_limit", "morlet_debug_skip_tickets", "EXPORTED_SYMBOLS", "source_hash",
-    "morlet_forward_noalloc", "morlet_plan_set_row_thresholds",
+    "morlet_forward_noalloc", "morlet_plan_set_row_thresholds", "gauss_filter_2d",
 ]
 
 MORLET_OK, MORLET_ERR_ARG, MORLET_ERR_UNSUPPORTED, MORLET_ERR_CUDA, MORLET_ERR_TIMEOUT, MORLET_ERR_NOMEM = (
@@ -35,7 +35,7 @@ EXPORTED_SYMBOLS = [
     "morlet_plan", "morlet_forward", "morlet_backward", "gauss_smooth", "morlet_plan_destroy",
     "morlet_strerror", "morlet_last_device_error", "morlet_plan_info", "morlet_plan_stats",
     "morlet_plan_set_spin_limit", "morlet_debug_skip_tickets", "morlet_forward_noalloc",
-    "morlet_plan_set_row_thresholds",
+    "morlet_plan_set_row_thresholds", "gauss_filter_2d",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -103,10 +103,11 @@ def lib():
     L.morlet_plan_set_spin_limit.argtypes = [vp, i64]
     L.morlet_debug_skip_tickets.argtypes = [vp, i64]
     L.morlet_plan_set_row_thresholds.argtypes = [vp, i64, i64]
+    L.gauss_filter_2d.argtypes = [vp, i64, i64, ctypes.c_double, i32, i32, i32, i32, vp, vp]
     L.morlet_forward_noalloc.argtypes = [vp, i64, ctypes.c_double, ctypes.c_double, i32, vp, vp]
     for f in ("morlet_plan", "morlet_forward", "morlet_backward", "gauss_smooth", "morlet_last_device_error",
               "morlet_plan_info", "morlet_plan_stats", "morlet_plan_set_spin_limit", "morlet_debug_skip_tickets",
-              "morlet_forward_noalloc", "morlet_plan_set_row_thresholds"):
+              "morlet_forward_noalloc", "morlet_plan_set_row_thresholds", "gauss_filter_2d"):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
@@ -194,6 +195,13 @@ def morlet_backward(plan: Plan, gW, gx, stream=None):
 def gauss_smooth(x, N, sigma, P, deriv, precision, y, stream=None):
     _check(lib().gauss_smooth(_ptr(x), int(N), float(sigma), int(P), int(deriv), int(precision), _ptr(y),
                               _stream(stream)), "gauss_smooth")
+
+
+def gauss_filter_2d(img, ny, nx, sigma, P, deriv_y, deriv_x, precision, out, stream=None):
+    """Separable Gaussian filtering of a [ny][nx] device image (G along y and x, or their
+    derivatives): batched 1-D transforms over the rows and the columns."""
+    _check(lib().gauss_filter_2d(_ptr(img), int(ny), int(nx), float(sigma), int(P), int(deriv_y), int(deriv_x),
+                                 int(precision), _ptr(out), _stream(stream)), "gauss_filter_2d")
 
 
 def morlet_plan_destroy(plan: Plan):

@@ -52,6 +52,11 @@ def test_strerror_and_argument_errors_without_gpu(built_lib):
     assert lib.morlet_plan(ctypes.byref(h), None, None) == m.MORLET_ERR_ARG
     assert lib.morlet_forward(None, None, None, None) == m.MORLET_ERR_ARG
     assert lib.gauss_smooth(None, 0, 1.0, 3, 0, 0, None, None) == m.MORLET_ERR_ARG
+    assert lib.gauss_filter_2d(None, 4, 4, 2.0, 3, 0, 0, 0, None, None) == m.MORLET_ERR_ARG
+    buf = ctypes.create_string_buffer(64)  # a non-null pointer for the size checks (never read)
+    assert lib.gauss_filter_2d(buf, 0, 4, 2.0, 3, 0, 0, 0, buf, None) == m.MORLET_ERR_ARG
+    assert lib.gauss_filter_2d(buf, 4, 4, 2.0, 3, 3, 0, 0, buf, None) == m.MORLET_ERR_ARG
+    assert lib.gauss_filter_2d(buf, 4, 4, 2.0, 3, 0, 0, 7, buf, None) == m.MORLET_ERR_ARG
 
     assert lib.morlet_plan_set_row_thresholds(None, 128, 4096) == m.MORLET_ERR_ARG
     assert lib.morlet_plan_set_spin_limit(None, 10) == m.MORLET_ERR_ARG

@@ -558,3 +558,44 @@ def test_approx_sweep_table_reproduces(xi):
         b = M.best_window(meth, d["sigma"], xi, int(P))
         assert b["L"] == row[case]["L"] and b["p0"] == row[case]["p_start"]
         assert abs(b["rmse"] - row[case]["rmse"]) <= 1e-9 * row[case]["rmse"]
+
+
+# ---- 2-D filtering as rows and columns (Sec. IV, 2-D signals) ----
+
+def test_gauss_filter_2d_is_the_2d_convolution():
+    """Filtering the rows then the columns equals the 2-D convolution with the outer product of the
+    two fitted kernels, summed literally over the support (brute force on a small image)."""
+    rng = np.random.default_rng(8)
+    img = rng.standard_normal((23, 31))
+    sigma, P = 2.0, 3
+    got = M.gauss_filter_2d_direct(img, sigma, P, 1, 2)
+    kx = M.kernel_gauss(M.fit_gauss(sigma, P, 2))
+    ky = M.kernel_gauss(M.fit_gauss(sigma, P, 1))
+    L = (len(kx) - 1) // 2
+    ny, nx = img.shape
+    want = np.zeros_like(img)
+    for y in range(ny):
+        for x in range(nx):
+            acc = 0.0
+            for dy in range(-L, L + 1):
+                for dx in range(-L, L + 1):
+                    yy, xx = y - dy, x - dx
+                    if 0 <= yy < ny and 0 <= xx < nx:
+                        acc += ky[dy + L] * kx[dx + L] * img[yy, xx]
+            want[y, x] = acc
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_gauss_filter_2d_cosine_closed_form():
+    """cos(nu_y y) cos(nu_x x) through G along y and G_D along x: A_y A_x cos(nu_y y) (-nu_x sin(nu_x x))
+    with A = e^{-sigma^2 nu^2 / 2}, away from the edges, up to the fit error."""
+    sigma, P, ny_, nx_ = 6.0, 8, 0.07, 0.11
+    y = np.arange(120)[:, None]
+    x = np.arange(150)[None, :]
+    img = np.cos(ny_ * y) * np.cos(nx_ * x)
+    out = M.gauss_filter_2d_direct(img, sigma, P, 0, 1)
+    A = lambda nu: math.exp(-0.5 * sigma * sigma * nu * nu)
+    ref = A(ny_) * A(nx_) * np.cos(ny_ * y) * (-nx_ * np.sin(nx_ * x))
+    L = M.window_half(sigma)
+    inner = (slice(L, 120 - L), slice(L, 150 - L))
+    assert np.abs(out[inner] - ref[inner]).max() <= 1e-2 * np.abs(ref[inner]).max()
