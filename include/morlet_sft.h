@@ -66,7 +66,11 @@ enum {
                                  few row-to-kernel thresholds (see morlet_plan_stats) on a zero input and
                                  a scratch output of the batch's size, and keep the fastest (the
                                  defaults unless another choice is at least 1 % faster) */
-  MORLET_FLAG_NO_HALO = 4     /* force one look-back chain per row (no per-tile window recompute) */
+  MORLET_FLAG_NO_HALO = 4,    /* force one look-back chain per row (no per-tile window recompute) */
+  MORLET_FLAG_EDGE = 8        /* forward: extend each signal with its edge values instead of zeros
+                                 (Sec. II: "zero or the values on the edges"); the plan holds a padded
+                                 copy of the batch (the longest window reach on each side), refreshed
+                                 by every forward; morlet_backward returns MORLET_ERR_UNSUPPORTED */
 };
 
 typedef struct {

@@ -447,6 +447,13 @@ def gauss_sft_direct(x, gfit, n_idx=None):
     return conv_direct(x, kernel_gauss(gfit), -gfit["L"], n_idx)
 
 
+def edge_extended(x, E: int):
+    """x extended by E copies of its first and last values (the "values on the edges" boundary of
+    Sec. II): a transform of this array at positions [E, E + N) is the edge-extended transform of x,
+    provided E covers the window's reach."""
+    return np.pad(np.asarray(x), (E, E), mode="edge")
+
+
 def gauss_filter_2d_direct(img, sigma: float, P: int, deriv_y: int, deriv_x: int):
     """Separable 2-D Gaussian filtering (Sec. IV, 2-D signals as independent rows and columns): the
     fitted 1-D kernel of eq. GsSFT (or its derivative form) convolved along every row (deriv_x),

@@ -125,6 +125,13 @@ struct morlet_plan_s {
   std::vector<double> sigmas;
   std::vector<int64_t> x_off;
   long long n_in = 0;  // input samples of the batch (sum of lengths)
+  // MORLET_FLAG_EDGE: every signal copied into a buffer with `pad` replicated edge samples on each
+  // side; the rows run on that buffer and store only their centre
+  long long pad = 0;
+  std::vector<int64_t> xp_off;
+  long long n_xpad = 0;
+  void* d_xpad = nullptr;
+  int64_t* d_pad_desc = nullptr;  // per signal: x_off, xp_off, N
   int K_fit = 0;     // terms per scale after the fit (max over scales)
   int K_kernel = 0;  // compiled term count used
   int form = 2;
@@ -222,12 +229,12 @@ bool ls_row(const morlet_plan_s* p, bool adjoint, const ScaleTab& tb, long long 
 }
 
 // Tiles of a start-state row: tile 0 starts at t_grid (the input element of every tile start is
-// 32-byte aligned); the outputs (positions [D, D + N)) lie in tiles [kD, kE].
-void ss_tiles(long long x_off, long long N, long long D, long long& t_grid, long long& kD, long long& kE) {
+// 32-byte aligned); the stored outputs (positions [o_lo, o_hi)) lie in tiles [kD, kE].
+void ss_tiles(long long x_off, long long o_lo, long long o_hi, long long& t_grid, long long& kD, long long& kE) {
   const long long g = (8 - (x_off % 8)) % 8;
   t_grid = g - PS_TILE_H;
-  kD = (D - t_grid) / PS_TILE_H;
-  kE = (D + N - 1 - t_grid) / PS_TILE_H;
+  kD = (o_lo - t_grid) / PS_TILE_H;
+  kE = (o_hi - 1 - t_grid) / PS_TILE_H;
 }
 
 void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& work, std::vector<ChainDesc>& chains,
@@ -259,7 +266,8 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
     const ScaleTab& tb = p->h_tabs[rs.second];
     if (!ss_row(p, adjoint, tb)) continue;
     long long tg, kD, kE;
-    ss_tiles(p->x_off[rs.first], p->lengths[rs.first], tb.D, tg, kD, kE);
+    const long long E = adjoint ? 0 : p->pad;
+    ss_tiles(E ? p->xp_off[rs.first] : p->x_off[rs.first], tb.D + E, tb.D + E + p->lengths[rs.first], tg, kD, kE);
     ss_total += kE - kD + 1;
   }
   const long long n_ss = std::max(4LL, std::min(32LL, ss_total / std::max(1LL, 4 * warp_slots)));
@@ -279,12 +287,17 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
       prev_scale = s;
     }
     const ScaleTab& tb = p->h_tabs[s];
-    const long long N = p->lengths[i];
+    const long long N0 = p->lengths[i];
+    // edge mode: the row is the padded signal (N0 + 2E samples) and stores positions
+    // [D + E, D + E + N0), i.e. the outputs of the original samples
+    const long long E = adjoint ? 0 : p->pad;
+    const long long N = N0 + 2 * E;
+    const long long o_lo = tb.D + E, o_hi = tb.D + E + N0;
     ChainDesc c{};
     c.n = N;
-    const long long row = (long long)S * p->x_off[i] + (long long)s * N;  // scalogram row
-    c.x_off = adjoint ? row : p->x_off[i];
-    c.out_off = adjoint ? p->x_off[i] : row;
+    const long long row = (long long)S * p->x_off[i] + (long long)s * N0;  // scalogram row
+    c.x_off = adjoint ? row : (E ? p->xp_off[i] : p->x_off[i]);
+    c.out_off = adjoint ? p->x_off[i] : row - E;
     c.scale = s;
     const int ci = (int)chains.size();
     chains.push_back(c);
@@ -294,8 +307,9 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
       // up to three positions before D (its outputs there are masked)
       const long long Cfull = std::min<long long>(4096, std::max<long long>(1024, (8 * tb.L + LS_STEP_H - 1) / LS_STEP_H * LS_STEP_H));
       const long long pro = (2 * tb.L + LS_STEP_H - 1) / LS_STEP_H * LS_STEP_H;
-      const long long t_first = tb.D, t_last = tb.D + N;
-      long long s0 = t_first - (((c.out_off % 4) + 4) % 4);
+      const long long t_first = o_lo, t_last = o_hi;
+      const long long e0 = c.out_off + (t_first - tb.D);  // output element of t_first
+      long long s0 = t_first - (((e0 % 4) + 4) % 4);
       while (s0 < t_last) {
         const long long rem = t_last - s0;
         long long Ci = Cfull;
@@ -323,7 +337,7 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
     }
     if (ss_row(p, adjoint, tb)) {
       long long tg, kD, kE;
-      ss_tiles(c.x_off, N, tb.D, tg, kD, kE);
+      ss_tiles(c.x_off, o_lo, o_hi, tg, kD, kE);
       const long long pbase = ln.n_ptiles;
       long long k_last = kD;  // tile of the last item start
       for (long long k = kD; k <= kE; k += n_ss) {
@@ -337,8 +351,8 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
         w.n_sub = (int)nsub;
         w.t_a = tg + PS_TILE_H * k;
         w.t_dom = 0;
-        w.t_out = std::max<int64_t>(w.t_a, tb.D);
-        w.t_end = std::min<int64_t>(w.t_a + PS_TILE_H * nsub, tb.D + N);
+        w.t_out = std::max<int64_t>(w.t_a, o_lo);
+        w.t_end = std::min<int64_t>(w.t_a + PS_TILE_H * nsub, o_hi);
         w.slot = -1;
         w.slot_first = -1;
         w.p_row = pbase;
@@ -372,7 +386,7 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
     }
     const bool warp_window = (p->form != 1);
     RowSpec r{N, tb.L, tb.D, c.x_off, c.out_off, s, 32 / esz, seg_policy(p), ci,
-              warp_window ? (long long)32 * ITEMS : TILE, warp_window ? 1 : 0};
+              warp_window ? (long long)32 * ITEMS : TILE, warp_window ? 1 : 0, o_lo, o_hi};
     long long sl = slots, st = 0;
     bool chained = false;
     const long long n = row_work(r, TILE, nullptr, &sl, &st, &chained);
@@ -488,6 +502,36 @@ size_t carry_bytes(const morlet_plan_s* p) {
 //  - on `st`, the prefix-sum kernel and after it the warp kernel over the start-state items, then
 //    the look-back kernel over the chain items.
 // tickets[0..3] count the look-back, window, start-state and prefix-sum kernels.
+// Edge mode: xp[xp_off_i + j] = x[x_off_i + clamp(j - E, 0, N_i - 1)] for j in [0, N_i + 2E) (the
+// paper's "values on the edges of the interval" extension, Sec. II).
+template <typename T>
+__global__ void pad_edges_kernel(const T* __restrict__ x, T* __restrict__ xp, const int64_t* __restrict__ desc,
+                                 int64_t nsig, int64_t E) {
+  for (int64_t i = blockIdx.y; i < nsig; i += gridDim.y) {
+    const int64_t xo = desc[3 * i], po = desc[3 * i + 1], n = desc[3 * i + 2];
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n + 2 * E;
+         j += (int64_t)gridDim.x * blockDim.x) {
+      int64_t u = j - E;
+      u = u < 0 ? 0 : (u >= n ? n - 1 : u);
+      xp[po + j] = x[xo + u];
+    }
+  }
+}
+
+cudaError_t pad_edges(const morlet_plan_s* p, const void* x, cudaStream_t st) {
+  long long longest = 0;
+  for (auto n : p->lengths) longest = std::max<long long>(longest, n + 2 * p->pad);
+  const long long nsig = (long long)p->lengths.size();
+  const dim3 grid((unsigned)std::min<long long>(1024, (longest + 255) / 256), (unsigned)std::min<long long>(65535, nsig));
+  if (p->elem == 8)
+    pad_edges_kernel<double><<<grid, 256, 0, st>>>(static_cast<const double*>(x), static_cast<double*>(p->d_xpad),
+                                                   p->d_pad_desc, nsig, p->pad);
+  else
+    pad_edges_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(x), static_cast<float*>(p->d_xpad),
+                                                  p->d_pad_desc, nsig, p->pad);
+  return cudaGetLastError();
+}
+
 cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out, long long w_begin, long long w_end,
                     long long w_chain_end, unsigned long long* tickets, bool clear_flags, cudaStream_t st,
                     int accumulate = 0) {
@@ -520,6 +564,12 @@ cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out
   kp.spin_limit = p->spin;
   kp.accumulate = accumulate;
   kp.n_x = (&ln == &p->adj) ? p->n_in * (long long)p->sigmas.size() : p->n_in;  // adjoint reads the scalogram
+  if (p->pad > 0 && &ln == &p->fwd) {  // edge mode: the rows read the padded copy of x
+    e = pad_edges(p, x, st);
+    if (e != cudaSuccess) return e;
+    kp.x = p->d_xpad;
+    kp.n_x = p->n_xpad;
+  }
   kp.pbuf = p->d_pbuf;
   bool forked = false;
   const bool lane_items = ln.n_lwork > 0 && &ln == &p->fwd;
@@ -772,6 +822,8 @@ void morlet_plan_destroy(morlet_plan_t p) {
   free_launch(p->adj);
   cudaFree(p->d_tabs);
   cudaFree(p->d_jobs);
+  cudaFree(p->d_xpad);
+  cudaFree(p->d_pad_desc);
   cudaFree(p->d_phase);
   cudaFree(p->d_flags);
   cudaFree(p->d_agg);
@@ -915,13 +967,34 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
     CK(cudaMemcpyAsync(p->h_tabs.data(), p->d_tabs, sizeof(ScaleTab) * S, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
 
+    // edge mode: pad every signal by the longest reach of any scale's window (L, plus the ASFT
+    // shift n0) so that no stored output sees past the replicated samples
+    if (d->flags & MORLET_FLAG_EDGE) {
+      long long reach = 0;
+      for (int s = 0; s < S; ++s) reach = std::max<long long>(reach, jobs[s].L + jobs[s].n0);
+      p->pad = reach;
+      p->xp_off.resize(p->lengths.size());
+      std::vector<int64_t> desc(3 * p->lengths.size());
+      long long at = 0;
+      for (size_t i = 0; i < p->lengths.size(); ++i) {
+        p->xp_off[i] = at;
+        desc[3 * i] = p->x_off[i];
+        desc[3 * i + 1] = at;
+        desc[3 * i + 2] = p->lengths[i];
+        at += p->lengths[i] + 2 * reach;
+      }
+      p->n_xpad = at;
+      CK(cudaMalloc(&p->d_xpad, p->elem * (size_t)at));
+      CK(cudaMalloc(&p->d_pad_desc, sizeof(int64_t) * desc.size()));
+      CK(cudaMemcpy(p->d_pad_desc, desc.data(), sizeof(int64_t) * desc.size(), cudaMemcpyHostToDevice));
+    }
     // work tables and status arrays
     p->ss_min_L = SS_MIN_L;
     p->ls_max_L = LS_MAX_L;
     long long slots = 0;
     rc = setup_launch(p, false, p->fwd, slots);
     if (rc) goto fail;
-    const bool has_adj = d->method == MORLET_DIRECT && d->transform == MORLET_SFT;
+    const bool has_adj = d->method == MORLET_DIRECT && d->transform == MORLET_SFT && !(d->flags & MORLET_FLAG_EDGE);
     long long slots_adj = 0;
     if (has_adj) {
       rc = setup_launch(p, true, p->adj, slots_adj);

@@ -31,6 +31,7 @@ struct RowSpec {
   int chain;           // row index stored in the work items
   long long wt;        // positions per step of a window segment: a CTA sub-tile, or one warp-tile
   int warp_window;     // 1: window segments go to the warp-independent kernel
+  long long o_lo = 0, o_hi = 0;  // stored output positions [o_lo, o_hi); o_hi = 0: [D, D + N)
 };
 
 __host__ __device__ inline long long ws_floordiv(long long a, long long b) {
@@ -41,7 +42,8 @@ __host__ __device__ inline long long ws_floordiv(long long a, long long b) {
 // the number of look-back slots the row uses, *subtiles by the sub-tiles it processes.
 __host__ __device__ inline long long row_work(const RowSpec& r, long long T, WorkItem* out, long long* slots,
                                               long long* subtiles, bool* chained) {
-  const long long t_first_out = r.D, t_last_out = r.D + r.N;  // output positions [D, D + N)
+  // stored output positions: [D, D + N), or the row's window (a padded row stores its centre only)
+  const long long t_first_out = r.o_hi > 0 ? r.o_lo : r.D, t_last_out = r.o_hi > 0 ? r.o_hi : r.D + r.N;
   const bool short_window = 2 * r.L <= 2 * T;
   long long n = 0;
   *chained = !(short_window && r.policy != SEG_PLAIN);

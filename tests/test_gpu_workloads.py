@@ -293,3 +293,60 @@ def test_gauss_filter_2d(precision):
         e = rel_err(out.cpu().numpy(), ref)
         print(f"gauss 2d sigma={sigma} P={P} dy={dy} dx={dx} precision={precision}: {e:.2e}")
         assert e < (1e-12 if f64 else 1e-5), (sigma, dy, dx, e)
+
+
+@pytest.mark.parametrize("case", ["comp", "fp64", "asft", "gauss_d1"])
+def test_edge_extension(case):
+    """MORLET_FLAG_EDGE: every row kind (lane chunks, window segments, start-state items; look-back
+    chains in FP64) on ragged signals, some shorter than the window, against the oracle run on the
+    edge-padded signal; nothing is written outside the scalogram."""
+    import torch
+    rng = np.random.default_rng(70)
+    lens = [1, 5, 1000, 30000, 70001]
+    sigs = [rng.standard_normal(n) for n in lens]
+    K = 4
+    if case == "gauss_d1":
+        sigmas, P = [5.0, 40.0, 700.0, 3000.0], 6
+        kw = dict(K=P + 1, method=m.MORLET_GAUSS, deriv=1, precision=m.MORLET_FP32_COMP)
+    elif case == "asft":
+        sigmas = [8.0, 40.0, 300.0]
+        kw = dict(K=K, transform=m.MORLET_ASFT, precision=m.MORLET_FP32_PLAIN)
+    else:
+        sigmas = [8.0, 40.0, 700.0, 3000.0]
+        kw = dict(K=K, precision=m.MORLET_FP64 if case == "fp64" else m.MORLET_FP32_COMP)
+    f64 = kw["precision"] == m.MORLET_FP64
+    real = case == "gauss_d1"
+    plan = m.morlet_plan(lens, sigmas, flags=m.MORLET_FLAG_EDGE, **kw)
+    S, n_in = len(sigmas), sum(lens)
+    xs = [v if f64 else v.astype(np.float32) for v in sigs]
+    xt = torch.from_numpy(np.concatenate(xs)).cuda()
+    dt = (torch.float64 if f64 else torch.float32) if real else (torch.complex128 if f64 else torch.complex64)
+    W = torch.full((n_in * S + 8,), float("nan"), dtype=dt, device="cuda")
+    m.morlet_forward(plan, xt, W)
+    torch.cuda.synchronize()
+    assert m.morlet_last_device_error(plan) == 0
+    Wh = W.cpu().numpy()
+    assert np.all(np.isnan(Wh[n_in * S:].real))
+    off = 0
+    for x, n in zip(xs, lens):
+        xd = x.astype(np.float64)
+        for s, sg in enumerate(sigmas):
+            if real:
+                gf = om.fit_gauss(sg, P, 1)
+                E = gf["L"]
+                ref = sft_dd.sft_gauss(om.edge_extended(xd, E), gf)[E:E + n]
+            elif case == "asft":
+                E = om.window_half(sg) + om.default_n0(sg)
+                ref = oracle_forward(om.edge_extended(xd, E), sg, K, transform=m.MORLET_ASFT)[E:E + n]
+            else:
+                E = om.window_half(sg)
+                ref = oracle_forward(om.edge_extended(xd, E), sg, K)[E:E + n]
+            got = Wh[S * off + s * n: S * off + (s + 1) * n]
+            e = rel_err(got, ref)
+            tol = {"comp": 1e-5, "fp64": 1e-12, "asft": 1e-4, "gauss_d1": 1e-5}[case]
+            assert e < tol, (case, n, sg, e)
+        off += n
+    with pytest.raises(m.MorletError) as err:
+        g = torch.zeros(n_in * S, dtype=dt, device="cuda")
+        m.morlet_backward(plan, g, torch.zeros(n_in, dtype=torch.float64 if f64 else torch.float32, device="cuda"))
+    assert err.value.code == m.MORLET_ERR_UNSUPPORTED

@@ -599,3 +599,24 @@ def test_gauss_filter_2d_cosine_closed_form():
     L = M.window_half(sigma)
     inner = (slice(L, 120 - L), slice(L, 150 - L))
     assert np.abs(out[inner] - ref[inner]).max() <= 1e-2 * np.abs(ref[inner]).max()
+
+
+# ---- Edge extension (Sec. II: x extended by zeros or by the values on the edges) ----
+
+def test_edge_extension_is_the_clamped_definition():
+    """Transforming the edge-padded signal and keeping the centre equals the literal definition
+    W[n] = sum_k psi_hat[k] x[clamp(n - k, 0, N - 1)] at every n, ends included; a constant signal
+    gives c sum_k psi_hat[k] everywhere (no taper at the ends, unlike zero extension)."""
+    rng = np.random.default_rng(12)
+    x = rng.standard_normal(90)
+    sigma, K = 6.0, 4
+    fit = M.fit_direct(sigma, 6.0, K)
+    L = fit["L"]
+    psi = M.kernel_direct(fit)
+    N = len(x)
+    want = np.array([sum(psi[k + L] * x[min(max(n - k, 0), N - 1)] for k in range(-L, L + 1)) for n in range(N)])
+    got = D.sft_direct_method(M.edge_extended(x, L), fit)[L:L + N]
+    assert np.abs(got - want).max() <= 1e-13 * np.abs(want).max()
+    c = 1.7
+    const = D.sft_direct_method(M.edge_extended(np.full(N, c), L), fit)[L:L + N]
+    assert np.abs(const - c * psi.sum()).max() <= 1e-13 * c * np.abs(psi).sum()  # the sum nearly cancels
