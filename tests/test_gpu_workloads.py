@@ -327,6 +327,11 @@ def test_edge_extension(case):
     assert m.morlet_last_device_error(plan) == 0
     Wh = W.cpu().numpy()
     assert np.all(np.isnan(Wh[n_in * S:].real))
+    # Rows shorter than the window are nearly constant once extended by their edge values, and the
+    # transform of a constant nearly cancels (the wavelet's mean is small): their error is measured
+    # against sum|kernel| max|x|, the scale of the arithmetic's rounding, instead of max|W|.
+    tol = {"comp": 1e-5, "fp64": 1e-12, "asft": 1e-4, "gauss_d1": 1e-5}[case]
+    bad = []
     off = 0
     for x, n in zip(xs, lens):
         xd = x.astype(np.float64)
@@ -335,17 +340,24 @@ def test_edge_extension(case):
                 gf = om.fit_gauss(sg, P, 1)
                 E = gf["L"]
                 ref = sft_dd.sft_gauss(om.edge_extended(xd, E), gf)[E:E + n]
+                knorm = np.abs(om.kernel_gauss(gf)).sum()
             elif case == "asft":
                 E = om.window_half(sg) + om.default_n0(sg)
                 ref = oracle_forward(om.edge_extended(xd, E), sg, K, transform=m.MORLET_ASFT)[E:E + n]
+                knorm = np.abs(om.kernel_asft(om.fit_direct(sg, 6.0, K), sg, 6.0, om.default_n0(sg))[1]).sum()
             else:
                 E = om.window_half(sg)
                 ref = oracle_forward(om.edge_extended(xd, E), sg, K)[E:E + n]
+                knorm = np.abs(om.kernel_direct(om.fit_direct(sg, 6.0, K))).sum()
             got = Wh[S * off + s * n: S * off + (s + 1) * n]
-            e = rel_err(got, ref)
-            tol = {"comp": 1e-5, "fp64": 1e-12, "asft": 1e-4, "gauss_d1": 1e-5}[case]
-            assert e < tol, (case, n, sg, e)
+            scale = np.abs(ref).max()
+            if n < 2 * om.window_half(sg):
+                scale = max(scale, knorm * np.abs(xd).max())
+            e = float(np.abs(got - ref).max() / scale)
+            if not e < tol:
+                bad.append((n, sg, e))
         off += n
+    assert not bad, (case, bad)
     with pytest.raises(m.MorletError) as err:
         g = torch.zeros(n_in * S, dtype=dt, device="cuda")
         m.morlet_backward(plan, g, torch.zeros(n_in, dtype=torch.float64 if f64 else torch.float32, device="cuda"))
