@@ -144,6 +144,8 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
   // FP32 real input: the per-position loops run the terms in pairs (packed FP32)
   constexpr bool PK = GF && std::is_same<R, float>::value && CH == 1;
   constexpr bool PKM = PK && C::OUT == OUT_MORLET;
+  constexpr bool PKR = PK && C::OUT == OUT_REAL;  // real output: both parts folded into one sum
+  constexpr bool PKO = PKM || PKR;
   constexpr bool V8 = PK;  // 256-bit loads of the FP32 input runs
   constexpr int H = Pairs<K>::H;
   using EIn = typename std::conditional<CH == 2, V, R>::type;
@@ -189,9 +191,10 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
         pn[j].y = -q.y;
       }
     }
-    // packed constants of the FP32 Morlet loops (term pairs; a padded term has rho = 0, weight 0)
+    // packed constants of the FP32 Morlet and real-output loops (term pairs; a padded term has
+    // rho = 0, weight 0)
     float2 rx2[H], ry2[H], nry2[H], cm2[H], cl2[H];
-    if constexpr (PKM) {
+    if constexpr (PKO) {
 #pragma unroll
       for (int h = 0; h < H; ++h) {
         const bool two = 2 * h + 1 < K;
@@ -280,7 +283,7 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
           for (int v = 0; v < NT; ++v) {
             const R s14 = sv[v] - ev[v];
             B[v].x = fma(R(0.5) * lam[v % K], s14, ev[v]);
-            if constexpr (PKM) B[v].y = ((v & 1) ? ry2[v >> 1].y : ry2[v >> 1].x) * s14;
+            if constexpr (PKO) B[v].y = ((v & 1) ? ry2[v >> 1].y : ry2[v >> 1].x) * s14;
             else B[v].y = rho[v % K].y * s14;
           }
         } else {
@@ -342,9 +345,9 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
         }
       }
       // pass 2: outputs for positions in [t_out, t_end)
-      // packed state (Morlet output): X = (Re G_2h, Re G_2h+1), Y likewise
+      // packed state (Morlet or real output): X = (Re G_2h, Re G_2h+1), Y likewise
       float2 X2[H], Y2[H];
-      if constexpr (PKM) {
+      if constexpr (PKO) {
 #pragma unroll
         for (int h = 0; h < H; ++h) {
           const V s0 = S[2 * h], s1 = 2 * h + 1 < K ? S[2 * h + 1] : V{};
@@ -367,6 +370,19 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
             oy = pk_fma(cl2[h], vi, oy);
           }
           return cmake<R>(fma(cx, xl[i], ox.x + ox.y), oy.x + oy.y);
+        } else if constexpr (PKR) {
+          // real output: sum_j cM_j Re V_j + cL_j Im V_j, two terms per instruction
+          const float2 dd = pk_dup(xa[i] - xl[i]);
+          float2 ox = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int h = 0; h < H; ++h) {
+            const float2 vr = pk_fma(rx2[h], X2[h], pk_fma(nry2[h], Y2[h], dd));
+            const float2 vi = pk_fma(ry2[h], X2[h], pk_mul(rx2[h], Y2[h]));
+            X2[h] = vr;
+            Y2[h] = vi;
+            ox = pk_fma(cl2[h], vi, pk_fma(cm2[h], vr, ox));
+          }
+          return cmake<R>(fma(cx, xl[i], ox.x + ox.y), R(0));
         }
         R xv[CH], xlv[CH];
         split_in<C>(xa[i], xl[i], xv, xlv);
@@ -383,6 +399,7 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
         return o;
       };
       constexpr bool STAGE = ((C::OUT == OUT_MORLET || C::OUT == OUT_CPLX) && sizeof(R) == 4 && ITEMS == 16);
+      constexpr bool STAGE_R = (C::OUT == OUT_REAL && sizeof(R) == 4 && ITEMS == 16);
       const int64_t tw = wi.t_a + (int64_t)k * WT;  // first position of the warp-tile
       if (tw >= t_end || tw + WT <= t_out) continue;  // no output in this warp-tile (warp-uniform)
       if constexpr (STAGE) {
@@ -441,6 +458,39 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
             const int o = 32 * r + lane;
             if (o >= lo_o && o < hi_o) __stcs(ob + o, reinterpret_cast<const float2*>(rows + (o >> 4) * 9)[o & 15]);
           }
+        }
+        __syncwarp();
+      } else if constexpr (STAGE_R) {
+        float* obr = reinterpret_cast<float*>(P.out) + (wi.out_off - D + tw);
+        const int lo_o = (int)(t_out > tw ? t_out - tw : 0);  // stored outputs [lo_o, hi_o)
+        const int hi_o = (int)(t_end < tw + WT ? t_end - tw : WT);
+        if (lo_o == 0 && hi_o == WT && (reinterpret_cast<uintptr_t>(obr) & 31) == 0) {
+          // every output of the tile, 32-byte aligned: each lane writes its 64 bytes as two
+          // whole-sector 256-bit stores
+          float* op = obr + lane * ITEMS;
+#pragma unroll
+          for (int i = 0; i < ITEMS; i += 8) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = one(i + u).x;
+            asm volatile("st.global.cs.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(op + i), "f"(v[0]),
+                         "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+                         : "memory");
+          }
+          continue;
+        }
+        // Otherwise through this warp's shared rows (17 floats per lane: conflict-free writes), so
+        // that each store instruction writes 128 contiguous bytes; positions outside
+        // [t_out, t_end) are masked.
+        __shared__ float s_outr[WARPS * 32 * 17];
+        float* rows = s_outr + (threadIdx.x >> 5) * (32 * 17);
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) rows[lane * 17 + i] = one(i).x;
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < ITEMS; ++r) {
+          const int o = 32 * r + lane;
+          if (o >= lo_o && o < hi_o) __stcs(obr + o, rows[(o >> 4) * 17 + (o & 15)]);
         }
         __syncwarp();
       } else {
