@@ -388,16 +388,22 @@ def secondary(m, torch, dev, st):
                          "hbm_frac_at_8B_per_output": 8.0 * n4 / (t * 1e-3) / 1e9 / peak}
             del p
         del y4, x4
-        # the multiplication method (Sec. III-B, K = 4 Gaussian terms: 7 non-harmonic terms) beside the
-        # direct method (K = 4) on the scalogram's scales with L <= 4096 (22 scales)
+        # the multiplication method (Sec. III-B, K = 4 Gaussian terms: 7 non-harmonic terms) and the
+        # ASFT (Sec. II-C, K = 4) beside the direct method (K = 4) on the scalogram's scales with
+        # L <= 4096 (22 scales)
         w3 = WL.c3_scalogram()
         sig3 = [v for v in w3.sigmas if 4 * v <= 4096]
         n3 = sum(w3.lengths) * len(sig3)
         x3 = torch.from_numpy(w3.concat()).to(dev)
         W3 = torch.empty(n3, dtype=torch.complex64, device=dev)
-        for name, meth, prec in (("multiply_K4_c3_L4096", m.MORLET_MULTIPLY, m.MORLET_FP32_PLAIN),
-                                 ("direct_K4_c3_L4096", m.MORLET_DIRECT, m.MORLET_FP32_COMP)):
-            p = m.morlet_plan(w3.lengths, sig3, K=4, method=meth, precision=prec)
+        # (the ASFT also with MORLET_FLAG_NO_HALO: one look-back chain per row instead of window segments)
+        for name, meth, prec, tr, fl in (
+                ("multiply_K4_c3_L4096", m.MORLET_MULTIPLY, m.MORLET_FP32_PLAIN, m.MORLET_SFT, 0),
+                ("asft_K4_c3_L4096", m.MORLET_DIRECT, m.MORLET_FP32_PLAIN, m.MORLET_ASFT, 0),
+                ("asft_K4_c3_L4096_row_chains", m.MORLET_DIRECT, m.MORLET_FP32_PLAIN, m.MORLET_ASFT,
+                 m.MORLET_FLAG_NO_HALO),
+                ("direct_K4_c3_L4096", m.MORLET_DIRECT, m.MORLET_FP32_COMP, m.MORLET_SFT, 0)):
+            p = m.morlet_plan(w3.lengths, sig3, K=4, method=meth, precision=prec, transform=tr, flags=fl)
             for _ in range(2):
                 m.morlet_forward(p, x3, W3, st)
             st.synchronize()
@@ -414,26 +420,32 @@ def secondary(m, torch, dev, st):
                          "hbm_frac_at_12B_per_output": 12.0 * n3 / (t * 1e-3) / 1e9 / peak}
             del p
         del W3, x3
-        # the full scalogram with edge extension (MORLET_FLAG_EDGE: padded copy + centre-only rows)
+        # the full scalogram with edge extension (MORLET_FLAG_EDGE: padded copy + centre-only rows),
+        # and the full scalogram by the ASFT (FP32)
         x1 = torch.from_numpy(w3.concat()).to(dev)
         n1 = w3.n_outputs
         W1 = torch.empty(n1, dtype=torch.complex64, device=dev)
-        p = m.morlet_plan(w3.lengths, w3.sigmas, K=4, precision=m.MORLET_FP32_COMP, flags=m.MORLET_FLAG_EDGE)
-        for _ in range(2):
-            m.morlet_forward(p, x1, W1, st)
-        st.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(st)
-        for _ in range(5):
-            m.morlet_forward(p, x1, W1, st)
-        b.record(st)
-        st.synchronize()
-        t = a.elapsed_time(b) / 5
-        out["edge_extension_c3"] = {"workload": "c3 scalogram (256 signals x 32 scales, K = 4) with edge extension",
-                                    "ms": t, "value": n1 / (t * 1e-3), "unit": "output samples/s",
-                                    "hbm_frac_at_12B_per_output": 12.0 * n1 / (t * 1e-3) / 1e9 / peak}
-        del p, W1, x1
+        for name, what, kw in (("edge_extension_c3", "with edge extension",
+                                dict(precision=m.MORLET_FP32_COMP, flags=m.MORLET_FLAG_EDGE)),
+                               ("asft_K4_c3", "by the ASFT (FP32)",
+                                dict(precision=m.MORLET_FP32_PLAIN, transform=m.MORLET_ASFT))):
+            p = m.morlet_plan(w3.lengths, w3.sigmas, K=4, **kw)
+            for _ in range(2):
+                m.morlet_forward(p, x1, W1, st)
+            st.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            for _ in range(5):
+                m.morlet_forward(p, x1, W1, st)
+            b.record(st)
+            st.synchronize()
+            t = a.elapsed_time(b) / 5
+            out[name] = {"workload": f"c3 scalogram (256 signals x 32 scales, K = 4) {what}",
+                         "ms": t, "value": n1 / (t * 1e-3), "unit": "output samples/s",
+                         "hbm_frac_at_12B_per_output": 12.0 * n1 / (t * 1e-3) / 1e9 / peak}
+            del p
+        del W1, x1
         # separable 2-D Gaussian filtering of a 4096 x 4096 image (rows, transpose, columns, transpose)
         ny = nx = 4096
         im = torch.randn(ny, nx, device=dev, dtype=torch.float32)

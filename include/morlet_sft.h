@@ -104,6 +104,10 @@ typedef struct {
  * target is G, G_D - alpha G or G_DD - 2 alpha G_D + alpha^2 G (cos terms for the even part, sin
  * terms for the odd part); the damped window sums then give G_X[n] at output n.
  * The ASFT runs in FP32 (either FP32 precision); MORLET_FP64 with MORLET_ASFT is unsupported.
+ * Its window sum depends only on the last 2L + 1 samples, so in either precision a row with
+ * 2L <= 8192 is cut into independent window segments, each started from a zero state 2L samples
+ * before its first output; longer windows run one look-back chain per row (as do all rows under
+ * MORLET_FLAG_NO_HALO).
  * MORLET_MULTIPLY (Sec. III-B): the envelope e^{-k^2/(2 sigma^2)} is fitted by K cos terms a_p
  * (p = 0 .. K-1) and the Morlet becomes sum_{p=-(K-1)}^{K-1} a'_p e^{i (omega0 + beta p) k}
  * (a'_0 = a_0, a'_{+-p} = a_p / 2): 2K - 1 non-harmonic window sums combined with complex weights.

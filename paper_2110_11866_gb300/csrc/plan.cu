@@ -208,7 +208,12 @@ long long floordiv(long long a, long long b) { return (a >= 0) ? a / b : -((-a +
 // into segments by row_work (work_plan.h), which explains the precision policies.
 int seg_policy(const morlet_plan_s* p) {
   if (p->desc.method == MORLET_MULTIPLY) return SEG_RESTART;  // window segments only (L <= 4096)
-  if (p->desc.precision == MORLET_FP32_PLAIN || (p->desc.flags & MORLET_FLAG_NO_HALO)) return SEG_PLAIN;
+  if (p->desc.flags & MORLET_FLAG_NO_HALO) return SEG_PLAIN;
+  // The damped ASFT forgets its rounding history, so it needs no restarts: short windows go to window
+  // segments like every other row, long windows keep one look-back chain per row (a restart would
+  // recompute a 2L prologue per segment for nothing).
+  if (p->desc.transform == MORLET_ASFT) return SEG_ROW;
+  if (p->desc.precision == MORLET_FP32_PLAIN) return SEG_PLAIN;
   if (p->desc.precision == MORLET_FP32_COMP && p->desc.transform == MORLET_SFT) return SEG_RESTART;
   return SEG_ROW;
 }

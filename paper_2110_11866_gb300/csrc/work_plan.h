@@ -10,15 +10,18 @@ constexpr int ITEMS_DEFAULT = 16;
 constexpr long long TILE_DEFAULT = (long long)THREADS * ITEMS_DEFAULT;
 
 // Segment policies.
-//   SEG_RESTART: compensated FP32. FP32 rounding leaves about one unit of roundoff of |x| per sample
-//     in the carried window state and, with |rho| = 1, nothing ever forgets it; restarting the scan
-//     from a zero state 2L samples before each segment bounds that history to (segment + 2L)
-//     samples. Windows of 2L <= 2T samples: one CTA per segment of ceil(10 L / T) sub-tiles (the
-//     window prologue costs at most about a fifth of the segment). Longer windows: a look-back chain
-//     per segment of max(4T, 4L) outputs.
-//   SEG_ROW: one segment per row (plain FP32, whose error grows with the row length; the damped ASFT;
-//     FP64) -- windows of 2L <= 2T still go to one CTA per segment of ceil(10 L / T) sub-tiles
-//     except in the plain precision, which always keeps one look-back chain per row.
+//   SEG_RESTART: compensated FP32 SFT and the multiplication method. FP32 rounding leaves about one
+//     unit of roundoff of |x| per sample in the carried window state and, with |rho| = 1, nothing
+//     ever forgets it; restarting the scan from a zero state 2L samples before each segment bounds
+//     that history to (segment + 2L) samples. Windows of 2L <= 2T samples: independent window
+//     segments (a prologue of at most about a fifth of the segment). Longer windows: a look-back
+//     chain per segment of max(4T, 4L) outputs.
+//   SEG_ROW: FP64, and the damped ASFT in either FP32 precision (|rho| < 1 forgets the rounding
+//     history). Windows of 2L <= 2T go to window segments as above (a segment restarted from a
+//     zero state 2L samples before its first output is exact, since the window sum depends only on
+//     the last 2L + 1 samples); longer windows keep one look-back chain per row.
+//   SEG_PLAIN: plain FP32 SFT (whose error grows with the row length) and MORLET_FLAG_NO_HALO: one
+//     look-back chain per row.
 enum { SEG_RESTART = 0, SEG_ROW = 1, SEG_PLAIN = 2 };
 
 struct RowSpec {

@@ -146,7 +146,12 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
   constexpr bool PKM = PK && C::OUT == OUT_MORLET;
   constexpr bool PKR = PK && C::OUT == OUT_REAL;  // real output: both parts folded into one sum
   constexpr bool PKO = PKM || PKR;
-  constexpr bool V8 = PK;  // 256-bit loads of the FP32 input runs
+  // FP32 ASFT and multiplication method with real input: the recursion V <- rho (V - kappa x_lag) + x
+  // (kappa real, or complex per term for the multiplication method) in term pairs
+  constexpr bool APK = C::ASFT && std::is_same<R, float>::value && CH == 1 &&
+                       (C::OUT == OUT_MORLET || C::OUT == OUT_REAL || C::OUT == OUT_CPLX);
+  constexpr bool APC = APK && C::OUT == OUT_CPLX;
+  constexpr bool V8 = PK || APK;  // 256-bit loads of the FP32 input runs
   constexpr int H = Pairs<K>::H;
   using EIn = typename std::conditional<CH == 2, V, R>::type;
   const int lane = threadIdx.x & 31;
@@ -194,7 +199,7 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
     // packed constants of the FP32 Morlet and real-output loops (term pairs; a padded term has
     // rho = 0, weight 0)
     float2 rx2[H], ry2[H], nry2[H], cm2[H], cl2[H];
-    if constexpr (PKO) {
+    if constexpr (PKO || APK) {
 #pragma unroll
       for (int h = 0; h < H; ++h) {
         const bool two = 2 * h + 1 < K;
@@ -204,6 +209,15 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
         nry2[h] = make_float2(-r0.y, -r1.y);
         cm2[h] = make_float2(cM[2 * h], two ? cM[2 * h + 1] : 0.f);
         cl2[h] = make_float2(cL[2 * h], two ? cL[2 * h + 1] : 0.f);
+      }
+    }
+    float2 nkr2[APC ? H : 1], nki2[APC ? H : 1];  // -kappa_j of the multiplication method, in pairs
+    if constexpr (APC) {
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        const bool two = 2 * h + 1 < K;
+        nkr2[h] = make_float2(-kapc[2 * h].x, two ? -kapc[2 * h + 1].x : 0.f);
+        nki2[h] = make_float2(-kapc[2 * h].y, two ? -kapc[2 * h + 1].y : 0.f);
       }
     }
     const V E = TabR<R>::E(tb);
@@ -286,6 +300,34 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
             if constexpr (PKO) B[v].y = ((v & 1) ? ry2[v >> 1].y : ry2[v >> 1].x) * s14;
             else B[v].y = rho[v % K].y * s14;
           }
+        } else if constexpr (APK) {
+          // the damped recursion from zero, two terms per instruction (the scalar step's operations
+          // in the same order)
+          float2 X2[H], Y2[H];
+#pragma unroll
+          for (int h = 0; h < H; ++h) X2[h] = Y2[h] = make_float2(0.f, 0.f);
+          const float2 nk2 = pk_dup(-kap);
+#pragma unroll
+          for (int i = 0; i < ITEMS; ++i) {
+            const float2 xv2 = pk_dup(xa[i]), xl2 = pk_dup(xl[i]);
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+              float2 tt, ti;
+              if constexpr (APC) {
+                tt = pk_fma(nkr2[h], xl2, X2[h]);
+                ti = pk_fma(nki2[h], xl2, Y2[h]);
+              } else {
+                tt = pk_fma(nk2, xl2, X2[h]);
+                ti = Y2[h];
+              }
+              const float2 vr = pk_fma(rx2[h], tt, pk_fma(nry2[h], ti, xv2));
+              Y2[h] = pk_fma(ry2[h], tt, pk_mul(rx2[h], ti));
+              X2[h] = vr;
+            }
+          }
+#pragma unroll
+          for (int v = 0; v < NT; ++v)
+            B[v] = (v & 1) ? cmake<R>(X2[v >> 1].y, Y2[v >> 1].y) : cmake<R>(X2[v >> 1].x, Y2[v >> 1].x);
         } else {
 #pragma unroll
           for (int i = 0; i < ITEMS; ++i) {
@@ -347,7 +389,7 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
       // pass 2: outputs for positions in [t_out, t_end)
       // packed state (Morlet or real output): X = (Re G_2h, Re G_2h+1), Y likewise
       float2 X2[H], Y2[H];
-      if constexpr (PKO) {
+      if constexpr (PKO || APK) {
 #pragma unroll
         for (int h = 0; h < H; ++h) {
           const V s0 = S[2 * h], s1 = 2 * h + 1 < K ? S[2 * h + 1] : V{};
@@ -383,6 +425,37 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
             ox = pk_fma(cl2[h], vi, pk_fma(cm2[h], vr, ox));
           }
           return cmake<R>(fma(cx, xl[i], ox.x + ox.y), R(0));
+        } else if constexpr (APK) {
+          // damped recursion and combine, two terms per instruction, then the ASFT factor E
+          const float2 xv2 = pk_dup(xa[i]), xl2 = pk_dup(xl[i]), nk2 = pk_dup(-kap);
+          float2 ox = make_float2(0.f, 0.f), oy = make_float2(0.f, 0.f), oz = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int h = 0; h < H; ++h) {
+            float2 tt, ti;
+            if constexpr (APC) {
+              tt = pk_fma(nkr2[h], xl2, X2[h]);
+              ti = pk_fma(nki2[h], xl2, Y2[h]);
+            } else {
+              tt = pk_fma(nk2, xl2, X2[h]);
+              ti = Y2[h];
+            }
+            const float2 vr = pk_fma(rx2[h], tt, pk_fma(nry2[h], ti, xv2));
+            const float2 vi = pk_fma(ry2[h], tt, pk_mul(rx2[h], ti));
+            X2[h] = vr;
+            Y2[h] = vi;
+            if constexpr (C::OUT == OUT_MORLET) {
+              ox = pk_fma(cm2[h], vr, ox);
+              oy = pk_fma(cl2[h], vi, oy);
+            } else if constexpr (C::OUT == OUT_REAL) {
+              ox = pk_fma(cl2[h], vi, pk_fma(cm2[h], vr, ox));
+            } else {  // complex weights w_j = cM_j + i cL_j: w V
+              ox = pk_fma(cm2[h], vr, ox);
+              oz = pk_fma(cl2[h], vi, oz);
+              oy = pk_fma(cm2[h], vi, pk_fma(cl2[h], vr, oy));
+            }
+          }
+          if constexpr (APC) return cmul(cmake<R>((ox.x + ox.y) - (oz.x + oz.y), oy.x + oy.y), E);
+          return cmul(cmake<R>(ox.x + ox.y, oy.x + oy.y), E);
         }
         R xv[CH], xlv[CH];
         split_in<C>(xa[i], xl[i], xv, xlv);

@@ -220,6 +220,10 @@ def test_gauss_smooth_asft(deriv):
     P = 6
     plan = m.morlet_plan(lens, sigmas, K=P + 1, method=m.MORLET_GAUSS, transform=m.MORLET_ASFT,
                          deriv=deriv, precision=m.MORLET_FP32_PLAIN)
+    # the damped window sum forgets everything older than 2L + 1 samples: every row (L <= 2800) runs
+    # as restarted window segments, none as a look-back chain
+    st = m.morlet_plan_stats(plan)
+    assert st["rows_lookback"] == 0 and st["rows_window"] == len(lens) * len(sigmas), st
     S, n_in = len(sigmas), sum(lens)
     xt = torch.from_numpy(np.concatenate(sigs)).cuda()
     y = torch.full((n_in * S,), float("nan"), dtype=torch.float32, device="cuda")
