@@ -3,7 +3,7 @@
 Workload (default): the batched scalogram -- 256 float32 signals with lengths log-uniform in
 [1024, 1048576] (seed 2), 32 scales sigma = 2^(3 + j/3), omega0 = 6/sigma, K = 4, compensated FP32
 (FP32 scan, two-float carries and prefix sums), complex64 outputs, one graph-captured forward per
-step (lane-chunk kernel, two warp-scan launches, prefix-sum kernel). A step is one whole transform of the batch (all
+step (lane-chunk kernel, two warp-scan launches, tile-sum kernel). A step is one whole transform of the batch (all
 hot-path steps: load, rotation, scan, start states, combine, store). Metric: complex output samples per second; the roofline counts the algorithmic
 12 bytes per output (4-byte input read + 8-byte output write) against the measured copy bandwidth.
 
@@ -124,6 +124,24 @@ def dist_setup():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """The largest of the ranks' values (x itself on one rank): a job of replicas takes as long as its
+    slowest rank."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, ws: int, seconds: float) -> float:
+    """Whole-job throughput of ws replicas that each processed units_per_rank units, the job taking
+    `seconds` (the max over ranks)."""
+    return ws * units_per_rank / seconds
+
+
 def run_reference(args, ws, rank):
     """The oracle as the reference arm: each step is a bounded sample of the workload on the host."""
     if rank != 0:
@@ -234,12 +252,9 @@ def main():
     ck = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     per_launch = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, ws, dev)
     err = err or m.morlet_last_device_error(plan, st)
-    value = ws * n_out / (ms * 1e-3)
+    value = job_rate(n_out, ws, ms * 1e-3)
     peak, peak_kind = _peaks()
     launch_ms = statistics.mean(per_launch)
     achieved = n_out * BYTES_PER_OUTPUT / (launch_ms * 1e-3) / 1e9
@@ -286,11 +301,8 @@ def main():
     t1 = time.perf_counter()
     barrier()
     e2e_s = (t1 - t0) / args.e2e_steps
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": ws * n_out / e2e_s, "unit": "output samples/s",
+    e2e_s = max_over_ranks(e2e_s, ws, dev)
+    e2e = {"value": job_rate(n_out, ws, e2e_s), "unit": "output samples/s",
            "h2d_bytes_per_step": int(x_host.numel() * 4), "d2h_bytes_per_step": int(n_out * 8)}
     del out_host
 
