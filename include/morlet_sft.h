@@ -48,7 +48,8 @@ enum { MORLET_DIRECT = 0, MORLET_GAUSS = 1, MORLET_MULTIPLY = 2 };
 enum { MORLET_SFT = 0, MORLET_ASFT = 1 };
 /* precision: arithmetic of the per-sample scan and of the cross-tile carries */
 enum {
-  MORLET_FP32_PLAIN = 0,  /* FP32 samples, FP32 scan, FP32 carries, one look-back chain per row */
+  MORLET_FP32_PLAIN = 0,  /* FP32 samples, FP32 scan, FP32 carries; the SFT runs one look-back chain
+                             per row */
   MORLET_FP32_COMP = 1,   /* FP32 samples and scan; two-float (FP32 hi + lo) carries and prefix sums;
                              windows restarted per segment or started from exact prefix-sum states */
   MORLET_FP64 = 2         /* FP64 everywhere */

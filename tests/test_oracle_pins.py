@@ -620,3 +620,27 @@ def test_edge_extension_is_the_clamped_definition():
     c = 1.7
     const = D.sft_direct_method(M.edge_extended(np.full(N, c), L), fit)[L:L + N]
     assert np.abs(const - c * psi.sum()).max() <= 1e-13 * c * np.abs(psi).sum()  # the sum nearly cancels
+
+
+def test_sft_batch_is_the_per_chain_transform():
+    """The OpenMP batch entry (the timed CPU baseline and the reference arm) lays out the scalogram as
+    [signal][scale][n] and computes, per (signal, scale) chain, the same transform as the single-chain
+    O-SFT, which in turn is the direct sum with the fitted kernel; ragged lengths, including one
+    shorter than the window."""
+    rng = np.random.default_rng(31)
+    lens = [700, 5, 2049]
+    sigs = [rng.standard_normal(n) for n in lens]
+    sigmas = [3.0, 10.0, 40.0]
+    fits = [M.fit_direct(s, 6.0, 4) for s in sigmas]
+    W, used = D.sft_batch(sigs, fits, n_threads=2)
+    assert used >= 1 and W.shape == (sum(lens) * len(sigmas),)
+    off = 0
+    for x, n in zip(sigs, lens):
+        for s, fit in enumerate(fits):
+            got = W[len(sigmas) * off + s * n: len(sigmas) * off + (s + 1) * n]
+            one = D.sft_direct_method(x, fit)
+            ref = M.morlet_sft_direct(x, fit)
+            scale = np.abs(ref).max()
+            assert np.abs(got - one).max() <= 1e-14 * scale
+            assert np.abs(got - ref).max() <= 1e-12 * scale
+        off += n
