@@ -63,10 +63,13 @@ enum {
 /* flags */
 enum {
   MORLET_FLAG_NO_GRAPH = 1,   /* launch kernels directly instead of replaying a CUDA graph */
-  MORLET_FLAG_AUTOTUNE = 2,   /* compensated FP32 SFT Morlet plans: at plan time, time the forward under a
-                                 few row-to-kernel thresholds (see morlet_plan_stats) on a zero input and
-                                 a scratch output of the batch's size, and keep the fastest (the
-                                 defaults unless another choice is at least 1 % faster) */
+  MORLET_FLAG_AUTOTUNE = 2,   /* compensated FP32 SFT Morlet and ASFT plans: at plan time, time the
+                                 forward (a sub-plan with a zero input and a scratch output: the whole
+                                 batch if that scratch takes at most a quarter of the free device
+                                 memory, else every k-th signal up to 2^28 outputs) under a few
+                                 schedules -- row thresholds, segment and item lengths, row order,
+                                 ASFT chains (morlet_plan_set_schedule) -- and keep the fastest (each
+                                 knob keeps its default unless another value is at least 1 % faster) */
   MORLET_FLAG_NO_HALO = 4,    /* force one look-back chain per row (no per-tile window recompute) */
   MORLET_FLAG_EDGE = 8        /* forward: extend each signal with its edge values instead of zeros
                                  (Sec. II: "zero or the values on the edges"); the plan holds a padded
@@ -216,11 +219,39 @@ int morlet_plan_set_spin_limit(morlet_plan_t plan, int64_t polls);
  * resonant inputs). The transform is the same for every accepted choice; only the schedule
  * changes. Rebuilds the forward's work tables synchronously (device memory is freed and
  * allocated, so no forward of this plan may be in flight). Errors: MORLET_ERR_ARG for a value out
- * of those ranges; MORLET_ERR_UNSUPPORTED when the choice needs more look-back slots than the plan
- * allocated (the plan keeps its previous thresholds); MORLET_ERR_TIMEOUT if an earlier launch timed
- * out and its error word was not read yet.
+ * of those ranges; MORLET_ERR_NOMEM or MORLET_ERR_CUDA if the rebuild fails (the plan keeps its
+ * previous thresholds); MORLET_ERR_TIMEOUT if an earlier launch timed out and its error word was
+ * not read yet.
  */
 int morlet_plan_set_row_thresholds(morlet_plan_t plan, int64_t lane_chunk_max_L, int64_t start_state_min_L);
+
+/*
+ * morlet_plan_set_schedule - the forward's scheduling knobs (none changes the transform; all keep
+ * every row within the precision gates):
+ *   seg_mult (8, 12 or 16): window segments run about seg_mult * L positions after their 2L-position
+ *     restart (a longer segment spends a smaller share on the restart);
+ *   ss_tiles_max (4..64): start-state work items hold at most this many 512-position tiles;
+ *   order (0 or 1): inside each block of signals the rows go scale by scale in index order (0) or
+ *     in decreasing window length (1, so that the last work items claimed are the short ones);
+ *   asft_chains (0 or 1): ASFT plans put every row on one look-back chain (1) instead of cutting
+ *     rows with 2L <= 8192 into window segments (0).
+ * MORLET_FLAG_AUTOTUNE picks them (and the row thresholds) by timing. Rebuilds the forward's work
+ * tables synchronously (device memory is freed and allocated; no forward of this plan may be in
+ * flight). Errors: MORLET_ERR_ARG for a value out of range (the plan keeps its schedule);
+ * MORLET_ERR_TIMEOUT if an earlier launch timed out and its error word was not read yet.
+ */
+int morlet_plan_set_schedule(morlet_plan_t plan, int32_t seg_mult, int32_t ss_tiles_max, int32_t order,
+                             int32_t asft_chains);
+
+/*
+ * morlet_plan_schedule - the forward's schedule, for measurement: out[0] / out[1] = the row
+ * thresholds (as morlet_plan_stats out[12] / out[13]), out[2] = seg_mult, out[3] = ss_tiles_max,
+ * out[4] = order, out[5] = asft_chains (see morlet_plan_set_schedule), out[6] = 1 if
+ * MORLET_FLAG_AUTOTUNE timed the schedules, -1 if it was skipped because its sub-plan or scratch
+ * buffers could not be allocated (the defaults are kept), 0 without the flag; out[7] = outputs of
+ * the rows the autotuner timed (the whole batch, or the subset of every k-th signal).
+ */
+int morlet_plan_schedule(morlet_plan_t plan, int64_t out[8]);
 
 /*
  * morlet_debug_skip_tickets - testing hook: in the next forward, the first kernel that waits on
@@ -232,21 +263,40 @@ int morlet_plan_set_row_thresholds(morlet_plan_t plan, int64_t lane_chunk_max_L,
 int morlet_debug_skip_tickets(morlet_plan_t plan, int64_t skip);
 
 /*
+ * morlet_measure_fp64_rate - measurement helper, not part of the transform (the paper has no
+ * counterpart): the device's FP64 fused multiply-add rate, in flops/s (2 per FMA), written to the
+ * host double *flops. It times one launch of a kernel in which every thread runs 8 independent FMA
+ * chains (one grid of resident CTAs on every SM, after a shorter warm-up launch) with CUDA events
+ * on `stream`. It is the denominator of the FP64 path's roofline: on this GPU the FP64 transform is
+ * bound by the FP64 pipe, not by memory. Allocates and frees a small device buffer; synchronous.
+ * Errors: MORLET_ERR_ARG (flops NULL), MORLET_ERR_NOMEM, MORLET_ERR_CUDA.
+ */
+int morlet_measure_fp64_rate(double* flops, void* stream);
+
+/*
  * morlet_forward_noalloc - forward transform that allocates no memory (no cudaMalloc, no cudaFree,
  * no allocating library call), for callers that cannot allocate device memory themselves, such as
  * code running inside a framework or allocator that owns all device memory.
  * The paper has no counterpart; this is a deployment convenience of this library.
  * One real FP32 signal x[0..N-1] (device), one scale sigma, omega0 = xi / sigma, K terms (1..12),
  * SFT, compensated FP32, unnormalised Morlet (norm 0), L = ceil(4 sigma); W: device complex64[N],
- * the caller's. Results equal morlet_plan + morlet_forward with the same parameters.
- * All working memory (fit, tables, tile table, look-back status) lives in one fixed device array of
- * about 8.1 MB inside the library; every GPU that loads the library holds it until the process exits.
- * Limits: the row may need at most 16384 sub-tiles of 4096 outputs (N up to about 6.7e7 for short
- * windows) and at most 16384 look-back slots; larger sizes return MORLET_ERR_ARG.
+ * the caller's. It runs the row on window segments (L <= 4096) or look-back chains (longer windows)
+ * only, so its schedule differs from the plan path's: its results agree with the oracle and with
+ * morlet_plan + morlet_forward (same parameters) within the compensated-FP32 gate, 1e-5 of max|W|,
+ * not bit for bit.
+ * All working memory (fit, tables, work-item table, look-back status) lives in one fixed device
+ * array of about 8.1 MB inside the library; every GPU that loads the library holds it until the
+ * process exits. The work-item table is cut on the host into a file-scope host array and copied in.
+ * Limits: at most 16384 work items and 16384 look-back slots per call; larger rows return
+ * MORLET_ERR_ARG. Window segments of L <= 4096 cover max(2, ceil(16 L / 512)) * 512 - 2L - 7
+ * outputs each (N up to about 1.56e7 at sigma = 8, 5.9e7 at sigma = 64, 2.3e8 at sigma = 256);
+ * longer windows use one slot per 4096 positions of segments of max(16384, 4L) outputs, each with a
+ * 2L restart (N up to about 3.8e7 to 4.7e7).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
  * device current; make that first call before any stream capture. Each call synchronises `stream`
- * once at entry to read the error word of the previous call (MORLET_ERR_TIMEOUT if its bounded
- * cross-tile wait gave up), then enqueues its kernels asynchronously. All calls on a device share the
+ * once at entry to read the error word the previous call on the device left (MORLET_ERR_TIMEOUT if
+ * its bounded cross-tile wait gave up), then enqueues its kernels asynchronously: a timeout in the
+ * last call of a sequence is reported only by a further call. All calls on a device share the
  * array: calls whose kernels overlap on the GPU (different streams, no ordering) race and corrupt
  * each other's results; order them on one stream.
  */

@@ -63,6 +63,20 @@ def sft_direct_method(x, fit):
     return W[0::2] + 1j * W[1::2]
 
 
+def adjoint_sft(g, fit):
+    """Adjoint of the direct-method transform (real input, real loss) by the kernel integral.
+
+    With g[n] = dLoss/dRe W[n] + i dLoss/dIm W[n] the gradient is
+    dx[t] = sum_k Re(conj(g[t+k]) psi_hat[k]) (the transpose of W = sum_k psi_hat[k] x[n-k]).
+    Write g = a + i b. The fitted kernel has an even real part and an odd imaginary part (Sec. III-A:
+    cos terms m_p, sin terms l_p), so sum_k psi_hat[k] a[t+k] is the transform of a evaluated with
+    the kernel reflected, which conjugates the imaginary part: dx = Re W(a) - Im W(b), where W(.) is
+    the O-SFT transform of a real signal. Two O(N K) runs instead of the O(N L) direct transpose
+    (morlet.adjoint_direct, which this is pinned against)."""
+    g = np.asarray(g, dtype=np.complex128)
+    return sft_direct_method(g.real, fit).real - sft_direct_method(g.imag, fit).imag
+
+
 def sft_gauss(x, gfit):
     """Gaussian smoothing / derivative by the kernel integral: sum_p coef_p c_p (cos) or s_p (sin)."""
     lib = _load()

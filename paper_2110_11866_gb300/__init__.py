@@ -21,6 +21,7 @@ __all__ = [
     "morlet_strerror", "morlet_last_device_error", "morlet_plan_info", "morlet_plan_stats",
     "morlet_plan_set_spin_limit", "morlet_debug_skip_tickets", "EXPORTED_SYMBOLS", "source_hash",
     "morlet_forward_noalloc", "morlet_plan_set_row_thresholds", "gauss_filter_2d",
+    "morlet_plan_set_schedule", "morlet_plan_schedule", "morlet_measure_fp64_rate",
 ]
 
 MORLET_OK, MORLET_ERR_ARG, MORLET_ERR_UNSUPPORTED, MORLET_ERR_CUDA, MORLET_ERR_TIMEOUT, MORLET_ERR_NOMEM = (
@@ -35,7 +36,8 @@ EXPORTED_SYMBOLS = [
     "morlet_plan", "morlet_forward", "morlet_backward", "gauss_smooth", "morlet_plan_destroy",
     "morlet_strerror", "morlet_last_device_error", "morlet_plan_info", "morlet_plan_stats",
     "morlet_plan_set_spin_limit", "morlet_debug_skip_tickets", "morlet_forward_noalloc",
-    "morlet_plan_set_row_thresholds", "gauss_filter_2d",
+    "morlet_plan_set_row_thresholds", "gauss_filter_2d", "morlet_plan_set_schedule", "morlet_plan_schedule",
+    "morlet_measure_fp64_rate",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -105,9 +107,13 @@ def lib():
     L.morlet_plan_set_row_thresholds.argtypes = [vp, i64, i64]
     L.gauss_filter_2d.argtypes = [vp, i64, i64, ctypes.c_double, i32, i32, i32, i32, vp, vp]
     L.morlet_forward_noalloc.argtypes = [vp, i64, ctypes.c_double, ctypes.c_double, i32, vp, vp]
+    L.morlet_plan_set_schedule.argtypes = [vp, i32, i32, i32, i32]
+    L.morlet_plan_schedule.argtypes = [vp, ctypes.POINTER(i64)]
+    L.morlet_measure_fp64_rate.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
     for f in ("morlet_plan", "morlet_forward", "morlet_backward", "gauss_smooth", "morlet_last_device_error",
               "morlet_plan_info", "morlet_plan_stats", "morlet_plan_set_spin_limit", "morlet_debug_skip_tickets",
-              "morlet_forward_noalloc", "morlet_plan_set_row_thresholds", "gauss_filter_2d"):
+              "morlet_forward_noalloc", "morlet_plan_set_row_thresholds", "gauss_filter_2d",
+              "morlet_plan_set_schedule", "morlet_plan_schedule", "morlet_measure_fp64_rate"):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
@@ -244,6 +250,28 @@ def morlet_plan_set_row_thresholds(plan: Plan, lane_chunk_max_L: int, start_stat
     start from exact states (0 turns either off); compensated-FP32 rotating-form SFT plans only."""
     _check(lib().morlet_plan_set_row_thresholds(plan.handle, int(lane_chunk_max_L), int(start_state_min_L)),
            "morlet_plan_set_row_thresholds")
+
+
+def morlet_plan_set_schedule(plan: Plan, seg_mult: int = 16, ss_tiles_max: int = 32, order: int = 0,
+                             asft_chains: int = 0):
+    """The forward's scheduling knobs (see the C header); none changes the transform."""
+    _check(lib().morlet_plan_set_schedule(plan.handle, int(seg_mult), int(ss_tiles_max), int(order),
+                                          int(asft_chains)), "morlet_plan_set_schedule")
+
+
+def morlet_plan_schedule(plan: Plan) -> dict:
+    o = (ctypes.c_int64 * 8)()
+    _check(lib().morlet_plan_schedule(plan.handle, o), "morlet_plan_schedule")
+    keys = ["lane_chunk_max_L", "start_state_min_L", "seg_mult", "ss_tiles_max", "order", "asft_chains",
+            "autotuned", "autotune_outputs"]
+    return dict(zip(keys, list(o)))
+
+
+def morlet_measure_fp64_rate(stream=None) -> float:
+    """Measured FP64 FMA rate of the current device in flops/s (a timed kernel of FMA chains)."""
+    v = ctypes.c_double()
+    _check(lib().morlet_measure_fp64_rate(ctypes.byref(v), _stream(stream)), "morlet_measure_fp64_rate")
+    return v.value
 
 
 def morlet_debug_skip_tickets(plan: Plan, skip: int):

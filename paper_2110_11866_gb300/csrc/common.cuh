@@ -98,6 +98,10 @@ struct ScaleTab {
   float2 f_E;
   float f_kappa;
   float2 f_kapc[KMAX];  // multiplication method: rho_j^{2L} per term (non-harmonic, complex)
+  // multiplication method: weights of the imaginary part of the combine, out.y += cMy Im V + cLy Re V
+  // (equal to cM, cL for the Morlet's complex terms; zero for the kappa terms of the normalised
+  // Morlet, whose cosine kernel contributes to the real part only)
+  float f_cMy[KMAX], f_cLy[KMAX];
 };
 
 // Table reads in the sample precision R (FP32 copies for the FP32 kernels).

@@ -43,21 +43,9 @@ static __device__ __align__(256) unsigned char na_scratch[NA_SCRATCH_BYTES];
 constexpr int NA_MAX_DEVICES = 64;
 std::mutex na_mu;
 unsigned char* na_addr[NA_MAX_DEVICES] = {nullptr};
-
-// Writes the work items of the row, the same decomposition the plan uses (work_plan.h).
-__global__ void na_build_row(RowSpec r, ChainDesc* chain, WorkItem* work) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    long long slots = 0, subtiles = 0;
-    bool chained = false;
-    row_work(r, NA_TILE, work, &slots, &subtiles, &chained);
-    ChainDesc c{};
-    c.x_off = 0;
-    c.n = r.N;
-    c.out_off = 0;
-    c.scale = 0;
-    *chain = c;
-  }
-}
+// The row's work items are cut on the host (the same decomposition as the plan's, work_plan.h) into
+// this file-scope host array and copied into the scratch array with one copy; guarded by na_mu.
+WorkItem na_items[NA_MAX_ITEMS];
 
 int na_status(cudaError_t e) {
   if (e == cudaSuccess) return MORLET_OK;
@@ -85,8 +73,9 @@ extern "C" int morlet_forward_noalloc(const void* x, int64_t N, double sigma, do
   const long long pc = (long long)floor((xi / sigma) * (double)L / M_PI + 0.5);
   const long long ph_lo = std::max<long long>(0, pc - K);
   if (pc + kk > L) return MORLET_ERR_ARG;  // every harmonic p0 + j must stay below L (beta p < pi)
-  // size limits of the scratch array
-  RowSpec r{N, L, L, 0, 0, 0, 4, SEG_RESTART, 0, 32LL * NA_THREADS_ITEMS, 1};
+  // the row as the plan describes it (32-byte aligned segment starts, window segments on the warp
+  // kernel); size limits of the scratch array
+  const RowSpec r = make_row_spec(N, L, L, 0, 0, 0, (int)sizeof(float), SEG_RESTART, 0, true, NA_TILE, 0, 0, 16);
   long long n_slots = 0, n_sub = 0;
   bool chained = false;
   const long long n_work = row_work(r, NA_TILE, nullptr, &n_slots, &n_sub, &chained);
@@ -96,17 +85,14 @@ extern "C" int morlet_forward_noalloc(const void* x, int64_t N, double sigma, do
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return na_status(e);
   if (dev < 0 || dev >= NA_MAX_DEVICES) return MORLET_ERR_UNSUPPORTED;
-  unsigned char* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(na_mu);
-    if (!na_addr[dev]) {
-      void* ptr = nullptr;
-      e = cudaGetSymbolAddress(&ptr, na_scratch);  // device address of the array on this device
-      if (e != cudaSuccess || !ptr) return na_status(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
-      na_addr[dev] = (unsigned char*)ptr;
-    }
-    base = na_addr[dev];
+  std::lock_guard<std::mutex> lk(na_mu);  // the host item array and the set-up below
+  if (!na_addr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, na_scratch);  // device address of the array on this device
+    if (e != cudaSuccess || !ptr) return na_status(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+    na_addr[dev] = (unsigned char*)ptr;
   }
+  unsigned char* const base = na_addr[dev];
   cudaStream_t st = (cudaStream_t)stream;
 
   // a timeout latched by the previous call on this device is reported now
@@ -139,9 +125,16 @@ extern "C" int morlet_forward_noalloc(const void* x, int64_t N, double sigma, do
   if (e == cudaSuccess) e = run_tables(d_tab, d_job, 1, kk, NA_THREADS_ITEMS, 2, st);
   ChainDesc* d_chain = (ChainDesc*)(base + OFF_CHAIN);
   WorkItem* d_work = (WorkItem*)(base + OFF_WORK);
+  ChainDesc chain{};
+  chain.n = N;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_chain, &chain, sizeof(ChainDesc), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
-    na_build_row<<<1, 1, 0, st>>>(r, d_chain, d_work);
-    e = cudaGetLastError();
+    // host memory that is not page-locked: each copy returns once its source has been read, so the
+    // host array and the stack values above may be reused right after
+    long long s2 = 0, t2 = 0;
+    bool c2 = false;
+    row_work(r, NA_TILE, na_items, &s2, &t2, &c2);
+    e = cudaMemcpyAsync(d_work, na_items, sizeof(WorkItem) * (size_t)n_work, cudaMemcpyHostToDevice, st);
   }
   // the counter and the status flags must start at zero for every call
   if (e == cudaSuccess) e = cudaMemsetAsync(base + OFF_TICKET, 0, sizeof(unsigned long long), st);

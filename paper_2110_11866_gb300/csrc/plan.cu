@@ -145,12 +145,20 @@ struct morlet_plan_s {
   void* d_agg = nullptr;
   void* d_incl = nullptr;
   long long n_slots = 0;
+  int nt_slot = 0;               // complex carry values per look-back slot (2K with an adjoint, else K)
   uint32_t* d_pflags = nullptr;  // prefix-sum kernel: status flags, aggregates, inclusive states
   void* d_pagg = nullptr;
   void* d_pincl = nullptr;
   void* d_pbuf = nullptr;        // prefix sums at tile ends
   long long ss_min_L = 0;        // rows with L above this use start states (0: none)
   long long ls_max_L = 0;        // rows with L up to this use the lane-chunk scan (0: none)
+  // schedule knobs (MORLET_FLAG_AUTOTUNE or morlet_plan_set_schedule); none changes the transform
+  int seg_mult = 16;             // window segments of about seg_mult * L positions
+  long long ss_tiles_max = 32;   // start-state items of at most this many 512-position tiles
+  int order = 0;                 // 0: scales in index order inside a signal block; 1: decreasing L
+  int asft_chains = 0;           // ASFT: 1 = one look-back chain per row, 0 = window segments (L <= 4096)
+  int tuned = 0;                 // 1: the autotuner ran; -1: it was skipped (no scratch memory)
+  long long tune_outputs = 0;    // outputs of the rows the autotuner timed
   unsigned long long* d_ticket = nullptr;  // TICKETS counters per launch (adjoint: per scale)
   int* h_err = nullptr;                    // host-mapped error word
   int* d_err = nullptr;
@@ -207,20 +215,34 @@ long long floordiv(long long a, long long b) { return (a >= 0) ? a / b : -((-a +
 // Work table of one transform. Rows are (signal, scale) pairs taken in `order`; each row is cut
 // into segments by row_work (work_plan.h), which explains the precision policies.
 int seg_policy(const morlet_plan_s* p) {
-  if (p->desc.method == MORLET_MULTIPLY) return SEG_RESTART;  // window segments only (L <= 4096)
+  if (p->desc.method == MORLET_MULTIPLY) return SEG_RESTART;  // window segments (L <= 4096), start states beyond
   if (p->desc.flags & MORLET_FLAG_NO_HALO) return SEG_PLAIN;
   // The damped ASFT forgets its rounding history, so it needs no restarts: short windows go to window
   // segments like every other row, long windows keep one look-back chain per row (a restart would
-  // recompute a 2L prologue per segment for nothing).
-  if (p->desc.transform == MORLET_ASFT) return SEG_ROW;
+  // recompute a 2L prologue per segment for nothing). The schedule may instead put every ASFT row on
+  // one chain (fewer, longer work units: better for small batches of long windows).
+  if (p->desc.transform == MORLET_ASFT) return p->asft_chains ? SEG_PLAIN : SEG_ROW;
   if (p->desc.precision == MORLET_FP32_PLAIN) return SEG_PLAIN;
   if (p->desc.precision == MORLET_FP32_COMP && p->desc.transform == MORLET_SFT) return SEG_RESTART;
   return SEG_ROW;
 }
 
-// Start-state rows: forward, compensated FP32 SFT in the rotating form, real input, long window.
+// Plans whose long-window rows start from window sums of Horner tile sums: the ASFT (damped rho)
+// unless the schedule puts its rows on chains, and the multiplication method (non-harmonic rho).
+bool horner_plan(const morlet_plan_s* p) {
+  if (p->form != 2 || p->desc.precision == MORLET_FP64 || (p->desc.flags & MORLET_FLAG_NO_HALO)) return false;
+  return p->desc.method == MORLET_MULTIPLY || (p->desc.transform == MORLET_ASFT && !p->asft_chains);
+}
+
+// Start-state rows (forward, real input, rotating form, long window):
+//  - the compensated FP32 SFT with L > ss_min_L (window sums of Reinsch tile sums, or prefix sums);
+//  - Horner plans with 2L > 2T, the rows that would otherwise need a look-back chain (their window
+//    of 2L + 1 samples summed from FP32 tile sums; the damped sum of the ASFT forgets the tile sums'
+//    rounding, the multiplication method's sums carry it like the SFT's window sums do).
 bool ss_row(const morlet_plan_s* p, bool adjoint, const ScaleTab& tb) {
-  return !adjoint && p->ss_min_L > 0 && p->form == 2 && p->desc.precision == MORLET_FP32_COMP &&
+  if (adjoint) return false;
+  if (horner_plan(p)) return tb.L > TILE;
+  return p->ss_min_L > 0 && p->form == 2 && p->desc.precision == MORLET_FP32_COMP &&
          p->desc.transform == MORLET_SFT && p->desc.method != MORLET_MULTIPLY &&
          !(p->desc.flags & MORLET_FLAG_NO_HALO) && tb.L > p->ss_min_L;
 }
@@ -250,6 +272,13 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
   // Row order. Forward: blocks of signals holding about 16 M input samples, scale by scale inside a
   // block, so that a block's samples are mostly served from L2 to its later scales. Adjoint:
   // scale-major (each scale is one launch that adds into the gradient).
+  // With p->order = 1 the scales of a block go in decreasing L, so that the last items claimed are the
+  // short ones and the kernels' tails are short.
+  std::vector<int> sorder(S);
+  for (int s = 0; s < S; ++s) sorder[s] = s;
+  if (p->order == 1 && !adjoint)
+    std::stable_sort(sorder.begin(), sorder.end(),
+                     [p](int a, int b) { return p->h_tabs[a].L > p->h_tabs[b].L; });
   std::vector<std::pair<long long, int>> order;  // (signal, scale)
   if (adjoint) {
     for (int s = 0; s < S; ++s)
@@ -259,8 +288,8 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
     while (b0 < nsig) {
       long long b1 = b0, acc = 0;
       while (b1 < nsig && (b1 == b0 || acc + p->lengths[b1] <= (16LL << 20))) acc += p->lengths[b1++];
-      for (int s = 0; s < S; ++s)
-        for (long long i = b0; i < b1; ++i) order.push_back({i, s});
+      for (int q = 0; q < S; ++q)
+        for (long long i = b0; i < b1; ++i) order.push_back({i, sorder[q]});
       b0 = b1;
     }
   }
@@ -275,13 +304,13 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
     ss_tiles(E ? p->xp_off[rs.first] : p->x_off[rs.first], tb.D + E, tb.D + E + p->lengths[rs.first], tg, kD, kE);
     ss_total += kE - kD + 1;
   }
-  const long long n_ss = std::max(4LL, std::min(32LL, ss_total / std::max(1LL, 4 * warp_slots)));
+  const long long n_ss = std::max(4LL, std::min(p->ss_tiles_max, ss_total / std::max(1LL, 4 * warp_slots)));
   // A start state costs a window sum over its 2L / 512 tiles: cheap next to an item of n_ss tiles
   // unless the window is much longer; then the prefix sums (one chained pass) are used instead.
   long long max_win = 0;
   for (auto& rs : order)
     if (ss_row(p, adjoint, p->h_tabs[rs.second])) max_win = std::max<long long>(max_win, 2 * p->h_tabs[rs.second].L / PS_TILE_H + 2);
-  ln.ss_window = (max_win <= 16 * n_ss) ? 1 : 0;
+  ln.ss_window = (horner_plan(p) || max_win <= 16 * n_ss) ? 1 : 0;  // Horner rows: window sums only
   ln.scale_begin.assign(S + 1, 0);
   int prev_scale = -1;
   for (auto& rs : order) {
@@ -390,8 +419,8 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
       continue;
     }
     const bool warp_window = (p->form != 1);
-    RowSpec r{N, tb.L, tb.D, c.x_off, c.out_off, s, 32 / esz, seg_policy(p), ci,
-              warp_window ? (long long)32 * ITEMS : TILE, warp_window ? 1 : 0, o_lo, o_hi};
+    const RowSpec r = make_row_spec(N, tb.L, tb.D, c.x_off, c.out_off, s, esz, seg_policy(p), ci, warp_window,
+                                    TILE, o_lo, o_hi, p->seg_mult);
     long long sl = slots, st = 0;
     bool chained = false;
     const long long n = row_work(r, TILE, nullptr, &sl, &st, &chained);
@@ -440,6 +469,9 @@ int setup_launch(morlet_plan_s* p, bool adjoint, Launch& ln, long long& slots) {
   }
   build_work(p, adjoint, work, chains, slots, ln, pwork, lwork, (long long)ln.grid_w * WARPS);
   ln.n_work = (long long)work.size();
+  // the multiplication method's combine (separate weights for the imaginary part) is built into the
+  // warp kernel only: its rows are window segments or start-state items, never look-back chains
+  if (p->desc.method == MORLET_MULTIPLY && ln.rows_chain > 0) return MORLET_ERR_UNSUPPORTED;
   {
     int occ = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ln.func, THREADS, 0));
@@ -447,7 +479,8 @@ int setup_launch(morlet_plan_s* p, bool adjoint, Launch& ln, long long& slots) {
     ln.grid = (int)std::min<long long>((long long)occ * p->sms, std::max<long long>(1, ln.n_work));
   }
   if (!pwork.empty()) {
-    ln.func_p = ln.ss_window ? kernel_tsum(p->K_kernel) : kernel_psum(p->K_kernel);
+    ln.func_p = horner_plan(p) ? kernel_tsum_h(p->K_kernel)
+                : ln.ss_window ? kernel_tsum(p->K_kernel) : kernel_psum(p->K_kernel);
     if (!ln.func_p) return MORLET_ERR_UNSUPPORTED;
     int occp = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occp, ln.func_p, THREADS, 0));
@@ -699,14 +732,37 @@ cudaError_t forward_graph(morlet_plan_s* p, const void* x, void* W) {
   return cudaSuccess;
 }
 
-// (Re)build the forward launch and its prefix-sum workspace for the plan's current row thresholds
-// (ls_max_L, ss_min_L). `slots` returns the look-back slots the forward needs.
+// Look-back status arrays for n slots (flags, aggregates, inclusive values), replacing the old ones.
+int alloc_slots(morlet_plan_s* p, long long n) {
+  int rc = MORLET_OK;
+  cudaFree(p->d_flags);
+  cudaFree(p->d_agg);
+  cudaFree(p->d_incl);
+  p->d_flags = nullptr;
+  p->d_agg = p->d_incl = nullptr;
+  p->n_slots = 0;
+  if (n > 0) {
+    CK(cudaMalloc(&p->d_flags, sizeof(uint32_t) * n));
+    CK(cudaMalloc(&p->d_agg, carry_bytes(p) * p->nt_slot * n));
+    CK(cudaMalloc(&p->d_incl, carry_bytes(p) * p->nt_slot * n));
+    p->n_slots = n;
+  }
+  return MORLET_OK;
+fail:
+  return rc;
+}
+
+// (Re)build the forward launch and its prefix-sum workspace for the plan's current schedule (row
+// thresholds ls_max_L / ss_min_L and the knobs seg_mult, ss_tiles_max, order, asft_chains); grows
+// the look-back status arrays if the new schedule needs more slots. Synchronous (frees and
+// allocates device memory). `slots` returns the look-back slots the forward needs.
 int build_forward(morlet_plan_s* p, long long& slots) {
   int rc = MORLET_OK;
   if (p->gexec) {
     cudaGraphExecDestroy(p->gexec);
     p->gexec = nullptr;
   }
+  cudaDeviceSynchronize();
   free_launch(p->fwd);
   p->fwd = Launch{};
   cudaFree(p->d_pflags);
@@ -718,87 +774,238 @@ int build_forward(morlet_plan_s* p, long long& slots) {
   slots = 0;
   rc = setup_launch(p, false, p->fwd, slots);
   if (rc) return rc;
+  if (slots > p->n_slots) {
+    rc = alloc_slots(p, slots);
+    if (rc) return rc;
+  }
   if (p->fwd.n_pwork > 0) return alloc_prefix(p);
   return MORLET_OK;
 }
 
-// MORLET_FLAG_AUTOTUNE: time the forward of this plan's batch (zero input, scratch output) under a
-// few choices of which rows take the lane-chunk scan (L <= ls_max_L) and which start from prefix
-// sums (L > ss_min_L), and keep the fastest. Only the compensated rotating-form SFT Morlet plans
-// have these choices; others, or a batch whose scratch output does not fit in memory, keep the
-// defaults.
+// One point of the schedule space.
+struct Sched {
+  long long ls, ss;   // row thresholds: lane-chunk rows L <= ls, start-state rows L > ss
+  int seg_mult;       // window segments of about seg_mult * L positions
+  int order;          // scale order inside a signal block
+  long long ss_tiles; // start-state item size limit (tiles)
+  int asft_chains;    // ASFT rows on one look-back chain each
+};
+
+Sched get_sched(const morlet_plan_s* p) {
+  return Sched{p->ls_max_L, p->ss_min_L, p->seg_mult, p->order, p->ss_tiles_max, p->asft_chains};
+}
+
+void put_sched(morlet_plan_s* p, const Sched& c) {
+  p->ls_max_L = c.ls;
+  p->ss_min_L = c.ss;
+  p->seg_mult = c.seg_mult;
+  p->order = c.order;
+  p->ss_tiles_max = c.ss_tiles;
+  p->asft_chains = c.asft_chains;
+}
+
+// Compensated FP32 SFT Morlet plans in the rotating form: the plans with row-kind choices.
+bool sft_schedulable(const morlet_plan_s* p) {
+  const morlet_plan_desc& d = p->desc;
+  return p->form == 2 && d.precision == MORLET_FP32_COMP && d.transform == MORLET_SFT && d.method == MORLET_DIRECT;
+}
+
+constexpr long long TUNE_OUTPUTS = 1LL << 28;  // outputs of the subset the autotuner times when the batch is too big
+
+// MORLET_FLAG_AUTOTUNE: time the forward of this plan's rows under a few schedules and keep the
+// fastest. The rows timed are a sub-plan (the same scales and options) with its own scratch input
+// and output: the whole batch when that scratch takes at most a quarter of the free device memory
+// (the fastest schedule depends on the batch's parallelism: a subset of the signals leaves some
+// kernels too few work items), otherwise every k-th signal up to TUNE_OUTPUTS outputs. Each
+// candidate is timed as replays of its captured forward graph, the way morlet_forward runs it.
+// Knobs are tried one at a time, each with the best values of the knobs before it:
+//  - compensated FP32 SFT Morlet: the row thresholds (8 pairs within the precision limits), the
+//    window-segment length (8, 12, 16 L), the scale order inside a signal block, the start-state
+//    item size (16, 32, 64 tiles);
+//  - the ASFT: one look-back chain per row against window segments, then the segment length.
+// Each candidate is timed twice (interleaved passes, the faster kept), and a knob keeps its current
+// value unless another is at least 1 % faster. Every schedule computes the same transform. If the
+// sub-plan or its scratch buffers cannot be allocated the plan keeps its defaults and reports the
+// tuner as skipped (morlet_plan_schedule).
 int autotune(morlet_plan_s* p, cudaStream_t st) {
   const morlet_plan_desc& d = p->desc;
-  if (!(p->form == 2 && d.precision == MORLET_FP32_COMP && d.transform == MORLET_SFT && d.method == MORLET_DIRECT))
-    return MORLET_OK;
+  const bool sft = sft_schedulable(p);
+  const bool asft = d.transform == MORLET_ASFT && !(d.flags & MORLET_FLAG_NO_HALO);
+  if (!sft && !asft) return MORLET_OK;
   const long long S = (long long)p->sigmas.size();
+  const long long nsig = (long long)p->lengths.size();
+  const long long total = p->n_in * S;
+  const size_t out_elem = (d.method == MORLET_GAUSS ? 1 : 2) * p->elem;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    free_b = 0;
+  }
+  const bool whole = (double)(out_elem * S + p->elem) * (double)p->n_in <= 0.25 * (double)free_b;
+  const long long k = whole ? 1 : std::max(1LL, (total + TUNE_OUTPUTS - 1) / TUNE_OUTPUTS);
+  std::vector<int64_t> sub;
+  long long acc = 0;
+  for (long long i = 0; i < nsig; i += k) {
+    if (!whole && !sub.empty() && (acc + p->lengths[i]) * S > TUNE_OUTPUTS) break;
+    sub.push_back(p->lengths[i]);
+    acc += p->lengths[i];
+  }
+  morlet_plan_desc sd = d;
+  sd.n_signals = (int64_t)sub.size();
+  sd.lengths = sub.data();
+  sd.sigmas = p->sigmas.data();
+  sd.flags &= ~MORLET_FLAG_AUTOTUNE;
+  morlet_plan_t q = nullptr;
+  int rc = morlet_plan(&q, &sd, st);
+  if (rc == MORLET_ERR_NOMEM) {
+    cudaGetLastError();
+    p->tuned = -1;
+    return MORLET_OK;
+  }
+  if (rc) return rc;
   void* x = nullptr;
   void* W = nullptr;
-  if (cudaMalloc(&x, sizeof(float) * std::max(1LL, p->n_in)) != cudaSuccess ||
-      cudaMalloc(&W, sizeof(float2) * std::max(1LL, p->n_in * S)) != cudaSuccess) {
+  if (cudaMalloc(&x, p->elem * std::max(1LL, acc)) != cudaSuccess ||
+      cudaMalloc(&W, out_elem * std::max(1LL, acc * S)) != cudaSuccess) {
     cudaFree(x);
     cudaFree(W);
     cudaGetLastError();
+    morlet_plan_destroy(q);
+    p->tuned = -1;
     return MORLET_OK;
   }
-  int rc = MORLET_OK;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  const long long cand[][2] = {{LS_MAX_L, SS_MIN_L}, {256, SS_MIN_L}, {64, SS_MIN_L}, {0, SS_MIN_L},
-                               {LS_MAX_L, 1024},     {256, 1024},     {64, 1024},       {0, 1024}};
-  constexpr int NC = (int)(sizeof(cand) / sizeof(cand[0]));
-  float tmin[NC];
-  for (int i = 0; i < NC; ++i) tmin[i] = -1.f;
-  long long best_ls = LS_MAX_L, best_ss = SS_MIN_L;
-  CK(cudaMemsetAsync(x, 0, sizeof(float) * std::max(1LL, p->n_in), st));
+  Sched best = get_sched(p);
+  float t_best = -1.f;
+  // times one schedule on the sub-plan: mean of 3 graph replays after one warm-up; -1 if it cannot run
+  auto time_one = [&](const Sched& c, float& ms) -> int {
+    ms = -1.f;
+    put_sched(q, c);
+    long long slots = 0;
+    int r = build_forward(q, slots);
+    if (r == MORLET_ERR_NOMEM) {
+      cudaGetLastError();
+      return MORLET_OK;
+    }
+    if (r) return r;
+    cudaError_t e = forward_graph(q, x, W);
+    if (e == cudaSuccess) e = cudaGraphLaunch(q->gexec, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaGraphLaunch(q->gexec, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (q->h_err && *(volatile int*)q->h_err) {  // a timed-out wait: not a candidate
+      *(volatile int*)q->h_err = 0;
+      return MORLET_OK;
+    }
+    ms = t / 3.f;
+    return MORLET_OK;
+  };
+  // tries the candidates (which include the incumbent) in two interleaved passes
+  auto try_set = [&](const std::vector<Sched>& cands) -> int {
+    std::vector<float> tm(cands.size(), -1.f);
+    for (int pass = 0; pass < 2; ++pass)
+      for (size_t i = 0; i < cands.size(); ++i) {
+        float ms = -1.f;
+        const int r = time_one(cands[i], ms);
+        if (r) return r;
+        if (ms >= 0.f && (tm[i] < 0.f || ms < tm[i])) tm[i] = ms;
+      }
+    // the incumbent's time in this set, then any candidate at least 1 % faster
+    for (size_t i = 0; i < cands.size(); ++i)
+      if (memcmp(&cands[i], &best, sizeof(Sched)) == 0 && tm[i] >= 0.f) t_best = tm[i];
+    for (size_t i = 0; i < cands.size(); ++i)
+      if (tm[i] >= 0.f && (t_best < 0.f || tm[i] < 0.99f * t_best)) {
+        best = cands[i];
+        t_best = tm[i];
+      }
+    return MORLET_OK;
+  };
+  CK(cudaMemsetAsync(x, 0, p->elem * std::max(1LL, acc), st));
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  // two passes over the candidates (the first also warms the GPU up); each candidate keeps its
-  // faster pass
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int i = 0; i < NC; ++i) {
-      p->ls_max_L = cand[i][0];
-      p->ss_min_L = cand[i][1];
-      long long slots = 0;
-      rc = build_forward(p, slots);
-      if (rc) goto fail;
-      if (slots > p->n_slots) continue;  // would need look-back slots the plan does not own
-      // timed exactly as morlet_forward runs it: replays of the captured graph
-      CK(forward_graph(p, x, W));
-      CK(cudaGraphLaunch(p->gexec, st));  // warm-up
-      CK(cudaEventRecord(e0, st));
-      for (int r = 0; r < 4; ++r) CK(cudaGraphLaunch(p->gexec, st));
-      CK(cudaEventRecord(e1, st));
-      CK(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, e0, e1));
-      if (p->h_err && *(volatile int*)p->h_err) {  // a timed-out wait: not a candidate
-        *(volatile int*)p->h_err = 0;
-        continue;
-      }
-      if (tmin[i] < 0.f || ms < tmin[i]) tmin[i] = ms;
+  if (sft) {
+    const long long pairs[][2] = {{LS_MAX_L, SS_MIN_L}, {256, SS_MIN_L}, {64, SS_MIN_L}, {0, SS_MIN_L},
+                                  {LS_MAX_L, 1024},     {256, 1024},     {64, 1024},       {0, 1024}};
+    std::vector<Sched> c;
+    for (auto& pr : pairs) {
+      Sched v = best;
+      v.ls = pr[0];
+      v.ss = pr[1];
+      c.push_back(v);
     }
-  }
-  {
-    // the defaults (candidate 0) stay unless another pair is at least 1 % faster
-    float best_ms = -1.f;
-    for (int i = 0; i < NC; ++i)
-      if (tmin[i] >= 0.f && (best_ms < 0.f || tmin[i] < 0.99f * best_ms)) {
-        best_ms = tmin[i];
-        best_ls = cand[i][0];
-        best_ss = cand[i][1];
+    rc = try_set(c);
+    if (rc) goto fail;
+    c.clear();
+    for (int m : {16, 12, 8}) {
+      Sched v = best;
+      v.seg_mult = m;
+      c.push_back(v);
+    }
+    rc = try_set(c);
+    if (rc) goto fail;
+    c.clear();
+    for (int o : {0, 1}) {
+      Sched v = best;
+      v.order = o;
+      c.push_back(v);
+    }
+    rc = try_set(c);
+    if (rc) goto fail;
+    c.clear();
+    for (long long t : {32LL, 16LL, 64LL}) {
+      Sched v = best;
+      v.ss_tiles = t;
+      c.push_back(v);
+    }
+    rc = try_set(c);
+    if (rc) goto fail;
+  } else {
+    std::vector<Sched> c;
+    for (int a : {0, 1}) {
+      Sched v = best;
+      v.asft_chains = a;
+      c.push_back(v);
+    }
+    rc = try_set(c);
+    if (rc) goto fail;
+    c.clear();
+    if (!best.asft_chains) {
+      for (int m : {16, 12, 8}) {
+        Sched v = best;
+        v.seg_mult = m;
+        c.push_back(v);
       }
+      rc = try_set(c);
+      if (rc) goto fail;
+      c.clear();
+    }
+    for (int o : {0, 1}) {
+      Sched v = best;
+      v.order = o;
+      c.push_back(v);
+    }
+    rc = try_set(c);
+    if (rc) goto fail;
   }
-  p->ls_max_L = best_ls;
-  p->ss_min_L = best_ss;
+  put_sched(p, best);
   {
     long long slots = 0;
-    rc = build_forward(p, slots);  // also drops the graph captured on the scratch buffers
+    rc = build_forward(p, slots);
+  }
+  if (rc == MORLET_OK) {
+    p->tuned = 1;
+    p->tune_outputs = acc * S;
   }
 fail:
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaFree(x);
   cudaFree(W);
+  morlet_plan_destroy(q);
   return rc;
 }
 
@@ -852,11 +1059,12 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
   if (d->K < 0 || d->K > KMAX) return d->K > KMAX ? MORLET_ERR_UNSUPPORTED : MORLET_ERR_ARG;
   if (d->K == 0 && !(d->fit_tol > 0)) return MORLET_ERR_ARG;
   if (d->method != MORLET_DIRECT && d->method != MORLET_GAUSS && d->method != MORLET_MULTIPLY) return MORLET_ERR_ARG;
-  // multiplication method: FP32, rotating form, the unnormalised Morlet (no kappa terms), 2K - 1
-  // non-harmonic terms (K Gaussian terms given), windows up to L = 4096 (window segments)
+  // multiplication method: FP32, rotating form, 2K - 1 non-harmonic terms (K Gaussian terms given),
+  // plus K harmonic kappa terms for the normalised Morlet (norm = 1); window segments for L <= 4096,
+  // start states from window sums of tile sums beyond (no look-back chains)
   if (d->method == MORLET_MULTIPLY &&
-      (d->transform != MORLET_SFT || d->precision == MORLET_FP64 || d->form == 1 || d->norm != 0 || d->K < 1 ||
-       2 * d->K - 1 > KMAX || (d->flags & MORLET_FLAG_NO_HALO)))
+      (d->transform != MORLET_SFT || d->precision == MORLET_FP64 || d->form == 1 || d->K < 1 ||
+       (d->norm == 1 ? 3 * d->K - 1 : 2 * d->K - 1) > KMAX || (d->flags & MORLET_FLAG_NO_HALO)))
     return MORLET_ERR_UNSUPPORTED;
   if (d->transform != MORLET_SFT && d->transform != MORLET_ASFT) return MORLET_ERR_ARG;
   if (d->precision < MORLET_FP32_PLAIN || d->precision > MORLET_FP64) return MORLET_ERR_ARG;
@@ -926,10 +1134,7 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
         J.nh = kmax_fit;
       }
       if (J.ph_lo + J.nh > J.L) { rc = MORLET_ERR_ARG; goto fail; }  // harmonics must stay below beta p < pi
-      if (J.method == 2) {
-        J.deriv = 0;
-        if (J.L > 4096) { rc = MORLET_ERR_UNSUPPORTED; goto fail; }  // only window segments are built
-      }
+      if (J.method == 2) J.deriv = 0;
       if (d->transform == MORLET_ASFT) {
         J.n0 = d->n0 > 0 ? d->n0 : std::max(1, (int)floor(sg / 8.0 + 0.5));
         if (J.n0 > J.L) { rc = MORLET_ERR_ARG; goto fail; }
@@ -951,7 +1156,8 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
     CK(cudaStreamSynchronize(st));
     p->K_fit = 0;
     for (int s = 0; s < S; ++s) p->K_fit = std::max(p->K_fit, (int)p->h_tabs[s].K);
-    p->K_kernel = round_k(std::max(d->method == MORLET_MULTIPLY ? 2 * p->K_fit - 1 : p->K_fit, 2));
+    p->K_kernel = round_k(std::max(
+        d->method == MORLET_MULTIPLY ? 2 * p->K_fit - 1 + (d->norm == 1 ? p->K_fit : 0) : p->K_fit, 2));
     if (p->K_kernel < 0) { rc = MORLET_ERR_UNSUPPORTED; goto fail; }
     for (int s = 0; s < S; ++s)
       if (p->h_tabs[s].p0 + p->K_kernel > jobs[s].L) { rc = MORLET_ERR_ARG; goto fail; }
@@ -1005,13 +1211,9 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
       rc = setup_launch(p, true, p->adj, slots_adj);
       if (rc) goto fail;
     }
-    p->n_slots = std::max(slots, slots_adj);
-    const int nt_adj = has_adj ? 2 * p->K_kernel : p->K_kernel;
-    if (p->n_slots > 0) {
-      CK(cudaMalloc(&p->d_flags, sizeof(uint32_t) * p->n_slots));
-      CK(cudaMalloc(&p->d_agg, carry_bytes(p) * nt_adj * p->n_slots));
-      CK(cudaMalloc(&p->d_incl, carry_bytes(p) * nt_adj * p->n_slots));
-    }
+    p->nt_slot = has_adj ? 2 * p->K_kernel : p->K_kernel;
+    rc = alloc_slots(p, std::max(slots, slots_adj));
+    if (rc) goto fail;
     if (p->fwd.n_pwork > 0) {
       rc = alloc_prefix(p);
       if (rc) goto fail;
@@ -1137,7 +1339,6 @@ int morlet_plan_set_row_thresholds(morlet_plan_t p, int64_t lane_chunk_max_L, in
   p->ss_min_L = start_state_min_L;
   long long slots = 0;
   int rc = build_forward(p, slots);
-  if (rc == MORLET_OK && slots > p->n_slots) rc = MORLET_ERR_UNSUPPORTED;
   if (rc != MORLET_OK) {  // back to the thresholds the plan had
     p->ls_max_L = old_ls;
     p->ss_min_L = old_ss;
@@ -1145,6 +1346,43 @@ int morlet_plan_set_row_thresholds(morlet_plan_t p, int64_t lane_chunk_max_L, in
     const int rc2 = build_forward(p, s2);
     return rc2 != MORLET_OK ? rc2 : rc;
   }
+  return MORLET_OK;
+}
+
+int morlet_plan_set_schedule(morlet_plan_t p, int32_t seg_mult, int32_t ss_tiles_max, int32_t order,
+                             int32_t asft_chains) {
+  if (!p || (seg_mult != 8 && seg_mult != 12 && seg_mult != 16) || ss_tiles_max < 4 || ss_tiles_max > 64 ||
+      order < 0 || order > 1 || asft_chains < 0 || asft_chains > 1)
+    return MORLET_ERR_ARG;
+  if (p->h_err && *(volatile int*)p->h_err) return MORLET_ERR_TIMEOUT;
+  const Sched old = get_sched(p);
+  Sched c = old;
+  c.seg_mult = seg_mult;
+  c.ss_tiles = ss_tiles_max;
+  c.order = order;
+  c.asft_chains = asft_chains;
+  put_sched(p, c);
+  long long slots = 0;
+  int rc = build_forward(p, slots);
+  if (rc != MORLET_OK) {  // back to the schedule the plan had
+    put_sched(p, old);
+    long long s2 = 0;
+    const int rc2 = build_forward(p, s2);
+    return rc2 != MORLET_OK ? rc2 : rc;
+  }
+  return MORLET_OK;
+}
+
+int morlet_plan_schedule(morlet_plan_t p, int64_t o[8]) {
+  if (!p || !o) return MORLET_ERR_ARG;
+  o[0] = p->ls_max_L;
+  o[1] = p->ss_min_L;
+  o[2] = p->seg_mult;
+  o[3] = p->ss_tiles_max;
+  o[4] = p->order;
+  o[5] = p->asft_chains;
+  o[6] = p->tuned;
+  o[7] = p->tune_outputs;
   return MORLET_OK;
 }
 

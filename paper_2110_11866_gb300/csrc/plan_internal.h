@@ -61,6 +61,7 @@ __host__ __device__ constexpr int kbuilt(int i) { return i == 0 ? 2 : i == 1 ? 3
 const void* kernel_for(int variant, int K, bool warp);
 const void* kernel_psum(int K);   // prefix sums of the start-state rows (k_psum.cu)
 const void* kernel_tsum(int K);   // tile sums of the start-state rows (k_psum.cu)
+const void* kernel_tsum_h(int K); // Horner tile sums: ASFT and multiplication-method start-state rows
 const void* kernel_lscan(int K);  // lane-chunk scan of short-window rows (k_lscan.cu)
 
 }  // namespace msft

@@ -131,6 +131,40 @@ __device__ __forceinline__ void lane_sums(const float (&xa)[ITEMS], const float2
   }
 }
 
+// The same weighted lane sum w sum_i rho^{15 - i} x_i for any rho (the damped rho of the ASFT, the
+// non-harmonic rho of the multiplication method), by Horner's rule b <- rho b + x_i from zero: four
+// operations per sample and term pair, two terms per instruction.
+template <int K, int ITEMS>
+__device__ __forceinline__ void lane_sums_horner(const float (&xa)[ITEMS], const float2 (&rho)[K],
+                                                 const float2 (&w)[K], float2 (&b)[K]) {
+  constexpr int H = Pairs<K>::H;
+  float2 rx2[H], ry2[H], nry2[H], X2[H], Y2[H];
+#pragma unroll
+  for (int h = 0; h < H; ++h) {
+    const bool two = 2 * h + 1 < K;
+    const float2 r0 = rho[2 * h], r1 = two ? rho[2 * h + 1] : make_float2(0.f, 0.f);
+    rx2[h] = make_float2(r0.x, r1.x);
+    ry2[h] = make_float2(r0.y, r1.y);
+    nry2[h] = make_float2(-r0.y, -r1.y);
+    X2[h] = Y2[h] = make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const float2 xv2 = pk_dup(xa[i]);
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      const float2 vr = pk_fma(rx2[h], X2[h], pk_fma(nry2[h], Y2[h], xv2));
+      Y2[h] = pk_fma(ry2[h], X2[h], pk_mul(rx2[h], Y2[h]));
+      X2[h] = vr;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const float2 v = (j & 1) ? make_float2(X2[j >> 1].y, Y2[j >> 1].y) : make_float2(X2[j >> 1].x, Y2[j >> 1].x);
+    b[j] = cmul(v, w[j]);
+  }
+}
+
 // Sum over the warp of each b[j] (all lanes receive the sums); returns the sum of term `lane`
 // (zero in lanes >= K).
 template <int K>
@@ -238,19 +272,22 @@ __device__ __forceinline__ void start_state(const KParams& P, const WorkItem& wi
 }
 
 // State entering a start-state item from a window sum of stored tile sums (used when the window
-// spans few tiles compared with the item): with b = wi.t_a a tile start and u0 = b - 2L,
+// spans few tiles compared with the item): with b = wi.t_a a tile start and u0 the window's first
+// sample (b - 2L for the SFT's 2L-sample G form, b - 1 - 2L for the 2L + 1 samples of the damped
+// form, HORNER),
 //     G(b - 1) = sum_{k = k0}^{kb - 1} rho^{512 (kb - 1 - k)} G_k,
 // G_k the FP32 tile sums sum_{u in tile k} rho^{e_k - u} x[u] (tsum_kernel), except that the tile
 // k0 holding u0 contributes only its samples from u0 on (a masked tile sum computed here). The lanes
-// of a term's group take the window's tiles in turn with FP32 running powers of rho^{512}.
-template <int K, int ITEMS>
+// of a term's group take the window's tiles in turn with FP32 running powers of rho^{512} (damped
+// for the ASFT, so every partial product stays below one in magnitude).
+template <int K, int ITEMS, bool HORNER = false>
 __device__ __forceinline__ void start_state_window(const KParams& P, const WorkItem& wi, const ScaleTab* tb,
                                                    const float2 (&rho)[K], int lane, float2 (&Cw)[K]) {
   constexpr int G = KPad<K>::G;
   const int tl = lane / G, sl = lane % G, tq = tl < K ? tl : 0;
   const int64_t L = tb->L;
   const int64_t kb = (wi.t_a - wi.t_grid) / PS_TILE;
-  const int64_t u0 = wi.t_a - 2 * L;
+  const int64_t u0 = wi.t_a - 2 * L - (HORNER ? 1 : 0);
   int64_t k0 = 0;
   float2 gp = make_float2(0.f, 0.f);  // masked sum of tile k0 for this lane's term
   bool partial = false;
@@ -263,13 +300,16 @@ __device__ __forceinline__ void start_state_window(const KParams& P, const WorkI
       float xa[ITEMS];
       load_run_v8<ITEMS>(xs, a0 + (int64_t)lane * ITEMS, u0 > 0 ? u0 : 0, wi.n, xa, P.n_x - wi.x_off);
       float2 wl[K], b[K];
-      float lam[K];
 #pragma unroll
-      for (int j = 0; j < K; ++j) {
-        wl[j] = __ldg(&tb->f_pw_lane[31 - lane][j]);
-        lam[j] = __ldg(&tb->f_lam[j]);
+      for (int j = 0; j < K; ++j) wl[j] = __ldg(&tb->f_pw_lane[31 - lane][j]);
+      if constexpr (HORNER) {
+        lane_sums_horner<K, ITEMS>(xa, rho, wl, b);
+      } else {
+        float lam[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) lam[j] = __ldg(&tb->f_lam[j]);
+        lane_sums<K, ITEMS>(xa, rho, lam, wl, b);
       }
-      lane_sums<K, ITEMS>(xa, rho, lam, wl, b);
       gp = warp_sum_scatter<K>(b, lane);
     }
   }
@@ -301,7 +341,9 @@ __device__ __forceinline__ void start_state_window(const KParams& P, const WorkI
 constexpr bool TS_PF = true;  // a tile-sum chunk prefetched into L2 when claimed
 
 // Tile sums only: G_k = sum_{u in tile k} rho^{e_k - u} x[u] for the tiles of a chunk, FP32, stored
-// for start_state_window. No look-back, no prefix: chunks are independent.
+// for start_state_window. No look-back, no prefix: chunks are independent. Lane sums by Reinsch's
+// recurrence for the SFT's harmonics (|rho| = 1), by Horner's rule for the damped or non-harmonic
+// rho of the ASFT and the multiplication method (C::ASFT).
 template <class C>
 __global__ void __launch_bounds__(THREADS, C::K <= 4 ? 4 : 2) tsum_kernel(const KParams P) {
   static_assert(std::is_same<typename C::R, float>::value && C::CH == 1 && C::ITEMS == 16,
@@ -339,7 +381,8 @@ __global__ void __launch_bounds__(THREADS, C::K <= 4 ? 4 : 2) tsum_kernel(const 
         float xa[ITEMS];
         load_run_v8<ITEMS>(xs, t0 + (int64_t)lane * ITEMS, 0, N, xa, P.n_x - wi.x_off);
         float2 b[K];
-        lane_sums<K, ITEMS>(xa, rho, lam, wl, b);
+        if constexpr (C::ASFT) lane_sums_horner<K, ITEMS>(xa, rho, wl, b);
+        else lane_sums<K, ITEMS>(xa, rho, lam, wl, b);
         g = warp_sum_scatter<K>(b, lane);
       }
       if (sl == 0 && tl < K) gb[(int64_t)k * K + tl] = g;

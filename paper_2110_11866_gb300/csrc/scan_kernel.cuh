@@ -61,6 +61,9 @@ struct Cfg {
   static constexpr int MINB = (sizeof(R_) == 4 && NT <= 4) ? 3 : (NT <= 8 ? 2 : 1);
   // start states from prefix sums (warp kernel): compensated FP32, real input, rotating form
   static constexpr bool START = std::is_same<CV_, DFC>::value && CH == 1 && FORM_ == FORM_RF && !ASFT_;
+  // start states from window sums of Horner tile sums (warp kernel): the damped recursion of the
+  // ASFT and the non-harmonic terms of the multiplication method, FP32, real input
+  static constexpr bool START_H = ASFT_ && std::is_same<R_, float>::value && CH == 1 && FORM_ == FORM_RF;
   static_assert(FORM_ == FORM_RF || CH == 1, "kernel-integral form is built for real input only");
   static_assert(NT <= 32, "one lane per scanned value in the block phase");
 };

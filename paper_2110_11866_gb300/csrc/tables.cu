@@ -245,16 +245,21 @@ __global__ void build_tables(ScaleTab* tabs, const FitJob* jobs, int n_scales, i
   const long long L = J.L;
   const double alpha = J.alpha;
   const bool rot = (form == 2);
-  // multiplication method: term j has the non-harmonic frequency omega_j = omega0 + beta (j - P),
-  // P = (Gaussian terms) - 1, and rho_j = e^{i omega_j}; its powers are e^{i omega0 n} (FP64 angle)
-  // times the exact harmonic e^{i beta (j - P) n}
+  // multiplication method: term j < 2P + 1 has the non-harmonic frequency omega_j = omega0 +
+  // beta (j - P), P = (Gaussian terms) - 1, and rho_j = e^{i omega_j}; its powers are e^{i omega0 n}
+  // (FP64 angle) times the exact harmonic e^{i beta (j - P) n}. The normalised Morlet (kappa_xi != 0)
+  // adds the terms j = 2P + 1 + q, q = 0..P, of the kappa part -kappa_xi sum_q m_q cos(beta q k): the
+  // harmonics rho = e^{i beta q} with exact powers.
   const bool mult = (J.method == 2);
   const long long Pm = mult ? (long long)tb.K - 1 : 0;
+  const long long n_morlet = 2 * Pm + 1;
   auto power = [&](long long p, long long n) -> double2 {
     if (mult) {
+      const long long j = p - tb.p0;
+      if (j >= n_morlet) return harmonic(j - n_morlet, n, L);
       double sn, cs;
       sincos(fmod(J.omega0 * (double)n, 2.0 * M_PI), &sn, &cs);
-      const double2 h = harmonic(p - tb.p0 - Pm, n, L);
+      const double2 h = harmonic(j - Pm, n, L);
       return make_double2(cs * h.x - sn * h.y, cs * h.y + sn * h.x);
     }
     const double2 e = harmonic(p, n, L);
@@ -346,17 +351,29 @@ __global__ void build_tables(ScaleTab* tabs, const FitJob* jobs, int n_scales, i
       // c(omega) + i s(omega) at n (Sec. III-B) is e^{-i omega L} V(n + L), and the Morlet output
       // sum_{p = -P}^{P} a'_p (c + i s)(omega_p) has the complex weights w_j = a'_j e^{-i omega_j L}
       // (a'_0 = a_0, a'_{+-p} = a_p / 2), held as cM_j + i cL_j.
+      // The kappa terms: sum_k m_q cos(beta q k) x[n - k] = Re(m_q e^{-i beta q L} V_q(n + L)) with
+      // e^{-i beta q L} = (-1)^q, so their weight is the real -kappa_xi (-1)^q m_q on Re V only.
       tb.E = make_double2(1.0, 0.0);
       tb.kappa = 0.0;
       for (int j = 0; j < KMAX; ++j) {
-        const long long q = j - Pm;
-        const long long aq = q < 0 ? -q : q;
-        const double ap = (j < K_kernel && aq <= Pm) ? (aq == 0 ? tb.m[0] : 0.5 * tb.m[aq]) : 0.0;
-        const double2 eL = power(tb.p0 + j, L);
-        tb.cM[j] = ap * eL.x;
-        tb.cL[j] = -ap * eL.y;
-        tb.f_cM[j] = (float)tb.cM[j];
-        tb.f_cL[j] = (float)tb.cL[j];
+        double wr = 0.0, wi = 0.0, wyr = 0.0, wyi = 0.0;
+        if (j < K_kernel && j < n_morlet) {
+          const long long q = j - Pm;
+          const long long aq = q < 0 ? -q : q;
+          const double ap = aq == 0 ? tb.m[0] : 0.5 * tb.m[aq];
+          const double2 eL = power(tb.p0 + j, L);
+          wr = wyr = ap * eL.x;
+          wi = wyi = -ap * eL.y;
+        } else if (j < K_kernel && J.kappa_xi != 0.0 && j - n_morlet <= Pm) {
+          const long long q = j - n_morlet;
+          wr = -J.kappa_xi * ((q & 1) ? -1.0 : 1.0) * tb.m[q];
+        }
+        tb.cM[j] = wr;
+        tb.cL[j] = wi;
+        tb.f_cM[j] = (float)wr;
+        tb.f_cL[j] = (float)wi;
+        tb.f_cMy[j] = (float)wyr;
+        tb.f_cLy[j] = (float)wyi;
         const double2 k2 = power(tb.p0 + j, 2 * L);
         tb.f_kapc[j] = j < K_kernel ? make_float2((float)k2.x, (float)k2.y) : make_float2(0.f, 0.f);
       }

@@ -35,7 +35,21 @@ struct RowSpec {
   long long wt;        // positions per step of a window segment: a CTA sub-tile, or one warp-tile
   int warp_window;     // 1: window segments go to the warp-independent kernel
   long long o_lo = 0, o_hi = 0;  // stored output positions [o_lo, o_hi); o_hi = 0: [D, D + N)
+  int seg_mult = 16;   // warp windows: a segment runs about seg_mult * L positions (8, 12 or 16)
 };
+
+// The row description both the plan and the allocation-free entry point use: segment starts aligned
+// to 32 bytes of input (elem_bytes per sample); window segments on the warp-independent kernel step
+// by one warp-tile of 32 x 16 positions, on the CTA kernel by a tile of T positions.
+__host__ __device__ inline RowSpec make_row_spec(long long N, long long L, long long D, long long x_off,
+                                                 long long out_off, int scale, int elem_bytes, int policy,
+                                                 int chain, bool warp_window, long long T, long long o_lo,
+                                                 long long o_hi, int seg_mult) {
+  RowSpec r{N, L, D, x_off, out_off, scale, 32 / elem_bytes, policy, chain,
+            warp_window ? 32LL * ITEMS_DEFAULT : T, warp_window ? 1 : 0, o_lo, o_hi};
+  r.seg_mult = seg_mult;
+  return r;
+}
 
 __host__ __device__ inline long long ws_floordiv(long long a, long long b) {
   return (a >= 0) ? a / b : -((-a + b - 1) / b);
@@ -52,9 +66,9 @@ __host__ __device__ inline long long row_work(const RowSpec& r, long long T, Wor
   *chained = !(short_window && r.policy != SEG_PLAIN);
   long long R;  // outputs per segment
   if (!*chained) {
-    // CTA windows: ceil(10 L / T) sub-tiles; warp windows: max(2, ceil(16 L / WT)) warp-tiles,
-    // i.e. a prologue of at most about an eighth of the segment
-    long long sub = r.warp_window ? (16 * r.L + r.wt - 1) / r.wt : (10 * r.L + r.wt - 1) / r.wt;
+    // CTA windows: ceil(10 L / T) sub-tiles; warp windows: max(2, ceil(seg_mult L / WT)) warp-tiles,
+    // i.e. a prologue of at most about 2 / seg_mult of the segment
+    long long sub = r.warp_window ? (r.seg_mult * r.L + r.wt - 1) / r.wt : (10 * r.L + r.wt - 1) / r.wt;
     if (sub < (r.warp_window ? 2 : 1)) sub = r.warp_window ? 2 : 1;
     R = sub * r.wt - 2 * r.L - (r.align - 1);  // room for rounding the segment start down to 32 bytes
   } else if (r.policy == SEG_RESTART) {

@@ -211,13 +211,16 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
         cl2[h] = make_float2(cL[2 * h], two ? cL[2 * h + 1] : 0.f);
       }
     }
-    float2 nkr2[APC ? H : 1], nki2[APC ? H : 1];  // -kappa_j of the multiplication method, in pairs
+    // multiplication method, in pairs: -kappa_j, and the weights of the imaginary part of the combine
+    float2 nkr2[APC ? H : 1], nki2[APC ? H : 1], cmy2[APC ? H : 1], cly2[APC ? H : 1];
     if constexpr (APC) {
 #pragma unroll
       for (int h = 0; h < H; ++h) {
         const bool two = 2 * h + 1 < K;
         nkr2[h] = make_float2(-kapc[2 * h].x, two ? -kapc[2 * h + 1].x : 0.f);
         nki2[h] = make_float2(-kapc[2 * h].y, two ? -kapc[2 * h + 1].y : 0.f);
+        cmy2[h] = make_float2(__ldg(&tb->f_cMy[2 * h]), two ? __ldg(&tb->f_cMy[2 * h + 1]) : 0.f);
+        cly2[h] = make_float2(__ldg(&tb->f_cLy[2 * h]), two ? __ldg(&tb->f_cLy[2 * h + 1]) : 0.f);
       }
     }
     const V E = TabR<R>::E(tb);
@@ -235,6 +238,8 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
         if (P.ss_window) start_state_window<K, ITEMS>(P, wi, tb, rho, lane, Cw);
         else start_state<K, ITEMS>(P, wi, tb, rho, lane, Cw);
       }
+    } else if constexpr (C::START_H) {
+      if (wi.p_row >= 0) start_state_window<K, ITEMS, true>(P, wi, tb, rho, lane, Cw);
     }
 
     for (int k = 0; k < wi.n_sub; ++k) {
@@ -448,10 +453,10 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
               oy = pk_fma(cl2[h], vi, oy);
             } else if constexpr (C::OUT == OUT_REAL) {
               ox = pk_fma(cl2[h], vi, pk_fma(cm2[h], vr, ox));
-            } else {  // complex weights w_j = cM_j + i cL_j: w V
+            } else {  // complex weights w_j = cM_j + i cL_j: Re(w V) + i (cMy Im V + cLy Re V)
               ox = pk_fma(cm2[h], vr, ox);
               oz = pk_fma(cl2[h], vi, oz);
-              oy = pk_fma(cm2[h], vi, pk_fma(cl2[h], vr, oy));
+              oy = pk_fma(cmy2[h], vi, pk_fma(cly2[h], vr, oy));
             }
           }
           if constexpr (APC) return cmul(cmake<R>((ox.x + ox.y) - (oz.x + oz.y), oy.x + oy.y), E);

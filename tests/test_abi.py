@@ -60,6 +60,9 @@ def test_strerror_and_argument_errors_without_gpu(built_lib):
 
     assert lib.morlet_plan_set_row_thresholds(None, 128, 4096) == m.MORLET_ERR_ARG
     assert lib.morlet_plan_set_spin_limit(None, 10) == m.MORLET_ERR_ARG
+    assert lib.morlet_plan_set_schedule(None, 16, 32, 0, 0) == m.MORLET_ERR_ARG
+    assert lib.morlet_plan_schedule(None, None) == m.MORLET_ERR_ARG
+    assert lib.morlet_measure_fp64_rate(None, None) == m.MORLET_ERR_ARG
 
 
 def test_plan_descriptor_errors_without_gpu(built_lib):
@@ -81,12 +84,13 @@ def test_plan_descriptor_errors_without_gpu(built_lib):
         (dict(lengths=[100], sigmas=[8.0], xi=float("inf")), m.MORLET_ERR_ARG),
         (dict(lengths=[100], sigmas=[8.0], norm=2), m.MORLET_ERR_ARG),
         (dict(lengths=[100], sigmas=[8.0], method=3), m.MORLET_ERR_ARG),
-        # multiplication method: only the SFT, FP32, rotating form, norm = 0, 2K - 1 <= 12
+        # multiplication method: only the SFT, FP32, rotating form, 2K - 1 terms (3K - 1 with the
+        # kappa terms of norm = 1) <= 12
         (dict(lengths=[100], sigmas=[8.0], method=m.MORLET_MULTIPLY, transform=m.MORLET_ASFT),
          m.MORLET_ERR_UNSUPPORTED),
         (dict(lengths=[100], sigmas=[8.0], method=m.MORLET_MULTIPLY, precision=m.MORLET_FP64),
          m.MORLET_ERR_UNSUPPORTED),
-        (dict(lengths=[100], sigmas=[8.0], method=m.MORLET_MULTIPLY, norm=1), m.MORLET_ERR_UNSUPPORTED),
+        (dict(lengths=[100], sigmas=[8.0], method=m.MORLET_MULTIPLY, norm=1, K=5), m.MORLET_ERR_UNSUPPORTED),
         (dict(lengths=[100], sigmas=[8.0], method=m.MORLET_MULTIPLY, K=7), m.MORLET_ERR_UNSUPPORTED),
         (dict(lengths=[100], sigmas=[8.0], method=m.MORLET_MULTIPLY, form=m.MORLET_FORM_KERNEL),
          m.MORLET_ERR_UNSUPPORTED),

@@ -13,6 +13,7 @@ import pytest
 import paper_2110_11866_gb300 as m
 import workloads as WL
 from oracle import morlet as om
+from oracle import sft_dd
 from tests.gpu_helpers import gpu_forward, oracle_forward, rel_err
 
 pytestmark = pytest.mark.gpu
@@ -105,6 +106,46 @@ def test_start_state_rows(K, longest):
     print(f"start-state rows K={K}: worst {worst:.3e}")
 
 
+@pytest.mark.parametrize("K", [3, 4, 6])
+def test_asft_start_state_rows(K):
+    """The ASFT's long windows (L > 4096) start from window sums of damped FP32 tile sums (Horner lane
+    sums, 2L + 1 samples): rows shorter than a tile, shorter than the window, spanning many work
+    items, every input alignment, next to window-segment rows of the same plan; the Morlet and the
+    Gaussian first derivative (real output), each against the oracle's double-double recursion."""
+    rng = np.random.default_rng(700 + K)
+    lens = [100000, 3, 50001, 262149, 1030, 77777]
+    sigs = [rng.standard_normal(n).astype(np.float32) for n in lens]
+    sigmas = [20.0, 1500.0, 2000.0, 5000.0]
+    plan, out = gpu_forward(sigs, sigmas, K=K, precision=m.MORLET_FP32_PLAIN, transform=m.MORLET_ASFT)
+    st = m.morlet_plan_stats(plan)
+    assert st["rows_start_state"] == 2 * len(lens) and st["rows_lookback"] == 0, st
+    worst = 0.0
+    for i, x in enumerate(sigs):
+        for s, sg in enumerate(sigmas):
+            e = rel_err(out[i][s], oracle_forward(x.astype(np.float64), sg, K, transform=m.MORLET_ASFT))
+            worst = max(worst, e)
+            assert e < 1e-4, (i, sg, e)
+    print(f"ASFT start-state rows K={K}: worst {worst:.2e}")
+    import torch
+    P = K + 3
+    gplan = m.morlet_plan(lens, sigmas, K=P + 1, method=m.MORLET_GAUSS, transform=m.MORLET_ASFT, deriv=1,
+                          precision=m.MORLET_FP32_PLAIN)
+    assert m.morlet_plan_stats(gplan)["rows_start_state"] == 2 * len(lens)
+    S, n_in = len(sigmas), sum(lens)
+    y = torch.full((n_in * S,), float("nan"), dtype=torch.float32, device="cuda")
+    m.morlet_forward(gplan, torch.from_numpy(np.concatenate(sigs)).cuda(), y)
+    torch.cuda.synchronize()
+    assert m.morlet_last_device_error(gplan) == 0
+    yh = y.cpu().numpy()
+    off = 0
+    for x, n in zip(sigs, lens):
+        for s, sg in enumerate(sigmas):
+            ref = sft_dd.asft_gauss(x.astype(np.float64), om.fit_gauss_asft(sg, P, 1, om.default_n0(sg)))
+            e = rel_err(yh[S * off + s * n: S * off + (s + 1) * n], ref)
+            assert e < 1e-4, (n, sg, e)
+        off += n
+
+
 @pytest.mark.parametrize("precision", [m.MORLET_FP32_COMP, m.MORLET_FP32_PLAIN, m.MORLET_FP64])
 @pytest.mark.parametrize("form", [m.MORLET_FORM_ROTATING, m.MORLET_FORM_KERNEL])
 @pytest.mark.parametrize("K", [2, 3, 4, 5, 6, 8, 12])
@@ -165,6 +206,9 @@ def test_autotune_keeps_results():
     plan, out = gpu_forward(sigs, sigmas, K=4, flags=m.MORLET_FLAG_AUTOTUNE)
     st = m.morlet_plan_stats(plan)
     assert st["lane_chunk_max_L"] in (0, 64, 128, 256) and st["start_state_min_L"] in (1024, 2048)
+    sc = m.morlet_plan_schedule(plan)
+    assert sc["autotuned"] == 1 and sc["autotune_outputs"] == sum(lens) * len(sigmas), sc
+    assert sc["seg_mult"] in (8, 12, 16) and sc["ss_tiles_max"] in (16, 32, 64) and sc["order"] in (0, 1)
     for i, x in enumerate(sigs):
         for s, sg in enumerate(sigmas):
             assert rel_err(out[i][s], oracle_forward(x.astype(np.float64), sg, 4)) < 1e-5
@@ -270,6 +314,115 @@ def test_chirp_long_windows_from_tile_sums():
             got = W[row + s * lens[i]: row + (s + 1) * lens[i]].cpu().numpy()
             e = rel_err(got, oracle_forward(sigs[i].astype(np.float64), sg, K))
             assert e < 1e-5, (i, sg, e)
+
+
+@pytest.mark.parametrize("seed", [1, 11, 12, 13])
+def test_chirp_seeds_default_schedule(seed):
+    """Config 2's chirp recipe (three linear chirps in 0.001-0.2 rad/sample plus N(0, 0.1^2)) drawn
+    from several seeds, at all six of its scales and K = 4 and 6, through the default compensated
+    schedule (lane chunks, window segments, start-state items): every row within 1e-5 of the
+    oracle's max |W|. The chirps sweep through the kernels' bands, the resonant worst case of the FP32
+    recursions."""
+    x = WL.c2_chirps(seed)
+    worst = {}
+    for K in (4, 6):
+        _, out = gpu_forward([x], WL.C2_SIGMAS, K=K, precision=m.MORLET_FP32_COMP)
+        for s, sg in enumerate(WL.C2_SIGMAS):
+            e = rel_err(out[0][s], oracle_forward(x.astype(np.float64), sg, K))
+            worst[(sg, K)] = e
+    print(f"chirp seed {seed}: " + ", ".join(f"sigma {sg:g} K {K}: {e:.2e}" for (sg, K), e in worst.items()))
+    bad = {k: v for k, v in worst.items() if not v < 1e-5}
+    assert not bad, bad
+
+
+SCHEDULES = [(16, 32, 0), (12, 32, 0), (8, 32, 0), (16, 16, 1), (16, 64, 1), (8, 64, 1)]
+
+
+@pytest.mark.parametrize("sched", SCHEDULES)
+def test_every_schedule_passes(sched):
+    """Every schedule the autotuner may pick (window-segment length, start-state item size, scale
+    order) gives the transform within the compensated-FP32 gate, on white noise and on a chirp through
+    the kernels' bands, at windows in every row kind (L = 32 ... 8192); the ASFT likewise with one
+    chain per row or window segments, within its gate."""
+    import torch
+    seg_mult, ss_tiles, order = sched
+    rng = np.random.default_rng(1000 + seg_mult + ss_tiles + order)
+    sigs = [rng.standard_normal(n).astype(np.float32) for n in (70001, 3000, 150000)]
+    sigs.append(WL.c2_chirps(12).astype(np.float32))
+    lens = [len(v) for v in sigs]
+    sigmas = [8.0, 40.0, 300.0, 512.0, 1024.0, 2048.0]
+    S, n_in = len(sigmas), sum(lens)
+    xt = torch.from_numpy(np.concatenate(sigs)).cuda()
+    for K, kw, tol, fn in ((6, dict(precision=m.MORLET_FP32_COMP), 1e-5, m.MORLET_SFT),
+                           (4, dict(precision=m.MORLET_FP32_PLAIN, transform=m.MORLET_ASFT), 1e-4, m.MORLET_ASFT)):
+        plan = m.morlet_plan(lens, sigmas, K=K, **kw)
+        for chains in ((0, 1) if fn == m.MORLET_ASFT else (0,)):
+            m.morlet_plan_set_schedule(plan, seg_mult, ss_tiles, order, chains)
+            sc = m.morlet_plan_schedule(plan)
+            assert (sc["seg_mult"], sc["ss_tiles_max"], sc["order"], sc["asft_chains"]) == (seg_mult, ss_tiles, order, chains)
+            W = torch.full((n_in * S,), float("nan"), dtype=torch.complex64, device="cuda")
+            m.morlet_forward(plan, xt, W)
+            torch.cuda.synchronize()
+            assert m.morlet_last_device_error(plan) == 0
+            Wh = W.cpu().numpy()
+            off = 0
+            for i, n in enumerate(lens):
+                for s, sg in enumerate(sigmas):
+                    got = Wh[S * off + s * n: S * off + (s + 1) * n]
+                    e = rel_err(got, oracle_forward(sigs[i].astype(np.float64), sg, K, transform=fn))
+                    assert e < tol, (sched, fn, chains, n, sg, e)
+                off += n
+    with pytest.raises(m.MorletError) as err:
+        m.morlet_plan_set_schedule(plan, 24, 32, 0, 0)
+    assert err.value.code == m.MORLET_ERR_ARG
+
+
+def test_autotune_times_a_bounded_subset_when_memory_is_short():
+    """The autotuner times the whole batch when its scratch copy takes at most a quarter of the free
+    device memory, and otherwise a sub-plan of every k-th signal holding at most 2^28 outputs (no
+    full-size scratch scalogram); the plan reports which. Memory is made short by holding most of
+    the free memory in a torch buffer while the plan is built."""
+    import torch
+    lens = [1 << 20] * 300  # 629 M outputs at two scales: 5 GB of scratch output
+    plan = m.morlet_plan(lens, [8.0, 300.0], K=4, flags=m.MORLET_FLAG_AUTOTUNE)
+    sc = m.morlet_plan_schedule(plan)
+    assert sc["autotuned"] == 1 and sc["autotune_outputs"] == 2 * sum(lens), sc
+    del plan
+    torch.cuda.synchronize()
+    free, _ = torch.cuda.mem_get_info()
+    hold = torch.empty(int(free - (12 << 30)), dtype=torch.uint8, device="cuda")  # leave 12 GB free
+    try:
+        plan = m.morlet_plan(lens, [8.0, 300.0], K=4, flags=m.MORLET_FLAG_AUTOTUNE)
+        sc = m.morlet_plan_schedule(plan)
+        assert sc["autotuned"] == 1 and 0 < sc["autotune_outputs"] <= (1 << 28) < 2 * sum(lens), sc
+        del plan
+    finally:
+        del hold
+        torch.cuda.empty_cache()
+
+
+def test_autotune_asft_keeps_results():
+    """MORLET_FLAG_AUTOTUNE on an ASFT plan chooses between window segments and one chain per row
+    (and the segment length) by timing; the transform stays within the ASFT gate."""
+    rng = np.random.default_rng(78)
+    lens = [50000, 120000, 3000]
+    sigs = [rng.standard_normal(n).astype(np.float32) for n in lens]
+    sigmas = [8.0, 300.0, 1500.0]
+    plan, out = gpu_forward(sigs, sigmas, K=4, precision=m.MORLET_FP32_PLAIN, transform=m.MORLET_ASFT,
+                            flags=m.MORLET_FLAG_AUTOTUNE)
+    sc = m.morlet_plan_schedule(plan)
+    assert sc["autotuned"] == 1 and sc["asft_chains"] in (0, 1), sc
+    for i, x in enumerate(sigs):
+        for s, sg in enumerate(sigmas):
+            ref = oracle_forward(x.astype(np.float64), sg, 4, transform=m.MORLET_ASFT)
+            assert rel_err(out[i][s], ref) < 1e-4
+
+
+def test_fp64_rate_measurement():
+    """The FP64 FMA rate helper returns a plausible rate for this GPU (between 0.1 and 100 TFLOP/s)."""
+    r = m.morlet_measure_fp64_rate()
+    print(f"measured FP64 FMA rate: {r / 1e12:.3f} TFLOP/s")
+    assert 1e11 < r < 1e14
 
 
 def test_deterministic_replay():

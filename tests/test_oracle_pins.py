@@ -378,6 +378,20 @@ def test_adjoint_inner_product_identity():
     assert np.abs(M.adjoint_direct(g, fit, idx) - dx[idx]).max() < 1e-12 * np.abs(dx).max()
 
 
+@pytest.mark.parametrize("sigma,K", [(3.0, 3), (9.0, 4), (40.0, 6)])
+def test_adjoint_by_kernel_integral_equals_the_transpose(sigma, K):
+    """The O(N K) adjoint (two O-SFT runs, from the fitted kernel's even real and odd imaginary
+    parts) equals the direct transpose sum_k Re(conj(g[t+k]) psi_hat[k]) element by element, on a
+    signal shorter and longer than the window."""
+    rng = np.random.default_rng(int(10 * sigma) + K)
+    fit = M.fit_direct(sigma, 6.0, K)
+    for N in (50, 1500):
+        g = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+        a = D.adjoint_sft(g, fit)
+        b = M.adjoint_direct(g, fit)
+        assert np.abs(a - b).max() < 1e-13 * np.abs(b).max()
+
+
 def test_adjoint_finite_differences_log_power_loss():
     """Loss sum_n w[n] log(1e-6 + |W[n]|^2) (the differentiation workload's loss). Its gradient
     dLoss/dx through adjoint_direct matches central differences (eps = 1e-6) at random coordinates."""
@@ -497,6 +511,29 @@ def test_multiply_kernel_approximates_morlet(sigma, K):
     assert err < 5e-3
     worse = M.fit_multiply(sigma, 6.0, K - 1)
     assert np.abs(M.kernel_multiply(worse) - psi).max() > err
+
+
+@pytest.mark.parametrize("xi", [1.0, 2.0, 6.0])
+def test_multiply_kernel_normalised_kappa_terms(xi):
+    """With norm = 1 the multiplication kernel is C_xi pi^{-1/4} sigma^{-1/2} G_hat[k] (e^{i omega0 k} -
+    kappa_xi): its distance to the normalised Morlet is exactly the envelope's fit error times
+    |e^{i omega0 k} - kappa_xi|, and leaving the kappa terms out costs kappa_xi times the envelope
+    (visible for small xi, where kappa_xi = e^{-xi^2/2} is large)."""
+    sigma, K = 40.0, 5
+    mf = M.fit_multiply(sigma, xi, K, norm=1)
+    L = mf["L"]
+    k = np.arange(-L, L + 1)
+    C, kappa = M.morlet_constants(xi)
+    amp = C * math.pi ** -0.25 / math.sqrt(sigma)
+    env = np.exp(-k.astype(np.float64) ** 2 / (2 * sigma * sigma))
+    env_hat = sum(a * np.cos(M.harmonic_angle(p, k, L)) for p, a in enumerate(mf["a"]))
+    psi = M.morlet(k, sigma, xi, 1)
+    got = M.kernel_multiply(mf)
+    want_err = amp * np.abs((env_hat - env) * (np.exp(1j * (xi / sigma) * k) - kappa))
+    assert np.abs(np.abs(got - psi) - want_err).max() <= 1e-13 * np.abs(psi).max()
+    no_kappa = amp * M.kernel_multiply(dict(mf, norm=0))
+    if xi <= 2.0:
+        assert np.abs(no_kappa - psi).max() > 100 * np.abs(got - psi).max()
 
 
 def test_multiply_sinusoid_closed_form():
