@@ -71,10 +71,13 @@ enum {
                                  ASFT chains (morlet_plan_set_schedule) -- and keep the fastest (each
                                  knob keeps its default unless another value is at least 1 % faster) */
   MORLET_FLAG_NO_HALO = 4,    /* force one look-back chain per row (no per-tile window recompute) */
-  MORLET_FLAG_EDGE = 8        /* forward: extend each signal with its edge values instead of zeros
+  MORLET_FLAG_EDGE = 8,       /* forward: extend each signal with its edge values instead of zeros
                                  (Sec. II: "zero or the values on the edges"); the plan holds a padded
                                  copy of the batch (the longest window reach on each side), refreshed
                                  by every forward; morlet_backward returns MORLET_ERR_UNSUPPORTED */
+  MORLET_FLAG_NO_ADJOINT = 16 /* build no adjoint: the plan does not hold the adjoint's workspace (two
+                                 real planes per scale of the batch); morlet_backward returns
+                                 MORLET_ERR_UNSUPPORTED */
 };
 
 typedef struct {
@@ -138,8 +141,16 @@ int morlet_forward(morlet_plan_t plan, const void* x, void* W, void* stream);
  * morlet_backward - adjoint of morlet_forward for a real-valued loss (SFT, MORLET_DIRECT only).
  * gW: device complex [signal][scale][n], gW = dLoss/dRe W + i dLoss/dIm W.
  * gx: device real, same layout as x: gx[t] = sum_scales sum_n Re(conj(gW[n]) dW[n]/dx[t]).
- * The scale sum is done in a fixed order (deterministic). Uses the plan's workspace.
- * Errors: MORLET_ERR_UNSUPPORTED for ASFT or MORLET_GAUSS plans.
+ * The fitted kernel has an even real and an odd imaginary part (Sec. III-A), so the adjoint of
+ * scale s is gx_s = Re W_s(Re gW_s) - Im W_s(Im gW_s), W_s the forward transform of a real signal.
+ * The call splits gW into its 2S real planes (planes of n_in = sum of lengths samples, held by the
+ * plan), runs their real-output transforms in one launch on the forward's kernels (rotating form,
+ * same precision; start states for long windows), and sums the 2S result planes in a fixed order
+ * (deterministic). Asynchronous; captured once per (gW, gx) pair into a CUDA graph and replayed
+ * (unless MORLET_FLAG_NO_GRAPH). A plan's forward and backward share its look-back status arrays:
+ * do not run them concurrently on different streams.
+ * Errors: MORLET_ERR_UNSUPPORTED for ASFT, MORLET_GAUSS, MORLET_MULTIPLY, MORLET_FLAG_EDGE or
+ * MORLET_FLAG_NO_ADJOINT plans.
  */
 int morlet_backward(morlet_plan_t plan, const void* gW, void* gx, void* stream);
 

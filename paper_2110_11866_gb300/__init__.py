@@ -16,7 +16,8 @@ __all__ = [
     "MORLET_OK", "MORLET_ERR_ARG", "MORLET_ERR_UNSUPPORTED", "MORLET_ERR_CUDA", "MORLET_ERR_TIMEOUT",
     "MORLET_ERR_NOMEM", "MORLET_DIRECT", "MORLET_GAUSS", "MORLET_MULTIPLY", "MORLET_SFT", "MORLET_ASFT", "MORLET_FP32_PLAIN",
     "MORLET_FP32_COMP", "MORLET_FP64", "MORLET_FORM_AUTO", "MORLET_FORM_KERNEL", "MORLET_FORM_ROTATING",
-    "MORLET_FLAG_NO_GRAPH", "MORLET_FLAG_AUTOTUNE", "MORLET_FLAG_NO_HALO", "MORLET_FLAG_EDGE", "MorletError", "lib", "lib_path",
+    "MORLET_FLAG_NO_GRAPH", "MORLET_FLAG_AUTOTUNE", "MORLET_FLAG_NO_HALO", "MORLET_FLAG_EDGE", "MORLET_FLAG_NO_ADJOINT",
+    "MorletError", "lib", "lib_path",
     "morlet_plan", "morlet_forward", "morlet_backward", "gauss_smooth", "morlet_plan_destroy",
     "morlet_strerror", "morlet_last_device_error", "morlet_plan_info", "morlet_plan_stats",
     "morlet_plan_set_spin_limit", "morlet_debug_skip_tickets", "EXPORTED_SYMBOLS", "source_hash",
@@ -30,7 +31,7 @@ MORLET_DIRECT, MORLET_GAUSS, MORLET_MULTIPLY = 0, 1, 2
 MORLET_SFT, MORLET_ASFT = 0, 1
 MORLET_FP32_PLAIN, MORLET_FP32_COMP, MORLET_FP64 = 0, 1, 2
 MORLET_FORM_AUTO, MORLET_FORM_KERNEL, MORLET_FORM_ROTATING = 0, 1, 2
-MORLET_FLAG_NO_GRAPH, MORLET_FLAG_AUTOTUNE, MORLET_FLAG_NO_HALO, MORLET_FLAG_EDGE = 1, 2, 4, 8
+MORLET_FLAG_NO_GRAPH, MORLET_FLAG_AUTOTUNE, MORLET_FLAG_NO_HALO, MORLET_FLAG_EDGE, MORLET_FLAG_NO_ADJOINT = 1, 2, 4, 8, 16
 
 EXPORTED_SYMBOLS = [
     "morlet_plan", "morlet_forward", "morlet_backward", "gauss_smooth", "morlet_plan_destroy",

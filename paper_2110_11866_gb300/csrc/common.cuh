@@ -77,11 +77,13 @@ struct ScaleTab {
   double2 pw_wofs[8][KMAX];   // rho^{items * 32 * w}
   double2 pw_lane[32][KMAX];  // rho^{items * lane}
   double2 pw_tile[33][KMAX];  // rho^{THREADS * items * q}
+  double2 pw_lane_t[KMAX][32];  // pw_lane term-major (the FP64 warp kernel's per-lane reads)
   const float2* ph_hi;        // kernel-integral form: e^{i pi 1024 a / L}, a = 0 .. 2L/1024
   const float2* ph_lo;        // kernel-integral form: e^{i pi b / L}, b = 0 .. 1023
   // FP32 copies for the warp-independent kernel
   float2 f_pw_thr[5][KMAX];   // rho^{items * 2^l}
-  float2 f_pw_lane[32][KMAX]; // rho^{items * lane}
+  float2 f_pw_lane_t[KMAX][32];  // rho^{items * lane}, term-major: the 32 lanes of a warp read one
+                                 // term's powers from 256 contiguous bytes (two cache lines)
   float2 f_pwt[2][KMAX];      // rho^{items * 32} as hi + lo
   float4 c_pw_tile[33][KMAX]; // pw_tile as two-float complex (re.hi, re.lo, im.hi, im.lo)
   float4 c_pw_chunk[8][KMAX]; // rho^{32 items (m + 1)}, m = 0..7, two-float complex
@@ -139,7 +141,6 @@ struct KParams {
   void* pbuf;                // start-state rows: per 512-position tile, K two-float complex prefix
                              // sums (ss_window = 0) or K FP32 complex tile sums (ss_window = 1)
   int ss_window;             // start states from window sums of tile sums instead of prefix sums
-  int accumulate;            // adjoint: add to the output instead of overwriting it
 };
 
 // ------------------------------------------------------------------------------------------------
@@ -211,6 +212,7 @@ __device__ __forceinline__ float2 pk_fma(float2 a, float2 b, float2 c) { return 
 __device__ __forceinline__ float2 pk_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 pk_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 pk_dup(float a) { return make_float2(a, a); }
+
 
 template <int K>
 struct Pairs {

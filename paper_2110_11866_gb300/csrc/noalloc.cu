@@ -161,7 +161,6 @@ extern "C" int morlet_forward_noalloc(const void* x, int64_t N, double sigma, do
   kp.ticket = (unsigned long long*)(base + OFF_TICKET);
   kp.err = (int*)(base + OFF_ERR);
   kp.spin_limit = 1LL << 20;
-  kp.accumulate = 0;
   kp.n_chain = chained ? n_work : 0;
   kp.n_x = N;
   void* args[] = {&kp};

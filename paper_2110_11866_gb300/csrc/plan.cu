@@ -25,9 +25,6 @@ MSFT_DECL(kernel_rf_f64_morlet)
 MSFT_DECL(kernel_rf_f32c_real)
 MSFT_DECL(kernel_rf_f32p_real)
 MSFT_DECL(kernel_rf_f64_real)
-MSFT_DECL(kernel_rf_f32c_adj)
-MSFT_DECL(kernel_rf_f32p_adj)
-MSFT_DECL(kernel_rf_f64_adj)
 #undef MSFT_DECL
 const void* kernel_ki_f32c_morlet(int);
 const void* kernel_ki_f32p_morlet(int);
@@ -49,9 +46,6 @@ const void* kernel_for(int variant, int K, bool warp) {
     case V_RF_F32C_REAL: return warp ? kernel_rf_f32c_real_w(K) : kernel_rf_f32c_real(K);
     case V_RF_F32P_REAL: return warp ? kernel_rf_f32p_real_w(K) : kernel_rf_f32p_real(K);
     case V_RF_F64_REAL: return warp ? kernel_rf_f64_real_w(K) : kernel_rf_f64_real(K);
-    case V_RF_F32C_ADJ: return warp ? kernel_rf_f32c_adj_w(K) : kernel_rf_f32c_adj(K);
-    case V_RF_F32P_ADJ: return warp ? kernel_rf_f32p_adj_w(K) : kernel_rf_f32p_adj(K);
-    case V_RF_F64_ADJ: return warp ? kernel_rf_f64_adj_w(K) : kernel_rf_f64_adj(K);
     default: return nullptr;
   }
 }
@@ -96,8 +90,9 @@ struct Launch {
   int grid_w = 0;
   long long sub_tiles = 0;
   long long rows_chain = 0, rows_halo = 0;
-  std::vector<long long> scale_begin;  // adjoint: work items of scale s are [scale_begin[s], scale_begin[s+1])
-  std::vector<long long> chain_end;    // per launch range: look-back items come first, up to chain_end
+  long long chain_end = 0;             // look-back items come first, [0, chain_end)
+  const ScaleTab* tabs = nullptr;      // the scales the rows refer to (the adjoint's 2S virtual scales)
+  long long n_x = 0;                   // elements of the input buffer the rows read
   // start-state rows (forward, compensated FP32, long windows): warp-kernel items [ss_begin, n_work)
   // start from the prefix sums that the psum kernel computes over the work items d_pwork
   long long ss_begin = 0;
@@ -107,6 +102,12 @@ struct Launch {
   int grid_p = 0;
   long long n_pslots = 0, n_ptiles = 0, rows_ss = 0;
   int ss_window = 0;  // start states from window sums of tile sums (tsum kernel) instead of prefix sums
+  // start-state workspace: prefix-sum status flags, aggregates and inclusive values, and the prefix
+  // sums (or tile sums) at tile ends
+  uint32_t* d_pflags = nullptr;
+  void* d_pagg = nullptr;
+  void* d_pincl = nullptr;
+  void* d_pbuf = nullptr;
   // lane-chunk rows (forward, compensated FP32 Morlet, short windows): items d_lwork
   const void* func_l = nullptr;
   WorkItem* d_lwork = nullptr;
@@ -145,11 +146,18 @@ struct morlet_plan_s {
   void* d_agg = nullptr;
   void* d_incl = nullptr;
   long long n_slots = 0;
-  int nt_slot = 0;               // complex carry values per look-back slot (2K with an adjoint, else K)
-  uint32_t* d_pflags = nullptr;  // prefix-sum kernel: status flags, aggregates, inclusive states
-  void* d_pagg = nullptr;
-  void* d_pincl = nullptr;
-  void* d_pbuf = nullptr;        // prefix sums at tile ends
+  int nt_slot = 0;               // complex carry values per look-back slot
+  // adjoint (morlet_backward): the real and imaginary planes of gW as real signals at 2S virtual
+  // scales (q = 2s: weights (cM, 0); q = 2s + 1: (0, -cL), rotating-form tables), their real
+  // transforms, one plane per virtual scale, and the descriptors the split kernel reads
+  std::vector<ScaleTab> h_tabs_adj;
+  ScaleTab* d_tabs_adj = nullptr;
+  void* d_gplanes = nullptr;
+  void* d_wplanes = nullptr;
+  int64_t* d_sig_desc = nullptr;  // per signal: x_off, N
+  cudaGraphExec_t gexec_b = nullptr;
+  const void* gb_in = nullptr;
+  void* gb_out = nullptr;
   long long ss_min_L = 0;        // rows with L above this use start states (0: none)
   long long ls_max_L = 0;        // rows with L up to this use the lane-chunk scan (0: none)
   // schedule knobs (MORLET_FLAG_AUTOTUNE or morlet_plan_set_schedule); none changes the transform
@@ -198,7 +206,8 @@ int round_k(int K) {
 
 int variant_of(const morlet_plan_s* p, bool adjoint) {
   const int prec = p->desc.precision;
-  if (adjoint) return prec == MORLET_FP64 ? V_RF_F64_ADJ : prec == MORLET_FP32_COMP ? V_RF_F32C_ADJ : V_RF_F32P_ADJ;
+  // the adjoint runs real-output rotating-form rows on the planes of gW
+  if (adjoint) return prec == MORLET_FP64 ? V_RF_F64_REAL : prec == MORLET_FP32_COMP ? V_RF_F32C_REAL : V_RF_F32P_REAL;
   if (p->desc.method == MORLET_MULTIPLY) return V_RF_F32P_MULT;
   if (p->desc.method == MORLET_GAUSS) {
     if (p->desc.transform == MORLET_ASFT) return V_RF_F32P_ASFT_REAL;
@@ -240,7 +249,10 @@ bool horner_plan(const morlet_plan_s* p) {
 //    of 2L + 1 samples summed from FP32 tile sums; the damped sum of the ASFT forgets the tile sums'
 //    rounding, the multiplication method's sums carry it like the SFT's window sums do).
 bool ss_row(const morlet_plan_s* p, bool adjoint, const ScaleTab& tb) {
-  if (adjoint) return false;
+  // the adjoint's rows are compensated (or plain, or FP64) real-output SFT rows in the rotating form
+  if (adjoint)
+    return p->ss_min_L > 0 && p->desc.precision == MORLET_FP32_COMP && !(p->desc.flags & MORLET_FLAG_NO_HALO) &&
+           tb.L > p->ss_min_L;
   if (horner_plan(p)) return tb.L > TILE;
   return p->ss_min_L > 0 && p->form == 2 && p->desc.precision == MORLET_FP32_COMP &&
          p->desc.transform == MORLET_SFT && p->desc.method != MORLET_MULTIPLY &&
@@ -267,23 +279,20 @@ void ss_tiles(long long x_off, long long o_lo, long long o_hi, long long& t_grid
 void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& work, std::vector<ChainDesc>& chains,
                 long long& slots, Launch& ln, std::vector<WorkItem>& pwork, std::vector<WorkItem>& lwork,
                 long long warp_slots) {
-  const int S = (int)p->sigmas.size();
+  // Forward: the S scales. Adjoint: 2S virtual scales q, the real (q = 2s) and imaginary (q = 2s + 1)
+  // plane of gW at scale s, each row reading and writing plane q (planes of n_in samples).
+  const int S = adjoint ? 2 * (int)p->sigmas.size() : (int)p->sigmas.size();
+  const std::vector<ScaleTab>& tabs = adjoint ? p->h_tabs_adj : p->h_tabs;
   const long long nsig = (long long)p->lengths.size();
-  // Row order. Forward: blocks of signals holding about 16 M input samples, scale by scale inside a
-  // block, so that a block's samples are mostly served from L2 to its later scales. Adjoint:
-  // scale-major (each scale is one launch that adds into the gradient).
-  // With p->order = 1 the scales of a block go in decreasing L, so that the last items claimed are the
-  // short ones and the kernels' tails are short.
+  // Row order: blocks of signals holding about 16 M input samples, scale by scale inside a block, so
+  // that a block's samples are mostly served from L2 to its later scales. With p->order = 1 the scales
+  // of a block go in decreasing L, so that the last items claimed are the short ones.
   std::vector<int> sorder(S);
   for (int s = 0; s < S; ++s) sorder[s] = s;
-  if (p->order == 1 && !adjoint)
-    std::stable_sort(sorder.begin(), sorder.end(),
-                     [p](int a, int b) { return p->h_tabs[a].L > p->h_tabs[b].L; });
+  if (p->order == 1)
+    std::stable_sort(sorder.begin(), sorder.end(), [&tabs](int a, int b) { return tabs[a].L > tabs[b].L; });
   std::vector<std::pair<long long, int>> order;  // (signal, scale)
-  if (adjoint) {
-    for (int s = 0; s < S; ++s)
-      for (long long i = 0; i < nsig; ++i) order.push_back({i, s});
-  } else {
+  {
     long long b0 = 0;
     while (b0 < nsig) {
       long long b1 = b0, acc = 0;
@@ -293,15 +302,24 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
       b0 = b1;
     }
   }
-  const int esz = (int)p->elem * (adjoint ? 2 : 1);  // bytes per input element
+  const int esz = (int)p->elem;  // bytes per input element
+  const long long E = adjoint ? 0 : p->pad;
+  // the row (signal i, scale s): first input element, first output element
+  auto row_in = [&](long long i, int s) -> long long {
+    if (adjoint) return (long long)s * p->n_in + p->x_off[i];
+    return E ? p->xp_off[i] : p->x_off[i];
+  };
+  auto row_out = [&](long long i, int s) -> long long {
+    if (adjoint) return (long long)s * p->n_in + p->x_off[i];
+    return (long long)S * p->x_off[i] + (long long)s * p->lengths[i] - E;  // scalogram row (minus the pad)
+  };
   // start-state items: n_ss tiles each, as many tiles as leaves about four items per warp slot
   long long ss_total = 0;
   for (auto& rs : order) {
-    const ScaleTab& tb = p->h_tabs[rs.second];
+    const ScaleTab& tb = tabs[rs.second];
     if (!ss_row(p, adjoint, tb)) continue;
     long long tg, kD, kE;
-    const long long E = adjoint ? 0 : p->pad;
-    ss_tiles(E ? p->xp_off[rs.first] : p->x_off[rs.first], tb.D + E, tb.D + E + p->lengths[rs.first], tg, kD, kE);
+    ss_tiles(row_in(rs.first, rs.second), tb.D + E, tb.D + E + p->lengths[rs.first], tg, kD, kE);
     ss_total += kE - kD + 1;
   }
   const long long n_ss = std::max(4LL, std::min(p->ss_tiles_max, ss_total / std::max(1LL, 4 * warp_slots)));
@@ -309,29 +327,21 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
   // unless the window is much longer; then the prefix sums (one chained pass) are used instead.
   long long max_win = 0;
   for (auto& rs : order)
-    if (ss_row(p, adjoint, p->h_tabs[rs.second])) max_win = std::max<long long>(max_win, 2 * p->h_tabs[rs.second].L / PS_TILE_H + 2);
-  ln.ss_window = (horner_plan(p) || max_win <= 16 * n_ss) ? 1 : 0;  // Horner rows: window sums only
-  ln.scale_begin.assign(S + 1, 0);
-  int prev_scale = -1;
+    if (ss_row(p, adjoint, tabs[rs.second])) max_win = std::max<long long>(max_win, 2 * tabs[rs.second].L / PS_TILE_H + 2);
+  ln.ss_window = ((!adjoint && horner_plan(p)) || max_win <= 16 * n_ss) ? 1 : 0;  // Horner rows: window sums only
   for (auto& rs : order) {
     const long long i = rs.first;
     const int s = rs.second;
-    if (adjoint && s != prev_scale) {
-      for (int q = prev_scale + 1; q <= s; ++q) ln.scale_begin[q] = (long long)work.size();
-      prev_scale = s;
-    }
-    const ScaleTab& tb = p->h_tabs[s];
+    const ScaleTab& tb = tabs[s];
     const long long N0 = p->lengths[i];
     // edge mode: the row is the padded signal (N0 + 2E samples) and stores positions
     // [D + E, D + E + N0), i.e. the outputs of the original samples
-    const long long E = adjoint ? 0 : p->pad;
     const long long N = N0 + 2 * E;
     const long long o_lo = tb.D + E, o_hi = tb.D + E + N0;
     ChainDesc c{};
     c.n = N;
-    const long long row = (long long)S * p->x_off[i] + (long long)s * N0;  // scalogram row
-    c.x_off = adjoint ? row : (E ? p->xp_off[i] : p->x_off[i]);
-    c.out_off = adjoint ? p->x_off[i] : row - E;
+    c.x_off = row_in(i, s);
+    c.out_off = row_out(i, s);
     c.scale = s;
     const int ci = (int)chains.size();
     chains.push_back(c);
@@ -395,30 +405,46 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
         ln.sub_tiles += nsub;
         k_last = k;
       }
-      // tile sums (window mode) or prefix sums at the ends of tiles 0 .. k_last - 1, in chunks
+      // Prefix sums at the ends of tiles 0 .. k_last - 1 (prefix mode: every tile); or tile sums
+      // (window mode) of the tiles inside the windows of the item starts kb, [kb - wt, kb - 1] with
+      // wt = ceil((2L + 1) / 512) + 1 (a window spans at most that many tiles), in chunks.
       const long long n_t = k_last;
       const long long first = ln.n_pslots;
       const long long chunk = ln.ss_window ? TS_CHUNK_H : PS_CHUNK_H;
-      for (long long k = 0; k < n_t; k += chunk) {
-        WorkItem w{};
-        w.x_off = c.x_off;
-        w.n = N;
-        w.out_off = c.out_off;
-        w.scale = s;
-        w.chain = ci;
-        w.n_sub = (int)std::min(chunk, n_t - k);
-        w.t_a = tg + PS_TILE_H * k;
-        w.slot = ln.n_pslots++;
-        w.slot_first = first;
-        w.p_row = pbase + k;
-        w.t_grid = tg;
-        pwork.push_back(w);
+      std::vector<std::pair<long long, long long>> need;  // tile ranges [a, b)
+      if (ln.ss_window) {
+        const long long wt = (2 * tb.L + 1 + PS_TILE_H - 1) / PS_TILE_H + 1;
+        for (long long kb = kD; kb <= k_last; kb += n_ss) {
+          const long long a = std::max(0LL, kb - wt), b = kb;
+          if (a >= b) continue;
+          if (!need.empty() && a <= need.back().second) need.back().second = std::max(need.back().second, b);
+          else need.push_back({a, b});
+        }
+      } else {
+        need.push_back({0, n_t});
+      }
+      for (auto& rg : need) {
+        for (long long k = rg.first; k < rg.second; k += chunk) {
+          WorkItem w{};
+          w.x_off = c.x_off;
+          w.n = N;
+          w.out_off = c.out_off;
+          w.scale = s;
+          w.chain = ci;
+          w.n_sub = (int)std::min(chunk, rg.second - k);
+          w.t_a = tg + PS_TILE_H * k;
+          w.slot = ln.n_pslots++;
+          w.slot_first = first;
+          w.p_row = pbase + k;
+          w.t_grid = tg;
+          pwork.push_back(w);
+        }
       }
       ln.n_ptiles += n_t;
       ln.rows_ss++;
       continue;
     }
-    const bool warp_window = (p->form != 1);
+    const bool warp_window = adjoint || p->form != 1;  // the adjoint's rows are rotating-form rows
     const RowSpec r = make_row_spec(N, tb.L, tb.D, c.x_off, c.out_off, s, esz, seg_policy(p), ci, warp_window,
                                     TILE, o_lo, o_hi, p->seg_mult);
     long long sl = slots, st = 0;
@@ -432,25 +458,13 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
     if (chained) ln.rows_chain++;
     else ln.rows_halo++;
   }
-  if (adjoint)
-    for (int q = prev_scale + 1; q <= S; ++q) ln.scale_begin[q] = (long long)work.size();
-  // Inside every launch range put the look-back items first (stable), so that independent items
-  // may claim their successor ticket early without ever holding an item that others wait on.
-  std::vector<std::pair<long long, long long>> ranges;
-  if (adjoint)
-    for (int q = 0; q < S; ++q) ranges.push_back({ln.scale_begin[q], ln.scale_begin[q + 1]});
-  else
-    ranges.push_back({0, (long long)work.size()});
-  ln.chain_end.clear();
-  for (auto& rg : ranges) {
-    auto mid = std::stable_partition(work.begin() + rg.first, work.begin() + rg.second,
-                                     [](const WorkItem& w) { return w.slot >= 0; });
-    ln.chain_end.push_back((long long)(mid - work.begin()));
-    // then the window items, then the start-state items (which wait for the prefix sums)
-    auto ss = std::stable_partition(mid, work.begin() + rg.second, [](const WorkItem& w) { return w.p_row < 0; });
-    ln.ss_begin = (long long)(ss - work.begin());
-  }
-  if (adjoint) ln.ss_begin = (long long)work.size();
+  // Put the look-back items first (stable), so that independent items may claim their successor ticket
+  // early without ever holding an item that others wait on; then the window items, then the
+  // start-state items (which wait for the prefix or tile sums).
+  auto mid = std::stable_partition(work.begin(), work.end(), [](const WorkItem& w) { return w.slot >= 0; });
+  ln.chain_end = (long long)(mid - work.begin());
+  auto ss = std::stable_partition(mid, work.end(), [](const WorkItem& w) { return w.p_row < 0; });
+  ln.ss_begin = (long long)(ss - work.begin());
 }
 
 int setup_launch(morlet_plan_s* p, bool adjoint, Launch& ln, long long& slots) {
@@ -459,7 +473,9 @@ int setup_launch(morlet_plan_s* p, bool adjoint, Launch& ln, long long& slots) {
   std::vector<ChainDesc> chains;
   ln.func = kernel_for(variant_of(p, adjoint), p->K_kernel, false);
   if (!ln.func) return MORLET_ERR_UNSUPPORTED;
-  if (p->form != 1) {
+  ln.tabs = adjoint ? p->d_tabs_adj : p->d_tabs;
+  ln.n_x = adjoint ? 2 * (long long)p->sigmas.size() * p->n_in : (p->pad > 0 ? p->n_xpad : p->n_in);
+  if (adjoint || p->form != 1) {
     ln.func_w = kernel_for(variant_of(p, adjoint), p->K_kernel, true);
     if (!ln.func_w) return MORLET_ERR_UNSUPPORTED;
     int occw = 0;
@@ -479,7 +495,7 @@ int setup_launch(morlet_plan_s* p, bool adjoint, Launch& ln, long long& slots) {
     ln.grid = (int)std::min<long long>((long long)occ * p->sms, std::max<long long>(1, ln.n_work));
   }
   if (!pwork.empty()) {
-    ln.func_p = horner_plan(p) ? kernel_tsum_h(p->K_kernel)
+    ln.func_p = (!adjoint && horner_plan(p)) ? kernel_tsum_h(p->K_kernel)
                 : ln.ss_window ? kernel_tsum(p->K_kernel) : kernel_psum(p->K_kernel);
     if (!ln.func_p) return MORLET_ERR_UNSUPPORTED;
     int occp = 0;
@@ -515,10 +531,16 @@ void free_launch(Launch& ln) {
   cudaFree(ln.d_chains);
   cudaFree(ln.d_pwork);
   cudaFree(ln.d_lwork);
+  cudaFree(ln.d_pflags);
+  cudaFree(ln.d_pagg);
+  cudaFree(ln.d_pincl);
+  cudaFree(ln.d_pbuf);
   ln.d_work = nullptr;
   ln.d_chains = nullptr;
   ln.d_pwork = nullptr;
   ln.d_lwork = nullptr;
+  ln.d_pflags = nullptr;
+  ln.d_pagg = ln.d_pincl = ln.d_pbuf = nullptr;
 }
 
 int check_latched(morlet_plan_s* p) {
@@ -535,11 +557,6 @@ size_t carry_bytes(const morlet_plan_s* p) {
   return (p->desc.precision == MORLET_FP32_PLAIN || p->desc.transform == MORLET_ASFT) ? 8 : 16;
 }
 
-// Enqueue one launch range: reset its work counters (and the status flags), then
-//  - on the plan's second stream, the warp kernel over the window items;
-//  - on `st`, the prefix-sum kernel and after it the warp kernel over the start-state items, then
-//    the look-back kernel over the chain items.
-// tickets[0..3] count the look-back, window, start-state and prefix-sum kernels.
 // Edge mode: xp[xp_off_i + j] = x[x_off_i + clamp(j - E, 0, N_i - 1)] for j in [0, N_i + 2E) (the
 // paper's "values on the edges of the interval" extension, Sec. II).
 template <typename T>
@@ -570,11 +587,18 @@ cudaError_t pad_edges(const morlet_plan_s* p, const void* x, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out, long long w_begin, long long w_end,
-                    long long w_chain_end, unsigned long long* tickets, bool clear_flags, cudaStream_t st,
-                    int accumulate = 0) {
+// Enqueue one launch: reset its work counters (and the status flags), then
+//  - on the plan's second stream, the lane-chunk kernel and the warp kernel over the window items;
+//  - on `st`, the prefix-sum (or tile-sum) kernel and after it the warp kernel over the start-state
+//    items, then the look-back kernel over the chain items;
+// and join the second stream back into `st`. tickets[0..4] count the look-back, window, start-state,
+// prefix-sum and lane-chunk kernels. `x` is the buffer the rows read (the forward's input, its padded
+// copy in edge mode, or the adjoint's planes), `out` the buffer they write.
+cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out, unsigned long long* tickets,
+                    cudaStream_t st) {
+  const long long w_end = ln.n_work;
   const bool two = ln.func_w != nullptr;
-  const long long c_end = two ? w_chain_end : w_end;
+  const long long c_end = two ? ln.chain_end : w_end;
   const long long s_beg = two ? std::min(std::max(ln.ss_begin, c_end), w_end) : w_end;
   cudaError_t e = cudaMemsetAsync(tickets, 0, TICKETS * sizeof(unsigned long long), st);
   if (e == cudaSuccess && p->skip_tickets > 0) {
@@ -586,7 +610,7 @@ cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out
     p->skip_tickets = 0;
   }
   if (e != cudaSuccess) return e;
-  if (clear_flags && p->n_slots > 0) {
+  if (c_end > 0 && p->n_slots > 0) {
     e = cudaMemsetAsync(p->d_flags, 0, sizeof(uint32_t) * p->n_slots, st);
     if (e != cudaSuccess) return e;
   }
@@ -594,23 +618,16 @@ cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out
   kp.x = x;
   kp.out = out;
   kp.chains = ln.d_chains;
-  kp.tabs = p->d_tabs;
+  kp.tabs = ln.tabs;
   kp.flags = p->d_flags;
   kp.agg = p->d_agg;
   kp.incl = p->d_incl;
   kp.err = p->d_err;
   kp.spin_limit = p->spin;
-  kp.accumulate = accumulate;
-  kp.n_x = (&ln == &p->adj) ? p->n_in * (long long)p->sigmas.size() : p->n_in;  // adjoint reads the scalogram
-  if (p->pad > 0 && &ln == &p->fwd) {  // edge mode: the rows read the padded copy of x
-    e = pad_edges(p, x, st);
-    if (e != cudaSuccess) return e;
-    kp.x = p->d_xpad;
-    kp.n_x = p->n_xpad;
-  }
-  kp.pbuf = p->d_pbuf;
+  kp.n_x = ln.n_x;
+  kp.pbuf = ln.d_pbuf;
   bool forked = false;
-  const bool lane_items = ln.n_lwork > 0 && &ln == &p->fwd;
+  const bool lane_items = ln.n_lwork > 0;
   if ((two && s_beg > c_end) || lane_items) {
     e = cudaEventRecord(p->ev_fork, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(p->aux, p->ev_fork, 0);
@@ -644,16 +661,16 @@ cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out
   if (two && w_end > s_beg) {
     if (ln.n_pwork > 0) {
       if (!ln.ss_window) {
-        e = cudaMemsetAsync(p->d_pflags, 0, sizeof(uint32_t) * ln.n_pslots, st);
+        e = cudaMemsetAsync(ln.d_pflags, 0, sizeof(uint32_t) * ln.n_pslots, st);
         if (e != cudaSuccess) return e;
       }
       KParams kq = kp;
       kq.work = ln.d_pwork;
       kq.n_work = ln.n_pwork;
       kq.n_chain = ln.n_pwork;
-      kq.flags = p->d_pflags;
-      kq.agg = p->d_pagg;
-      kq.incl = p->d_pincl;
+      kq.flags = ln.d_pflags;
+      kq.agg = ln.d_pagg;
+      kq.incl = ln.d_pincl;
       kq.ticket = tickets + 3;
       void* args[] = {&kq};
       const int grid = (int)std::min<long long>(ln.grid_p, (kq.n_work + WARPS - 1) / WARPS);
@@ -671,10 +688,10 @@ cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out
     e = cudaLaunchKernel(ln.func_w, dim3(grid), dim3(THREADS), args, 0, st);
     if (e != cudaSuccess) return e;
   }
-  if (c_end > w_begin) {
-    kp.work = ln.d_work + w_begin;
-    kp.n_work = c_end - w_begin;
-    kp.n_chain = std::min(w_chain_end, c_end) - w_begin;
+  if (c_end > 0) {
+    kp.work = ln.d_work;
+    kp.n_work = c_end;
+    kp.n_chain = std::min(ln.chain_end, c_end);
     kp.ticket = tickets;
     void* args[] = {&kp};
     const int grid = (int)std::min<long long>(ln.grid, kp.n_work);
@@ -685,32 +702,100 @@ cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out
   return e;
 }
 
-// Workspace of the start-state rows: tile sums (K FP32 complex per tile) in window mode; prefix sums
-// (K two-float complex per tile) plus the look-back status, aggregates and inclusive values otherwise.
-int alloc_prefix(morlet_plan_s* p) {
+// Workspace of a launch's start-state rows: tile sums (K FP32 complex per tile) in window mode; prefix
+// sums (K two-float complex per tile) plus the look-back status, aggregates and inclusive values
+// otherwise.
+int alloc_prefix(morlet_plan_s* p, Launch& f) {
   int rc = MORLET_OK;
-  const Launch& f = p->fwd;
   if (f.ss_window) {
-    CK(cudaMalloc(&p->d_pbuf, sizeof(float2) * p->K_kernel * std::max(1LL, f.n_ptiles)));
+    CK(cudaMalloc(&f.d_pbuf, sizeof(float2) * p->K_kernel * std::max(1LL, f.n_ptiles)));
   } else {
     const size_t kb = sizeof(float4) * p->K_kernel;  // K two-float complex values
-    CK(cudaMalloc(&p->d_pflags, sizeof(uint32_t) * f.n_pslots));
-    CK(cudaMalloc(&p->d_pagg, kb * f.n_pslots));
-    CK(cudaMalloc(&p->d_pincl, kb * f.n_pslots));
-    CK(cudaMalloc(&p->d_pbuf, kb * std::max(1LL, f.n_ptiles)));
+    CK(cudaMalloc(&f.d_pflags, sizeof(uint32_t) * f.n_pslots));
+    CK(cudaMalloc(&f.d_pagg, kb * f.n_pslots));
+    CK(cudaMalloc(&f.d_pincl, kb * f.n_pslots));
+    CK(cudaMalloc(&f.d_pbuf, kb * std::max(1LL, f.n_ptiles)));
   }
   return MORLET_OK;
 fail:
   return rc;
 }
 
-// The forward as one CUDA graph (memsets and kernels of both streams), captured once per (x, W);
-// replays are a single graph launch.
-cudaError_t forward_graph(morlet_plan_s* p, const void* x, void* W) {
-  if (p->gexec && p->g_x == x && p->g_out == W) return cudaSuccess;
-  if (p->gexec) {
-    cudaGraphExecDestroy(p->gexec);
-    p->gexec = nullptr;
+// The adjoint's input: gW [signal][scale][n] (complex) split into its real and imaginary planes,
+// plane 2s (real) and 2s + 1 (imaginary) of n_in samples each, signal i at x_off_i in every plane.
+template <typename T>
+__global__ void split_planes_kernel(const T* __restrict__ g, T* __restrict__ planes, const int64_t* __restrict__ desc,
+                                    int64_t nsig, int32_t S, int64_t n_in) {
+  for (int64_t r = blockIdx.y; r < nsig * S; r += gridDim.y) {
+    const int64_t i = r / S, s = r % S;
+    const int64_t xo = desc[2 * i], n = desc[2 * i + 1];
+    const T* gr = g + 2 * (S * xo + s * n);
+    T* pa = planes + (2 * s) * n_in + xo;
+    T* pb = pa + n_in;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+      pa[j] = gr[2 * j];
+      pb[j] = gr[2 * j + 1];
+    }
+  }
+}
+
+// gx[t] = sum over the 2S planes in order (q = 0, 1, ..., 2S - 1), so the sum over scales has a fixed
+// order (deterministic, no atomics).
+template <typename T>
+__global__ void sum_planes_kernel(const T* __restrict__ planes, T* __restrict__ gx, int32_t nq, int64_t n_in) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_in; t += (int64_t)gridDim.x * blockDim.x) {
+    T acc = planes[t];
+    for (int32_t q = 1; q < nq; ++q) acc += planes[q * n_in + t];
+    gx[t] = acc;
+  }
+}
+
+// One forward: the edge-padded copy of x first in edge mode, then the launch.
+cudaError_t forward_enqueue(morlet_plan_s* p, const void* x, void* W, cudaStream_t st) {
+  if (p->pad > 0) {
+    const cudaError_t e = pad_edges(p, x, st);
+    if (e != cudaSuccess) return e;
+    x = p->d_xpad;
+  }
+  return enqueue(p, p->fwd, x, W, p->d_ticket, st);
+}
+
+// One backward: split gW into planes, the real transforms of the 2S planes, the ordered plane sum.
+cudaError_t backward_enqueue(morlet_plan_s* p, const void* gW, void* gx, cudaStream_t st) {
+  const long long nsig = (long long)p->lengths.size();
+  const int S = (int)p->sigmas.size();
+  long long longest = 0;
+  for (auto n : p->lengths) longest = std::max<long long>(longest, n);
+  const dim3 gs((unsigned)std::min<long long>(256, (longest + 255) / 256), (unsigned)std::min<long long>(65535, nsig * S));
+  const unsigned gr = (unsigned)std::min<long long>(4LL * p->sms * 8, (p->n_in + 255) / 256);
+  if (p->elem == 8)
+    split_planes_kernel<double><<<gs, 256, 0, st>>>(static_cast<const double*>(gW), static_cast<double*>(p->d_gplanes),
+                                                    p->d_sig_desc, nsig, S, p->n_in);
+  else
+    split_planes_kernel<float><<<gs, 256, 0, st>>>(static_cast<const float*>(gW), static_cast<float*>(p->d_gplanes),
+                                                   p->d_sig_desc, nsig, S, p->n_in);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = enqueue(p, p->adj, p->d_gplanes, p->d_wplanes, p->d_ticket + TICKETS, st);
+  if (e != cudaSuccess) return e;
+  if (p->elem == 8)
+    sum_planes_kernel<double><<<gr, 256, 0, st>>>(static_cast<const double*>(p->d_wplanes), static_cast<double*>(gx),
+                                                  2 * S, p->n_in);
+  else
+    sum_planes_kernel<float><<<gr, 256, 0, st>>>(static_cast<const float*>(p->d_wplanes), static_cast<float*>(gx),
+                                                 2 * S, p->n_in);
+  return cudaGetLastError();
+}
+
+// The forward (or backward) as one CUDA graph (memsets and kernels of both streams), captured once
+// per (input, output) pair; replays are a single graph launch.
+cudaError_t capture_graph(morlet_plan_s* p, bool backward, const void* in, void* out) {
+  cudaGraphExec_t& gx = backward ? p->gexec_b : p->gexec;
+  const void*& gin = backward ? p->gb_in : p->g_x;
+  void*& gout = backward ? p->gb_out : p->g_out;
+  if (gx && gin == in && gout == out) return cudaSuccess;
+  if (gx) {
+    cudaGraphExecDestroy(gx);
+    gx = nullptr;
   }
   cudaStream_t cs;
   cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
@@ -718,23 +803,28 @@ cudaError_t forward_graph(morlet_plan_s* p, const void* x, void* W) {
   cudaGraph_t g = nullptr;
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    const long long ce = p->fwd.chain_end.empty() ? 0 : p->fwd.chain_end[0];
-    cudaError_t e2 = enqueue(p, p->fwd, x, W, 0, p->fwd.n_work, ce, p->d_ticket, true, cs);
+    cudaError_t e2 = backward ? backward_enqueue(p, in, out, cs) : forward_enqueue(p, in, out, cs);
     e = cudaStreamEndCapture(cs, &g);
     if (e2 != cudaSuccess) e = e2;
   }
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&p->gexec, g, 0);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&gx, g, 0);
   if (g) cudaGraphDestroy(g);
   cudaStreamDestroy(cs);
   if (e != cudaSuccess) return e;
-  p->g_x = x;
-  p->g_out = W;
+  gin = in;
+  gout = out;
   return cudaSuccess;
 }
+
+cudaError_t forward_graph(morlet_plan_s* p, const void* x, void* W) { return capture_graph(p, false, x, W); }
 
 // Look-back status arrays for n slots (flags, aggregates, inclusive values), replacing the old ones.
 int alloc_slots(morlet_plan_s* p, long long n) {
   int rc = MORLET_OK;
+  if (p->gexec_b) {  // a captured backward refers to the old arrays
+    cudaGraphExecDestroy(p->gexec_b);
+    p->gexec_b = nullptr;
+  }
   cudaFree(p->d_flags);
   cudaFree(p->d_agg);
   cudaFree(p->d_incl);
@@ -765,12 +855,6 @@ int build_forward(morlet_plan_s* p, long long& slots) {
   cudaDeviceSynchronize();
   free_launch(p->fwd);
   p->fwd = Launch{};
-  cudaFree(p->d_pflags);
-  cudaFree(p->d_pagg);
-  cudaFree(p->d_pincl);
-  cudaFree(p->d_pbuf);
-  p->d_pflags = nullptr;
-  p->d_pagg = p->d_pincl = p->d_pbuf = nullptr;
   slots = 0;
   rc = setup_launch(p, false, p->fwd, slots);
   if (rc) return rc;
@@ -778,7 +862,7 @@ int build_forward(morlet_plan_s* p, long long& slots) {
     rc = alloc_slots(p, slots);
     if (rc) return rc;
   }
-  if (p->fwd.n_pwork > 0) return alloc_prefix(p);
+  if (p->fwd.n_pwork > 0) return alloc_prefix(p, p->fwd);
   return MORLET_OK;
 }
 
@@ -854,7 +938,7 @@ int autotune(morlet_plan_s* p, cudaStream_t st) {
   sd.n_signals = (int64_t)sub.size();
   sd.lengths = sub.data();
   sd.sigmas = p->sigmas.data();
-  sd.flags &= ~MORLET_FLAG_AUTOTUNE;
+  sd.flags = (sd.flags & ~MORLET_FLAG_AUTOTUNE) | MORLET_FLAG_NO_ADJOINT;
   morlet_plan_t q = nullptr;
   int rc = morlet_plan(&q, &sd, st);
   if (rc == MORLET_ERR_NOMEM) {
@@ -1041,10 +1125,11 @@ void morlet_plan_destroy(morlet_plan_t p) {
   cudaFree(p->d_agg);
   cudaFree(p->d_incl);
   cudaFree(p->d_ticket);
-  cudaFree(p->d_pflags);
-  cudaFree(p->d_pagg);
-  cudaFree(p->d_pincl);
-  cudaFree(p->d_pbuf);
+  if (p->gexec_b) cudaGraphExecDestroy(p->gexec_b);
+  cudaFree(p->d_tabs_adj);
+  cudaFree(p->d_gplanes);
+  cudaFree(p->d_wplanes);
+  cudaFree(p->d_sig_desc);
   if (p->h_err) cudaFreeHost(p->h_err);
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
@@ -1085,6 +1170,7 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
   int rc = MORLET_OK;
   const int S = d->n_scales;
   const double wm = d->window_mult > 0 ? d->window_mult : 4.0;
+  bool has_adj = false;
   std::vector<FitJob> jobs(S);
   double* d_partial = nullptr;
   const int nblk = 64;
@@ -1178,6 +1264,46 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
     CK(cudaMemcpyAsync(p->h_tabs.data(), p->d_tabs, sizeof(ScaleTab) * S, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
 
+    // adjoint: rotating-form tables of every scale from the same fit (whatever the forward's form),
+    // each as two virtual scales, the real plane's (weights cM on Re V, 0) and the imaginary plane's
+    // (0, -cL on Im V): gx = sum_s Re W_s(Re gW_s) - Im W_s(Im gW_s)
+    has_adj = d->method == MORLET_DIRECT && d->transform == MORLET_SFT &&
+              !(d->flags & (MORLET_FLAG_EDGE | MORLET_FLAG_NO_ADJOINT));
+    if (has_adj) {
+      CK(cudaMalloc(&p->d_tabs_adj, sizeof(ScaleTab) * 2 * S));
+      CK(cudaMemcpyAsync(p->d_tabs_adj, p->d_tabs, sizeof(ScaleTab) * S, cudaMemcpyDeviceToDevice, st));
+      CK(run_tables(p->d_tabs_adj, p->d_jobs, S, p->K_kernel, ITEMS, 2, st));
+      std::vector<ScaleTab> rf(S);
+      CK(cudaMemcpyAsync(rf.data(), p->d_tabs_adj, sizeof(ScaleTab) * S, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      p->h_tabs_adj.resize(2 * S);
+      for (int s = 0; s < S; ++s) {
+        ScaleTab a = rf[s], b = rf[s];
+        for (int j = 0; j < KMAX; ++j) {
+          a.cL[j] = 0.0;
+          a.f_cL[j] = 0.f;
+          b.cM[j] = 0.0;
+          b.f_cM[j] = 0.f;
+          b.cL[j] = -rf[s].cL[j];
+          b.f_cL[j] = -rf[s].f_cL[j];
+        }
+        p->h_tabs_adj[2 * s] = a;
+        p->h_tabs_adj[2 * s + 1] = b;
+      }
+      CK(cudaMemcpyAsync(p->d_tabs_adj, p->h_tabs_adj.data(), sizeof(ScaleTab) * 2 * S, cudaMemcpyHostToDevice, st));
+      const size_t planes = p->elem * 2 * (size_t)S * (size_t)p->n_in;
+      CK(cudaMalloc(&p->d_gplanes, planes));
+      CK(cudaMalloc(&p->d_wplanes, planes));
+      std::vector<int64_t> sd(2 * p->lengths.size());
+      for (size_t i = 0; i < p->lengths.size(); ++i) {
+        sd[2 * i] = p->x_off[i];
+        sd[2 * i + 1] = p->lengths[i];
+      }
+      CK(cudaMalloc(&p->d_sig_desc, sizeof(int64_t) * sd.size()));
+      CK(cudaMemcpyAsync(p->d_sig_desc, sd.data(), sizeof(int64_t) * sd.size(), cudaMemcpyHostToDevice, st));
+      CK(cudaStreamSynchronize(st));
+    }
+
     // edge mode: pad every signal by the longest reach of any scale's window (L, plus the ASFT
     // shift n0) so that no stored output sees past the replicated samples
     if (d->flags & MORLET_FLAG_EDGE) {
@@ -1205,20 +1331,23 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
     long long slots = 0;
     rc = setup_launch(p, false, p->fwd, slots);
     if (rc) goto fail;
-    const bool has_adj = d->method == MORLET_DIRECT && d->transform == MORLET_SFT && !(d->flags & MORLET_FLAG_EDGE);
     long long slots_adj = 0;
     if (has_adj) {
       rc = setup_launch(p, true, p->adj, slots_adj);
       if (rc) goto fail;
     }
-    p->nt_slot = has_adj ? 2 * p->K_kernel : p->K_kernel;
+    p->nt_slot = p->K_kernel;
     rc = alloc_slots(p, std::max(slots, slots_adj));
     if (rc) goto fail;
     if (p->fwd.n_pwork > 0) {
-      rc = alloc_prefix(p);
+      rc = alloc_prefix(p, p->fwd);
       if (rc) goto fail;
     }
-    CK(cudaMalloc(&p->d_ticket, sizeof(unsigned long long) * TICKETS * (S + 1)));
+    if (p->adj.n_pwork > 0) {
+      rc = alloc_prefix(p, p->adj);
+      if (rc) goto fail;
+    }
+    CK(cudaMalloc(&p->d_ticket, sizeof(unsigned long long) * TICKETS * 2));
     CK(cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
@@ -1245,8 +1374,7 @@ int morlet_forward(morlet_plan_t p, const void* x, void* W, void* stream) {
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const bool use_graph = !(p->desc.flags & MORLET_FLAG_NO_GRAPH) && p->skip_tickets == 0;
-  if (!use_graph)
-    return cuda_status(enqueue(p, p->fwd, x, W, 0, p->fwd.n_work, p->fwd.chain_end[0], p->d_ticket, true, st));
+  if (!use_graph) return cuda_status(forward_enqueue(p, x, W, st));
   const cudaError_t e = forward_graph(p, x, W);
   if (e != cudaSuccess) return cuda_status(e);
   return cuda_status(cudaGraphLaunch(p->gexec, st));
@@ -1258,15 +1386,11 @@ int morlet_backward(morlet_plan_t p, const void* gW, void* gx, void* stream) {
   int rc = check_latched(p);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  // One launch per scale, in scale order: the first writes gx, the later ones add to it, so the
-  // sum over scales has a fixed order (deterministic, no float atomics).
-  const int S = (int)p->sigmas.size();
-  for (int s = 0; s < S; ++s) {
-    const cudaError_t e = enqueue(p, p->adj, gW, gx, p->adj.scale_begin[s], p->adj.scale_begin[s + 1],
-                                  p->adj.chain_end[s], p->d_ticket + TICKETS * (1 + s), s == 0, st, s > 0 ? 1 : 0);
-    if (e != cudaSuccess) return cuda_status(e);
-  }
-  return MORLET_OK;
+  const bool use_graph = !(p->desc.flags & MORLET_FLAG_NO_GRAPH) && p->skip_tickets == 0;
+  if (!use_graph) return cuda_status(backward_enqueue(p, gW, gx, st));
+  const cudaError_t e = capture_graph(p, true, gW, gx);
+  if (e != cudaSuccess) return cuda_status(e);
+  return cuda_status(cudaGraphLaunch(p->gexec_b, st));
 }
 
 int morlet_last_device_error(morlet_plan_t p, void* stream) {
@@ -1296,7 +1420,7 @@ int morlet_plan_stats(morlet_plan_t p, int64_t o[15]) {
   if (!p || !o) return MORLET_ERR_ARG;
   const Launch& f = p->fwd;
   const bool two = f.func_w != nullptr;
-  const long long c_end = two ? f.chain_end[0] : f.n_work;
+  const long long c_end = two ? f.chain_end : f.n_work;
   const long long s_beg = two ? std::min(std::max(f.ss_begin, c_end), f.n_work) : f.n_work;
   o[0] = THREADS;
   o[1] = ITEMS;
@@ -1322,6 +1446,10 @@ int morlet_plan_set_spin_limit(morlet_plan_t p, int64_t polls) {
   if (p->gexec) {
     cudaGraphExecDestroy(p->gexec);
     p->gexec = nullptr;
+  }
+  if (p->gexec_b) {
+    cudaGraphExecDestroy(p->gexec_b);
+    p->gexec_b = nullptr;
   }
   return MORLET_OK;
 }

@@ -46,9 +46,6 @@ enum Variant {
   V_RF_F32C_REAL,        // Gaussian smoothing
   V_RF_F32P_REAL,
   V_RF_F64_REAL,
-  V_RF_F32C_ADJ,         // adjoint
-  V_RF_F32P_ADJ,
-  V_RF_F64_ADJ,
   V_RF_F32P_ASFT_REAL,   // ASFT Gaussian smoothing, FP32
   V_RF_F32P_MULT,        // multiplication method, FP32
   V_COUNT

@@ -253,7 +253,7 @@ __device__ __forceinline__ void start_state(const KParams& P, const WorkItem& wi
     float lam[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-      wl[j] = __ldg(&tb->f_pw_lane[31 - lane][j]);
+      wl[j] = __ldg(&tb->f_pw_lane_t[j][31 - lane]);
       lam[j] = __ldg(&tb->f_lam[j]);
     }
     lane_sums<K, ITEMS>(xa, rho, lam, wl, b);
@@ -301,7 +301,7 @@ __device__ __forceinline__ void start_state_window(const KParams& P, const WorkI
       load_run_v8<ITEMS>(xs, a0 + (int64_t)lane * ITEMS, u0 > 0 ? u0 : 0, wi.n, xa, P.n_x - wi.x_off);
       float2 wl[K], b[K];
 #pragma unroll
-      for (int j = 0; j < K; ++j) wl[j] = __ldg(&tb->f_pw_lane[31 - lane][j]);
+      for (int j = 0; j < K; ++j) wl[j] = __ldg(&tb->f_pw_lane_t[j][31 - lane]);
       if constexpr (HORNER) {
         lane_sums_horner<K, ITEMS>(xa, rho, wl, b);
       } else {
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(THREADS, C::K <= 4 ? 4 : 2) tsum_kernel(const 
 #pragma unroll
     for (int j = 0; j < K; ++j) {
       rho[j] = tb->f_rho[j];
-      wl[j] = __ldg(&tb->f_pw_lane[31 - lane][j]);
+      wl[j] = __ldg(&tb->f_pw_lane_t[j][31 - lane]);
       lam[j] = __ldg(&tb->f_lam[j]);
     }
     const float* __restrict__ xs = reinterpret_cast<const float*>(P.x) + wi.x_off;
@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(THREADS, C::K <= 4 ? 3 : 2) psum_kernel(const 
 #pragma unroll
     for (int j = 0; j < K; ++j) {
       rho[j] = tb->f_rho[j];
-      wl[j] = __ldg(&tb->f_pw_lane[31 - lane][j]);  // rho^{16 (31 - lane)}
+      wl[j] = __ldg(&tb->f_pw_lane_t[j][31 - lane]);  // rho^{16 (31 - lane)}
       lam[j] = __ldg(&tb->f_lam[j]);
     }
     const float* __restrict__ xs = reinterpret_cast<const float*>(P.x) + wi.x_off;

@@ -41,9 +41,9 @@ namespace msft {
 
 enum { FORM_KI = 1, FORM_RF = 2 };
 // Output of a position: Morlet direct method W = sum_j cM_j Re V_j + i cL_j Im V_j (complex);
-// real (Gaussian smoothing: sum_j cM_j Re V_j + cL_j Im V_j); adjoint; or a complex combine
-// W = sum_j w_j V_j with w_j = cM_j + i cL_j (multiplication method, non-harmonic terms).
-enum { OUT_MORLET = 0, OUT_REAL = 1, OUT_ADJ = 2, OUT_CPLX = 3 };
+// real (Gaussian smoothing, and the adjoint's planes: sum_j cM_j Re V_j + cL_j Im V_j); or a complex
+// combine W = sum_j w_j V_j with w_j = cM_j + i cL_j (multiplication method, non-harmonic terms).
+enum { OUT_MORLET = 0, OUT_REAL = 1, OUT_CPLX = 3 };
 
 template <typename R_, typename CV_, int K_, int FORM_, int OUT_, bool ASFT_, int ITEMS_>
 struct Cfg {
@@ -55,7 +55,7 @@ struct Cfg {
   static constexpr int OUT = OUT_;
   static constexpr bool ASFT = ASFT_;
   static constexpr int ITEMS = ITEMS_;
-  static constexpr int CH = (OUT_ == OUT_ADJ) ? 2 : 1;
+  static constexpr int CH = 1;  // one real input channel
   static constexpr int NT = CH * K_;
   static constexpr int T = THREADS * ITEMS_;
   static constexpr int MINB = (sizeof(R_) == 4 && NT <= 4) ? 3 : (NT <= 8 ? 2 : 1);
@@ -239,9 +239,6 @@ __device__ __forceinline__ void store_item(const KParams& P, int64_t oo, int i, 
       }
     }
     if (all_in || in) __stcs(op + i, o);
-  } else if constexpr (C::OUT == OUT_ADJ) {
-    R* op = reinterpret_cast<R*>(P.out) + oo;
-    if (all_in || in) op[i] = P.accumulate ? op[i] + o.x : o.x;
   } else {
     R* op = reinterpret_cast<R*>(P.out) + oo;
     if (all_in || in) __stcs(op + i, o.x);
@@ -261,7 +258,7 @@ __global__ void __launch_bounds__(THREADS, C::MINB) scan_kernel(const KParams P)
   constexpr int K = C::K, NT = C::NT, CH = C::CH, ITEMS = C::ITEMS, T = C::T;
   constexpr bool ROT = (C::FORM == FORM_RF);
   // element type of one input sample (real, or complex for the adjoint's two channels)
-  using EIn = typename std::conditional<CH == 2, V, R>::type;
+  using EIn = R;
 
   __shared__ Smem<C> s;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -287,7 +284,7 @@ __global__ void __launch_bounds__(THREADS, C::MINB) scan_kernel(const KParams P)
       for (int i = tid; i < K; i += THREADS) {
         s.rho[i] = TabR<R>::rho(tb, i);
         s.cM[i] = TabR<R>::cM(tb, i);
-        s.cL[i] = (C::OUT == OUT_ADJ) ? -TabR<R>::cL(tb, i) : TabR<R>::cL(tb, i);
+        s.cL[i] = TabR<R>::cL(tb, i);
       }
       for (int i = tid; i < 5 * K; i += THREADS) s.pw_thr[i / K][i % K] = conv2<V>(tb->pw_thr[i / K][i % K]);
       for (int i = tid; i < 32 * K; i += THREADS) s.pw_lane[i / K][i % K] = conv2<V>(tb->pw_lane[i / K][i % K]);
@@ -370,14 +367,8 @@ __global__ void __launch_bounds__(THREADS, C::MINB) scan_kernel(const KParams P)
           for (int i = 0; i < ITEMS; ++i) {
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
-              R xv, xlv;
-              if constexpr (CH == 2) {
-                xv = c ? reinterpret_cast<const V&>(xa[i]).y : reinterpret_cast<const V&>(xa[i]).x;
-                xlv = c ? reinterpret_cast<const V&>(xl[i]).y : reinterpret_cast<const V&>(xl[i]).x;
-              } else {
-                xv = reinterpret_cast<const R&>(xa[i]);
-                xlv = reinterpret_cast<const R&>(xl[i]);
-              }
+              const R xv = reinterpret_cast<const R&>(xa[i]);
+              const R xlv = reinterpret_cast<const R&>(xl[i]);
 #pragma unroll
               for (int j = 0; j < K; ++j) {
                 V& b = B[c * K + j];
@@ -612,14 +603,8 @@ __global__ void __launch_bounds__(THREADS, C::MINB) scan_kernel(const KParams P)
         if constexpr (ROT) {
 #pragma unroll
           for (int c = 0; c < CH; ++c) {
-            R xv, xlv;
-            if constexpr (CH == 2) {
-              xv = c ? reinterpret_cast<const V&>(xa[i]).y : reinterpret_cast<const V&>(xa[i]).x;
-              xlv = c ? reinterpret_cast<const V&>(xl[i]).y : reinterpret_cast<const V&>(xl[i]).x;
-            } else {
-              xv = reinterpret_cast<const R&>(xa[i]);
-              xlv = reinterpret_cast<const R&>(xl[i]);
-            }
+            const R xv = reinterpret_cast<const R&>(xa[i]);
+            const R xlv = reinterpret_cast<const R&>(xl[i]);
 #pragma unroll
             for (int j = 0; j < K; ++j) {
               V& b = S[c * K + j];

@@ -297,7 +297,33 @@ __global__ void build_tables(ScaleTab* tabs, const FitJob* jobs, int n_scales, i
     sincospi((double)(tb.p0 + j) / (double)(2 * L), &sh, &ch);  // sin, cos of beta p / 2
     tb.d_lam[j] = j < K_kernel ? 4.0 * sh * sh : 0.0;
     tb.f_lam[j] = (float)tb.d_lam[j];
-    tb.f_shear[j] = j < K_kernel ? make_float2((float)(sh / ch), (float)(2.0 * sh * ch)) : make_float2(0.f, 0.f);
+    // Shears x += t y, y -= s x, x += t y: their product has trace 2 (1 - t s), so it turns by the
+    // angle theta' with cos theta' = 1 - t s whatever t and s are (and has determinant one). Rounding
+    // t = tan(theta / 2) and s = sin(theta) to FP32 on their own leaves theta' off by about u theta,
+    // a phase drift that grows with every step of a long serial recursion. So t is taken within 8
+    // ulps of tan(theta / 2) and s next to 2 sin^2(theta / 2) / t, the pair whose exact product
+    // (exact in FP64) is closest to 1 - cos(theta) = 2 sin^2(theta / 2): theta' is then right to a
+    // small fraction of an ulp, while the map stays within 8 ulps of the rotation.
+    float2 shear = make_float2(0.f, 0.f);
+    if (j < K_kernel && sh > 0.0) {
+      const double target = 2.0 * sh * sh;
+      const float t0 = (float)(sh / ch);
+      double best = -1.0;
+      for (int k = -8; k <= 8; ++k) {
+        const float t = __int_as_float(__float_as_int(t0) + k);
+        if (!(t > 0.f)) continue;
+        const float sc = (float)(target / (double)t);
+        for (int q = -1; q <= 1; ++q) {
+          const float sv = __int_as_float(__float_as_int(sc) + q);
+          const double e = fabs((double)t * (double)sv - target);
+          if (best < 0.0 || e < best) {
+            best = e;
+            shear = make_float2(t, sv);
+          }
+        }
+      }
+    }
+    tb.f_shear[j] = shear;
   }
   for (int idx = threadIdx.x; idx < K_kernel * 8; idx += blockDim.x) {
     const int j = idx % K_kernel, mm = idx / K_kernel;
@@ -318,7 +344,8 @@ __global__ void build_tables(ScaleTab* tabs, const FitJob* jobs, int n_scales, i
       tb.f_pw_thr[q][j] = make_float2((float)v.x, (float)v.y);
     } else if (q < 37) {
       const double2 v = tb.pw_lane[q - 5][j];
-      tb.f_pw_lane[q - 5][j] = make_float2((float)v.x, (float)v.y);
+      tb.f_pw_lane_t[j][q - 5] = make_float2((float)v.x, (float)v.y);
+      tb.pw_lane_t[j][q - 5] = v;
     } else {
       const double2 v = tb.pw_warp[j];
       const float hx = (float)v.x, hy = (float)v.y;

@@ -20,8 +20,8 @@ template <typename V> __device__ __forceinline__ V pw_thr(const ScaleTab* tb, in
 template <> __device__ __forceinline__ float2 pw_thr<float2>(const ScaleTab* tb, int l, int j) { return __ldg(&tb->f_pw_thr[l][j]); }
 template <> __device__ __forceinline__ double2 pw_thr<double2>(const ScaleTab* tb, int l, int j) { return tb->pw_thr[l][j]; }
 template <typename V> __device__ __forceinline__ V pw_lane(const ScaleTab* tb, int q, int j);
-template <> __device__ __forceinline__ float2 pw_lane<float2>(const ScaleTab* tb, int q, int j) { return __ldg(&tb->f_pw_lane[q][j]); }
-template <> __device__ __forceinline__ double2 pw_lane<double2>(const ScaleTab* tb, int q, int j) { return tb->pw_lane[q][j]; }
+template <> __device__ __forceinline__ float2 pw_lane<float2>(const ScaleTab* tb, int q, int j) { return __ldg(&tb->f_pw_lane_t[j][q]); }
+template <> __device__ __forceinline__ double2 pw_lane<double2>(const ScaleTab* tb, int q, int j) { return tb->pw_lane_t[j][q]; }
 // rho^{32 ITEMS} as hi (h = 0) + lo (h = 1); for FP64 the whole power in hi and zero in lo
 template <typename V> __device__ __forceinline__ V pwt(const ScaleTab* tb, int h, int j);
 template <> __device__ __forceinline__ float2 pwt<float2>(const ScaleTab* tb, int h, int j) { return __ldg(&tb->f_pwt[h][j]); }
@@ -118,17 +118,8 @@ __device__ __forceinline__ typename C::V step_g(typename C::V (&S)[C::NT], const
 template <class C, typename EIn>
 __device__ __forceinline__ void split_in(const EIn& a, const EIn& l, typename C::R (&xv)[C::CH],
                                          typename C::R (&xlv)[C::CH]) {
-  using R = typename C::R;
-  using V = typename C::V;
-  if constexpr (C::CH == 2) {
-    xv[0] = reinterpret_cast<const V&>(a).x;
-    xv[1] = reinterpret_cast<const V&>(a).y;
-    xlv[0] = reinterpret_cast<const V&>(l).x;
-    xlv[1] = reinterpret_cast<const V&>(l).y;
-  } else {
-    xv[0] = reinterpret_cast<const R&>(a);
-    xlv[0] = reinterpret_cast<const R&>(l);
-  }
+  xv[0] = a;
+  xlv[0] = l;
 }
 
 template <class C>
@@ -153,7 +144,7 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
   constexpr bool APC = APK && C::OUT == OUT_CPLX;
   constexpr bool V8 = PK || APK;  // 256-bit loads of the FP32 input runs
   constexpr int H = Pairs<K>::H;
-  using EIn = typename std::conditional<CH == 2, V, R>::type;
+  using EIn = R;
   const int lane = threadIdx.x & 31;
 
   // Work items are claimed two ahead, and the record of the next one is prefetched into L1 while the
@@ -188,7 +179,7 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
     for (int j = 0; j < K; ++j) {
       rho[j] = TabR<R>::rho(tb, j);
       cM[j] = TabR<R>::cM(tb, j);
-      cL[j] = (C::OUT == OUT_ADJ) ? -TabR<R>::cL(tb, j) : TabR<R>::cL(tb, j);
+      cL[j] = TabR<R>::cL(tb, j);
       cx += cM[j];
       if constexpr (GF) {  // conj(rho^{ITEMS (lane + 1)}) = rho^{-ITEMS (lane + 1)}
         const V q = cmul(pw_lane<V>(tb, lane, j), pw_thr<V>(tb, 0, j));

@@ -115,7 +115,7 @@ def test_asft_start_state_rows(K):
     rng = np.random.default_rng(700 + K)
     lens = [100000, 3, 50001, 262149, 1030, 77777]
     sigs = [rng.standard_normal(n).astype(np.float32) for n in lens]
-    sigmas = [20.0, 1500.0, 2000.0, 5000.0]
+    sigmas = [20.0, 800.0, 2000.0, 5000.0]  # L = 80, 3200 (window segments), 8000, 20000 (start states)
     plan, out = gpu_forward(sigs, sigmas, K=K, precision=m.MORLET_FP32_PLAIN, transform=m.MORLET_ASFT)
     st = m.morlet_plan_stats(plan)
     assert st["rows_start_state"] == 2 * len(lens) and st["rows_lookback"] == 0, st
@@ -137,11 +137,17 @@ def test_asft_start_state_rows(K):
     torch.cuda.synchronize()
     assert m.morlet_last_device_error(gplan) == 0
     yh = y.cpu().numpy()
+    # A row shorter than the window gives a derivative that nearly cancels (the kernel is odd): its
+    # error is measured against sum|kernel| max|x|, the scale of the arithmetic's rounding.
     off = 0
     for x, n in zip(sigs, lens):
         for s, sg in enumerate(sigmas):
-            ref = sft_dd.asft_gauss(x.astype(np.float64), om.fit_gauss_asft(sg, P, 1, om.default_n0(sg)))
-            e = rel_err(yh[S * off + s * n: S * off + (s + 1) * n], ref)
+            gf = om.fit_gauss_asft(sg, P, 1, om.default_n0(sg))
+            ref = sft_dd.asft_gauss(x.astype(np.float64), gf)
+            scale = np.abs(ref).max()
+            if n < 2 * gf["L"]:
+                scale = max(scale, np.abs(om.kernel_gauss_asft(gf)[1]).sum() * np.abs(x).max())
+            e = float(np.abs(yh[S * off + s * n: S * off + (s + 1) * n] - ref).max() / scale)
             assert e < 1e-4, (n, sg, e)
         off += n
 

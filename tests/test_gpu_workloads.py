@@ -189,6 +189,45 @@ def test_c4_adjoint_vs_direct_and_finite_differences():
     assert worst_fd < 1e-5
 
 
+@pytest.mark.parametrize("precision,form", [(m.MORLET_FP32_COMP, m.MORLET_FORM_ROTATING),
+                                            (m.MORLET_FP32_COMP, m.MORLET_FORM_KERNEL),
+                                            (m.MORLET_FP32_PLAIN, m.MORLET_FORM_ROTATING),
+                                            (m.MORLET_FP64, m.MORLET_FORM_ROTATING)])
+def test_backward_every_coordinate(precision, form):
+    """morlet_backward on a ragged batch (rows shorter than the window, rows of window segments and of
+    start-state items, every alignment) in each precision and form, against the oracle's adjoint
+    (sum over scales of the kernel-integral adjoint) at every coordinate; gate 1e-5 of max|gx|
+    (1e-12 in FP64, 1e-3 in plain FP32). Two calls with the same buffers replay one graph."""
+    import torch
+    rng = np.random.default_rng(31 + precision + 3 * form)
+    lens = [1, 70001, 4097, 300000, 999]
+    sigmas = [8.0, 100.0, 700.0, 3000.0, 9000.0]
+    S, n_in = len(sigmas), sum(lens)
+    f64 = precision == m.MORLET_FP64
+    plan = m.morlet_plan(lens, sigmas, K=4, precision=precision, form=form)
+    g = (rng.standard_normal(n_in * S) + 1j * rng.standard_normal(n_in * S))
+    gt = torch.from_numpy(g.astype(np.complex128 if f64 else np.complex64)).cuda()
+    gx = torch.full((n_in,), float("nan"), dtype=torch.float64 if f64 else torch.float32, device="cuda")
+    for _ in range(2):
+        m.morlet_backward(plan, gt, gx)
+    torch.cuda.synchronize()
+    assert m.morlet_last_device_error(plan) == 0
+    gxh = gx.cpu().numpy()
+    gh = gt.cpu().numpy().astype(np.complex128)
+    fits = [om.fit_direct(sg, 6.0, 4) for sg in sigmas]
+    tol = {m.MORLET_FP32_COMP: 1e-5, m.MORLET_FP32_PLAIN: 1e-3, m.MORLET_FP64: 1e-12}[precision]
+    off = 0
+    for n in lens:
+        ref = sum(sft_dd.adjoint_sft(gh[S * off + s * n: S * off + (s + 1) * n], fits[s]) for s in range(S))
+        e = rel_err(gxh[off:off + n], ref)
+        assert e < tol, (n, e)
+        off += n
+    with pytest.raises(m.MorletError) as err:
+        p2 = m.morlet_plan(lens, sigmas, K=4, precision=precision, flags=m.MORLET_FLAG_NO_ADJOINT)
+        m.morlet_backward(p2, gt, gx)
+    assert err.value.code == m.MORLET_ERR_UNSUPPORTED
+
+
 def test_autograd_function_matches_backward():
     import torch
     from paper_2110_11866_gb300.torch_ops import MorletFn, MorletTransform

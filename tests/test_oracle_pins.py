@@ -553,6 +553,34 @@ def test_multiply_sinusoid_closed_form():
     assert np.abs(W[inner] - ref[inner]).max() <= 5e-3 * np.abs(ref[inner]).max()
 
 
+# ---- The direct method's own error against the true Morlet, per K (reported, never gated) ----
+
+def test_sft_vs_true_morlet_table_reproduces_and_falls_with_K():
+    """tests/golden/sft_vs_true_morlet.json (written by make_sft_vs_true_morlet.py from the oracle
+    alone) reproduces, and has the expected shape: at L = 4 sigma the error falls as K grows, and for a
+    given K it hardly depends on sigma (the fit is the same function sampled more finely)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("mk", os.path.join(GOLD, "make_sft_vs_true_morlet.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    d = _gold("sft_vs_true_morlet.json")
+    rows = {(r["K"], r["sigma"]): r for r in d["rows"]}
+    import workloads as WL
+    x = WL.c1_fp64_single().signals[0]
+    for K, sg in ((4, 64.0), (6, 512.0)):
+        r = mk.row(K, sg, x if sg == 64.0 else None)
+        for key in ("kernel_rmse", "kernel_max", "transform_max"):
+            if key in rows[(K, sg)]:
+                assert abs(r[key] - rows[(K, sg)][key]) <= 1e-9 * rows[(K, sg)][key], (K, sg, key)
+    Ks = sorted({r["K"] for r in d["rows"]})
+    for sg in mk.SIGMAS:
+        errs = [rows[(K, sg)]["kernel_rmse"] for K in Ks]
+        assert all(a > b for a, b in zip(errs, errs[1:])), (sg, errs)
+    for K in Ks:
+        e = [rows[(K, sg)]["kernel_rmse"] for sg in mk.SIGMAS if sg >= 64.0]
+        assert max(e) <= 1.01 * min(e), (K, e)
+
+
 # ---- Approximation error of the Morlet wavelet (Sec. IV, Figs. MSE1 and MSE2) ----
 
 def _sweep():
