@@ -1,6 +1,7 @@
 // Shared device-side types and helpers of the SFT/ASFT Morlet library (sm_103a).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -141,6 +142,11 @@ struct KParams {
   void* pbuf;                // start-state rows: per 512-position tile, K two-float complex prefix
                              // sums (ss_window = 0) or K FP32 complex tile sums (ss_window = 1)
   int ss_window;             // start states from window sums of tile sums instead of prefix sums
+  int use_tma;               // warp scan, complex FP32 output: whole warp-tiles leave by TMA stores
+  // the output buffer as 2-D tensors of 128-byte rows (32 floats) starting at out + 16 m bytes,
+  // m = 0..7, so that a warp-tile starting on any 16-byte boundary is a box of 32 whole rows of one
+  // of them (128-byte swizzle)
+  CUtensorMap omap[8];
 };
 
 // ------------------------------------------------------------------------------------------------

@@ -10,6 +10,8 @@
 #include <tuple>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "../../include/morlet_sft.h"
 #include "plan_internal.h"
 #include "work_plan.h"
@@ -594,6 +596,44 @@ cudaError_t pad_edges(const morlet_plan_s* p, const void* x, cudaStream_t st) {
 // and join the second stream back into `st`. tickets[0..4] count the look-back, window, start-state,
 // prefix-sum and lane-chunk kernels. `x` is the buffer the rows read (the forward's input, its padded
 // copy in edge mode, or the adjoint's planes), `out` the buffer they write.
+// The driver's tensor-map encoder, looked up once (the runtime links no driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    else
+      (void)cudaGetLastError();
+  });
+  return fn;
+}
+
+// Tensor maps of an output buffer of `bytes` bytes for the warp scan's TMA stores: map m views the
+// buffer from out + 16 m as rows of 32 floats (128 bytes), with boxes of 32 rows and the 128-byte
+// swizzle. False (plain stores) when the buffer is not 16-byte aligned, too small to hold a
+// warp-tile, too long for 32-bit row coordinates, or the encoder is unavailable.
+bool encode_out_maps(KParams& kp, void* out, size_t bytes) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || (reinterpret_cast<uintptr_t>(out) & 15) != 0 || bytes < 4096 + 128) return false;
+  for (int m = 0; m < 8; ++m) {
+    const cuuint64_t rows = (cuuint64_t)((bytes - 16 * (size_t)m) / 128);
+    if (rows >= (1ull << 31)) return false;
+    const cuuint64_t dims[2] = {32, rows};
+    const cuuint64_t strides[1] = {128};
+    const cuuint32_t box[2] = {32, 32};
+    const cuuint32_t es[2] = {1, 1};
+    if (enc(&kp.omap[m], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, static_cast<char*>(out) + 16 * m, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
+}
+
 cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out, unsigned long long* tickets,
                     cudaStream_t st) {
   const long long w_end = ln.n_work;
@@ -626,6 +666,9 @@ cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out
   kp.spin_limit = p->spin;
   kp.n_x = ln.n_x;
   kp.pbuf = ln.d_pbuf;
+  // complex FP32 forward output: whole warp-tiles leave the warp scan by TMA tensor stores
+  if (&ln == &p->fwd && p->elem == 4 && p->desc.method != MORLET_GAUSS && ln.func_w != nullptr)
+    kp.use_tma = encode_out_maps(kp, out, sizeof(float2) * p->sigmas.size() * (size_t)p->n_in) ? 1 : 0;
   bool forked = false;
   const bool lane_items = ln.n_lwork > 0;
   if ((two && s_beg > c_end) || lane_items) {

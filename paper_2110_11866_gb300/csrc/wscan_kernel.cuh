@@ -123,7 +123,7 @@ __device__ __forceinline__ void split_in(const EIn& a, const EIn& l, typename C:
 }
 
 template <class C>
-__global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P) {
+__global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const __grid_constant__ KParams P) {
   using R = typename C::R;
   using V = typename C::V;
   constexpr int K = C::K, NT = C::NT, CH = C::CH, ITEMS = C::ITEMS;
@@ -157,6 +157,7 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
   }
   w = __shfl_sync(0xffffffffu, w, 0);
   w1 = __shfl_sync(0xffffffffu, w1, 0);
+  bool tma_pending = false;  // a TMA store of this warp's staging tile may still be reading it
   while (w < P.n_work) {
     const WorkItem wi = P.work[w];
     long long w2 = 0;
@@ -472,50 +473,66 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
       const int64_t tw = wi.t_a + (int64_t)k * WT;  // first position of the warp-tile
       if (tw >= t_end || tw + WT <= t_out) continue;  // no output in this warp-tile (warp-uniform)
       if constexpr (STAGE) {
-        {
-          V* obd = reinterpret_cast<V*>(P.out) + (wi.out_off - D + tw);
-          if (tw >= t_out && tw + WT <= t_end && (reinterpret_cast<uintptr_t>(obd) & 31) == 0) {
-            // every output of the tile, 32-byte aligned: each lane writes its 128 bytes as four
-            // whole-sector 256-bit stores
-            float* op = reinterpret_cast<float*>(obd + lane * ITEMS);
+        V* ob = reinterpret_cast<V*>(P.out) + (wi.out_off - D + tw);
+        const bool full = tw >= t_out && tw + WT <= t_end;
+        if (!P.use_tma && full && (reinterpret_cast<uintptr_t>(ob) & 31) == 0) {
+          // every output of the tile, 32-byte aligned, no tensor maps: each lane writes its 128
+          // bytes as four whole-sector 256-bit stores
+          float* op = reinterpret_cast<float*>(ob + lane * ITEMS);
 #pragma unroll
-            for (int i = 0; i < ITEMS; i += 4) {
-              const V o0 = one(i), o1 = one(i + 1), o2 = one(i + 2), o3 = one(i + 3);
-              asm volatile("st.global.cs.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(op + 2 * i),
-                           "f"(o0.x), "f"(o0.y), "f"(o1.x), "f"(o1.y), "f"(o2.x), "f"(o2.y), "f"(o3.x), "f"(o3.y)
-                           : "memory");
-            }
-            continue;
+          for (int i = 0; i < ITEMS; i += 4) {
+            const V o0 = one(i), o1 = one(i + 1), o2 = one(i + 2), o3 = one(i + 3);
+            asm volatile("st.global.cs.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(op + 2 * i),
+                         "f"(o0.x), "f"(o0.y), "f"(o1.x), "f"(o1.y), "f"(o2.x), "f"(o2.y), "f"(o3.x), "f"(o3.y)
+                         : "memory");
           }
+          continue;
         }
-        // Otherwise the warp-tile's 512 outputs go through this warp's shared rows (one padded
-        // 144-byte row per lane, conflict-free both ways) so that every store instruction writes
-        // 512 (or 256) contiguous bytes instead of 32 scattered half-sectors; positions outside
-        // [t_out, t_end) are masked.
-        __shared__ float4 s_out[WARPS * 32 * 9];
-        float4* rows = s_out + (threadIdx.x >> 5) * (32 * 9);
+        // The warp's 512 outputs are staged in its 4 KB tile of shared memory: lane l's 128 bytes
+        // form row l, and its 16-byte chunk c sits at chunk position c ^ (l & 7) (the TMA unit's
+        // 128-byte swizzle), so that the 8 lanes of each quarter-warp writing chunk c cover all 32
+        // banks. A whole tile on a 16-byte boundary then leaves as one TMA tensor store of 32 rows;
+        // other tiles are stored from the staged rows, masked to [t_out, t_end).
+        __shared__ __align__(1024) float4 s_tile[WARPS * 256];
+        float4* rows = s_tile + (threadIdx.x >> 5) * 256;
+        if (tma_pending) {  // the previous tile's store must have read the staging tile
+          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+          __syncwarp();
+          tma_pending = false;
+        }
 #pragma unroll
         for (int i = 0; i < ITEMS; i += 2) {
           const V o0 = one(i);
           const V o1 = one(i + 1);
-          rows[lane * 9 + i / 2] = make_float4(o0.x, o0.y, o1.x, o1.y);
+          rows[lane * 8 + ((i / 2) ^ (lane & 7))] = make_float4(o0.x, o0.y, o1.x, o1.y);
+        }
+        const uint64_t ofs = (uint64_t)(wi.out_off - D + tw) * sizeof(V);  // bytes from the output base
+        const uint32_t sa = (uint32_t)__cvta_generic_to_shared(rows);
+        // (the swizzle pattern is that of 1024-byte aligned shared addresses)
+        if (P.use_tma && full && (ofs & 15) == 0 && (sa & 1023) == 0) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) {
+            const int m = (int)((ofs >> 4) & 7);
+            const int y = (int)((ofs - 16 * (uint64_t)m) >> 7);
+            asm volatile(
+                "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                    reinterpret_cast<uint64_t>(&P.omap[m])),
+                "r"(0), "r"(y), "r"(sa)
+                : "memory");
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          }
+          tma_pending = true;
+          continue;
         }
         __syncwarp();
-        V* ob = reinterpret_cast<V*>(P.out) + (wi.out_off - D + tw);
-        const int lo_o = (int)(t_out > tw ? t_out - tw : 0);         // stored outputs [lo_o, hi_o)
+        const int lo_o = (int)(t_out > tw ? t_out - tw : 0);  // stored outputs [lo_o, hi_o)
         const int hi_o = (int)(t_end < tw + WT ? t_end - tw : WT);
-        const bool aligned = (reinterpret_cast<uintptr_t>(ob) & 15) == 0;
-        if (aligned && lo_o == 0 && hi_o == WT) {  // the common case: every output of the tile
+        if ((reinterpret_cast<uintptr_t>(ob) & 15) == 0) {
 #pragma unroll
           for (int r = 0; r < 8; ++r) {
-            const int c = 32 * r + lane;
-            __stcs(reinterpret_cast<float4*>(ob) + c, rows[(c >> 3) * 9 + (c & 7)]);
-          }
-        } else if (aligned) {
-#pragma unroll
-          for (int r = 0; r < 8; ++r) {
-            const int c = 32 * r + lane;  // 16-byte chunk: outputs 2c, 2c + 1
-            const float4 v = rows[(c >> 3) * 9 + (c & 7)];
+            const int c = 32 * r + lane;  // 16-byte chunk of the tile: outputs 2c, 2c + 1
+            const float4 v = rows[(c >> 3) * 8 + ((c & 7) ^ ((c >> 3) & 7))];
             const bool in0 = 2 * c >= lo_o && 2 * c < hi_o, in1 = 2 * c + 1 >= lo_o && 2 * c + 1 < hi_o;
             if (in0 && in1) __stcs(reinterpret_cast<float4*>(ob) + c, v);
             else if (in0) __stcs(ob + 2 * c, make_float2(v.x, v.y));
@@ -525,7 +542,9 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
 #pragma unroll
           for (int r = 0; r < 16; ++r) {
             const int o = 32 * r + lane;
-            if (o >= lo_o && o < hi_o) __stcs(ob + o, reinterpret_cast<const float2*>(rows + (o >> 4) * 9)[o & 15]);
+            const int row = o >> 4;
+            if (o >= lo_o && o < hi_o)
+              __stcs(ob + o, reinterpret_cast<const float2*>(rows + row * 8 + (((o & 15) >> 1) ^ (row & 7)))[o & 1]);
           }
         }
         __syncwarp();
@@ -592,6 +611,8 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const KParams P
     w = w1;
     w1 = __shfl_sync(0xffffffffu, w2, 0);
   }
+  // the warp's TMA stores complete before it exits (its staging tile is freed with the CTA)
+  if (tma_pending && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 }  // namespace msft
