@@ -122,6 +122,24 @@ __device__ __forceinline__ void split_in(const EIn& a, const EIn& l, typename C:
   xlv[0] = l;
 }
 
+// One warp-tile of complex FP32 outputs (32 staged rows of 128 bytes at shared address sa, in the
+// 128-byte swizzle) to the output bytes [ofs, ofs + 4096), ofs a multiple of 16, by one TMA tensor
+// store of the map whose rows start at that offset modulo 128. The lanes' generic-proxy writes of
+// the rows are made visible to the async proxy first; lane 0 issues and commits the store.
+__device__ __forceinline__ void tma_store_tile(const KParams& P, uint64_t ofs, uint32_t sa, int lane) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncwarp();
+  if (lane == 0) {
+    const int m = (int)((ofs >> 4) & 7);
+    const int y = (int)((ofs - 16 * (uint64_t)m) >> 7);
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(&P.omap[m])),
+                 "r"(0), "r"(y), "r"(sa)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  }
+}
+
 template <class C>
 __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const __grid_constant__ KParams P) {
   using R = typename C::R;
@@ -158,6 +176,7 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const __grid_co
   w = __shfl_sync(0xffffffffu, w, 0);
   w1 = __shfl_sync(0xffffffffu, w1, 0);
   bool tma_pending = false;  // a TMA store of this warp's staging tile may still be reading it
+  V carry{};                 // odd tiles: the last output of the warp's previous tile
   while (w < P.n_work) {
     const WorkItem wi = P.work[w];
     long long w2 = 0;
@@ -500,28 +519,41 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const __grid_co
           __syncwarp();
           tma_pending = false;
         }
+        const uint64_t ofs = (uint64_t)(wi.out_off - D + tw) * sizeof(V);  // bytes from the output base
+        const uint32_t sa = (uint32_t)__cvta_generic_to_shared(rows);
+        // (the swizzle pattern is that of 1024-byte aligned shared addresses)
+        const bool tma = P.use_tma && full && (sa & 1023) == 0;
+        const bool odd = (ofs & 15) == 8;  // the tile starts on an 8-byte boundary only
+        if (tma && odd && tw > t_out && k > 0) {
+          // Odd tile: the box starts one output earlier, at the previous warp-tile's last output
+          // (computed by this warp and carried; written before, rewritten with the same value), so
+          // row l holds outputs 16 l - 1 .. 16 l + 14; the tile's last output, outside the box,
+          // is stored by lane 31 itself.
+          const V f = one(0);
+#pragma unroll
+          for (int c = 1; c < ITEMS / 2; ++c) {
+            const V a = one(2 * c - 1);
+            const V b = one(2 * c);
+            rows[lane * 8 + (c ^ (lane & 7))] = make_float4(a.x, a.y, b.x, b.y);
+          }
+          const V l = one(ITEMS - 1);
+          V pv = cmake<R>(__shfl_up_sync(0xffffffffu, l.x, 1), __shfl_up_sync(0xffffffffu, l.y, 1));
+          if (lane == 0) pv = carry;
+          rows[lane * 8 + (lane & 7)] = make_float4(pv.x, pv.y, f.x, f.y);
+          carry = cmake<R>(__shfl_sync(0xffffffffu, l.x, 31), __shfl_sync(0xffffffffu, l.y, 31));
+          if (lane == 31) __stcs(ob + (WT - 1), l);
+          tma_store_tile(P, ofs - 8, sa, lane);
+          tma_pending = true;
+          continue;
+        }
 #pragma unroll
         for (int i = 0; i < ITEMS; i += 2) {
           const V o0 = one(i);
           const V o1 = one(i + 1);
           rows[lane * 8 + ((i / 2) ^ (lane & 7))] = make_float4(o0.x, o0.y, o1.x, o1.y);
         }
-        const uint64_t ofs = (uint64_t)(wi.out_off - D + tw) * sizeof(V);  // bytes from the output base
-        const uint32_t sa = (uint32_t)__cvta_generic_to_shared(rows);
-        // (the swizzle pattern is that of 1024-byte aligned shared addresses)
-        if (P.use_tma && full && (ofs & 15) == 0 && (sa & 1023) == 0) {
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          __syncwarp();
-          if (lane == 0) {
-            const int m = (int)((ofs >> 4) & 7);
-            const int y = (int)((ofs - 16 * (uint64_t)m) >> 7);
-            asm volatile(
-                "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
-                    reinterpret_cast<uint64_t>(&P.omap[m])),
-                "r"(0), "r"(y), "r"(sa)
-                : "memory");
-            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-          }
+        if (tma && !odd) {
+          tma_store_tile(P, ofs, sa, lane);
           tma_pending = true;
           continue;
         }
@@ -546,6 +578,9 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const __grid_co
             if (o >= lo_o && o < hi_o)
               __stcs(ob + o, reinterpret_cast<const float2*>(rows + row * 8 + (((o & 15) >> 1) ^ (row & 7)))[o & 1]);
           }
+          // the tile's last output (row 31, chunk 7 at position 7 ^ 7 = 0) for the next, shifted box
+          const float4 e = rows[31 * 8];
+          carry = cmake<R>(e.z, e.w);
         }
         __syncwarp();
       } else if constexpr (STAGE_R) {
