@@ -147,6 +147,12 @@ struct KParams {
   // m = 0..7, so that a warp-tile starting on any 16-byte boundary is a box of 32 whole rows of one
   // of them (128-byte swizzle)
   CUtensorMap omap[8];
+  // lane-chunk scan: the output buffer viewed as rows of one lane chunk each (lmap_c[q] positions,
+  // 8 lmap_c[q] bytes; lmap_rows[q] whole rows), boxes of 32 floats x 32 rows, 128-byte swizzle,
+  // for up to four chunk lengths (lmap_c[q] = 0: no map)
+  CUtensorMap lmap[4];
+  int64_t lmap_rows[4];
+  int32_t lmap_c[4];
 };
 
 // ------------------------------------------------------------------------------------------------

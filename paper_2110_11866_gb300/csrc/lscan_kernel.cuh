@@ -16,16 +16,20 @@
 // shared buffers, transposed:
 //  - inputs: per step of 16 positions the warp copies the 32 lanes' runs of x[t] and x[t - 2L] into
 //    shared memory as 16-byte pieces (5 per run, covering a misalignment of up to 3 samples;
-//    consecutive lanes take consecutive pieces) with cp.async, one step ahead into the other of two
-//    buffers, so the copy of step k + 1 overlaps the arithmetic of step k; each lane reads its run
-//    back from a padded 80-byte row and shifts it by the run's misalignment, which is the same for
-//    every lane and step;
-//  - outputs: a lane's 16 complex outputs of a step are 128 contiguous bytes. When every lane's
-//    outputs of the step are in range and 32-byte aligned (the plan starts every row's chunks on an
-//    output element that is a multiple of 4), each lane writes them as four 256-bit stores of whole
-//    sectors. Otherwise (the steps that touch the ends of the row, or a misaligned output buffer)
-//    each lane writes them into a padded 144-byte row (over the input buffer it has just read) and
-//    the warp stores them as masked 16-byte pieces, eight lanes per row.
+//    consecutive lanes take consecutive pieces) with cp.async into the step's buffer (two buffers,
+//    alternating). The copies of step k + 1 are issued as soon as step k's runs are in registers,
+//    so they overlap step k's arithmetic; each lane reads its run back from a padded 80-byte row
+//    and shifts it by the run's misalignment, which is the same for every lane and step;
+//  - outputs: a lane's 16 complex outputs of a step are 128 contiguous bytes, and the 32 lanes'
+//    pieces lie one chunk (8 C bytes) apart. When every lane's outputs of the step are in range,
+//    the lanes write them as the 32 rows of a 4 KB tile in the buffer just read (128-byte
+//    swizzle), which leaves as one TMA tensor store through a map of the output buffer viewed as
+//    rows of one chunk (one map per chunk length, up to four). The copies of step k + 2 into the
+//    same buffer wait until the store has read it. Without a map, such steps use four 256-bit stores
+//    of whole sectors per lane (the plan starts every row's chunks on an output element that is a
+//    multiple of 4). Other steps (those that touch the ends of the row, or a misaligned output
+//    buffer) go through a padded 144-byte row per lane and are stored as masked 16-byte pieces,
+//    eight lanes per row.
 // Every bank access is conflict-free (row strides of 20 and 36 words).
 //
 // Work item fields (see WorkItem): t_a = first position of lane 0's chunk, n_sub = C (multiple of
@@ -68,7 +72,6 @@ __device__ __forceinline__ void ls_cp16(float4* dst, const float* src, int bytes
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void ls_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void ls_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void ls_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Piece of samples [e, e + 4) of the n-sample buffer x into dst: asynchronous when inside the
@@ -91,12 +94,13 @@ __device__ __forceinline__ int64_t ls_floordiv(int64_t a, int64_t b) { return a 
 __device__ __forceinline__ int ls_clamp(int64_t v, int hi) { return (int)(v < 0 ? 0 : (v > hi ? hi : v)); }
 
 template <class C>
-__global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel(const KParams P) {
+__global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel(const __grid_constant__ KParams P) {
   static_assert(std::is_same<typename C::R, float>::value && C::CH == 1 && C::OUT == OUT_MORLET && !C::ASFT,
                 "the lane-chunk scan is built for the FP32 SFT Morlet transform");
   constexpr int K = C::K;
   const int lane = threadIdx.x & 31;
-  __shared__ __align__(16) float4 s_buf[LS_WARPS][2][LS_BUF_F4];
+  // (1024-byte aligned buffers: a consumed input buffer doubles as a TMA staging tile)
+  __shared__ __align__(1024) float4 s_buf[LS_WARPS][2][LS_BUF_F4];
   float4 (*const bufs)[LS_BUF_F4] = s_buf[threadIdx.x >> 5];
   const float* __restrict__ xg = reinterpret_cast<const float*>(P.x);
   const int64_t b0 = (int64_t)(reinterpret_cast<uintptr_t>(xg) >> 2);
@@ -104,6 +108,7 @@ __global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel
   long long w = 0;
   if (lane == 0) w = (long long)atomicAdd(P.ticket, 1ull);
   w = __shfl_sync(0xffffffffu, w, 0);
+  bool tma_pending = false;  // a TMA store may still be reading the buffer of the previous step
   while (w < P.n_work) {
     const WorkItem wi = P.work[w];
     long long w2 = 0;  // items are independent: claim the next one now
@@ -162,6 +167,20 @@ __global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel
     const bool o16 = ((reinterpret_cast<uintptr_t>(orow + wi.t_a) & 15) == 0);
     const bool o32 = ((reinterpret_cast<uintptr_t>(orow + wi.t_a) & 31) == 0);
     const int so = (lane >> 3) * Cc + 2 * (lane & 7);  // this lane's store piece in round 0
+    // TMA stores when the item's chunk length has a tensor map: (ys, rs) = view row and byte offset
+    // in it of lane 0's outputs at the current output step; chunk c of the step lies c rows below
+    int q = -1;
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq)
+      if (P.lmap_c[qq] == Cc) q = qq;
+    const int CB = 8 * Cc;
+    int ys = 0, rs = 0;  // (view rows are below 2^31)
+    if (q >= 0) {
+      const int64_t A0 = 8LL * (wi.out_off - tb->D + wi.t_a);
+      const int64_t y0 = ls_floordiv(A0, CB);
+      ys = (int)y0;
+      rs = (int)(A0 - y0 * CB);
+    }
 
     // copies of step k into buffer k & 1
     auto issue = [&](int k) {
@@ -191,14 +210,16 @@ __global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel
 #pragma unroll
     for (int j = 0; j < K; ++j) S[j] = make_float2(0.f, 0.f);
 
+    // Buffer k & 1 takes the copies of step k; they are issued once step k - 1's inputs are in
+    // registers, after the TMA store staged in that buffer two steps earlier has read it.
+    if (tma_pending) {
+      if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      __syncwarp();
+      tma_pending = false;
+    }
     issue(0);
     for (int k = 0; k < n_steps; ++k) {
-      if (k + 1 < n_steps) {
-        issue(k + 1);
-        ls_wait_prev();
-      } else {
-        ls_wait_all();
-      }
+      ls_wait_all();
       __syncwarp();
       float4* bl = bufs[k & 1];
       const int step0 = a0 + k * LS_ITEMS;  // lane 0's first position of this step
@@ -216,6 +237,14 @@ __global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel
         }
       }
       __syncwarp();
+      if (k + 1 < n_steps) {
+        if (tma_pending) {
+          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+          __syncwarp();
+          tma_pending = false;
+        }
+        issue(k + 1);
+      }
       if (k < kl_a || k >= kh_a || (!pro_step && (k < kl_g || k >= kh_g))) {  // warp-uniform
         const int p = step0 + lane * Cc;
 #pragma unroll
@@ -251,7 +280,36 @@ __global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel
         }
         return make_float2(fmaf(cx, xl[i], ox), oy);
       };
-      if (o32 && step0 >= t_out && step0 + 31 * Cc + LS_ITEMS <= t_end) {  // warp-uniform
+      const bool full = step0 >= t_out && step0 + 31 * Cc + LS_ITEMS <= t_end;  // warp-uniform
+      const int ys_k = ys, rs_k = rs;
+      if (q >= 0) {  // the next output step's position in the view
+        rs += 128;
+        if (rs >= CB) {
+          rs -= CB;
+          ++ys;
+        }
+      }
+      if (q >= 0 && full && rs_k + 128 <= CB && ys_k >= 0 && ys_k + 32 <= P.lmap_rows[q]) {
+        // every lane's 16 outputs are in range and in one view row: the lanes' 128-byte rows are
+        // staged in the buffer just read (128-byte swizzle) and leave as one TMA tensor store
+#pragma unroll
+        for (int i = 0; i < LS_ITEMS; i += 2) {
+          const float2 o0 = one(i), o1 = one(i + 1);
+          bl[lane * 8 + ((i / 2) ^ (lane & 7))] = make_float4(o0.x, o0.y, o1.x, o1.y);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                           reinterpret_cast<uint64_t>(&P.lmap[q])),
+                       "r"(rs_k >> 2), "r"(ys_k), "r"((uint32_t)__cvta_generic_to_shared(bl))
+                       : "memory");
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
+        tma_pending = true;
+        continue;
+      }
+      if (o32 && full) {
         // every lane's 16 outputs are in range: four 32-byte stores of whole sectors per lane
         float2* op = orow + (step0 + lane * Cc);
 #pragma unroll
@@ -296,6 +354,8 @@ __global__ void __launch_bounds__(LS_WARPS * 32, C::K <= 4 ? 4 : 2) lscan_kernel
     }
     w = __shfl_sync(0xffffffffu, w2, 0);
   }
+  // the warp's TMA stores complete before it exits (its buffers are freed with the CTA)
+  if (tma_pending && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 }  // namespace msft

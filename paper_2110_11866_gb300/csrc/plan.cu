@@ -116,6 +116,7 @@ struct Launch {
   long long n_lwork = 0;
   int grid_l = 0;
   long long rows_lane = 0;
+  int32_t l_chunks[4] = {0, 0, 0, 0};  // the most frequent chunk lengths of the items (TMA maps)
 };
 
 }  // namespace
@@ -516,6 +517,15 @@ int setup_launch(morlet_plan_s* p, bool adjoint, Launch& ln, long long& slots) {
     if (occl < 1) occl = 1;
     ln.grid_l = occl * p->sms;
     ln.n_lwork = (long long)lwork.size();
+    {
+      std::map<int32_t, long long> cnt;
+      for (const auto& it : lwork) cnt[it.n_sub]++;
+      std::vector<std::pair<long long, int32_t>> by(cnt.size());
+      size_t u = 0;
+      for (const auto& c : cnt) by[u++] = {c.second, c.first};
+      std::sort(by.begin(), by.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+      for (size_t q = 0; q < 4 && q < by.size(); ++q) ln.l_chunks[q] = by[q].second;
+    }
     CK(cudaMalloc(&ln.d_lwork, sizeof(WorkItem) * lwork.size()));
     CK(cudaMemcpy(ln.d_lwork, lwork.data(), sizeof(WorkItem) * lwork.size(), cudaMemcpyHostToDevice));
   }
@@ -634,6 +644,31 @@ bool encode_out_maps(KParams& kp, void* out, size_t bytes) {
   return true;
 }
 
+// Tensor maps of the output for the lane-chunk scan's TMA stores: for each chunk length C of
+// `chunks` (0: none), the buffer viewed as rows of C complex outputs (8 C bytes), boxes of 32 floats
+// (16 outputs) x 32 rows (the 32 lane chunks of an item), 128-byte swizzle. A length whose view has
+// fewer than 32 rows, or that fails to encode, gets none (plain stores).
+void encode_chunk_maps(KParams& kp, void* out, size_t bytes, const int32_t (&chunks)[4]) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  for (int q = 0; q < 4; ++q) {
+    kp.lmap_c[q] = 0;
+    kp.lmap_rows[q] = 0;
+    const int32_t c = chunks[q];
+    if (!enc || c < 16 || c % 16 != 0 || (reinterpret_cast<uintptr_t>(out) & 15) != 0) continue;
+    const cuuint64_t rows = (cuuint64_t)(bytes / (8 * (size_t)c));
+    if (rows < 32 || rows >= (1ull << 31)) continue;
+    const cuuint64_t dims[2] = {2 * (cuuint64_t)c, rows};
+    const cuuint64_t strides[1] = {8 * (cuuint64_t)c};
+    const cuuint32_t box[2] = {32, 32};
+    const cuuint32_t es[2] = {1, 1};
+    if (enc(&kp.lmap[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, out, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      continue;
+    kp.lmap_c[q] = c;
+    kp.lmap_rows[q] = (int64_t)rows;
+  }
+}
+
 cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out, unsigned long long* tickets,
                     cudaStream_t st) {
   const long long w_end = ln.n_work;
@@ -666,9 +701,13 @@ cudaError_t enqueue(morlet_plan_s* p, const Launch& ln, const void* x, void* out
   kp.spin_limit = p->spin;
   kp.n_x = ln.n_x;
   kp.pbuf = ln.d_pbuf;
-  // complex FP32 forward output: whole warp-tiles leave the warp scan by TMA tensor stores
-  if (&ln == &p->fwd && p->elem == 4 && p->desc.method != MORLET_GAUSS && ln.func_w != nullptr)
-    kp.use_tma = encode_out_maps(kp, out, sizeof(float2) * p->sigmas.size() * (size_t)p->n_in) ? 1 : 0;
+  // complex FP32 forward output: whole warp-tiles leave the warp scan, and whole steps the lane-chunk
+  // scan, by TMA tensor stores
+  if (&ln == &p->fwd && p->elem == 4 && p->desc.method != MORLET_GAUSS) {
+    const size_t bytes = sizeof(float2) * p->sigmas.size() * (size_t)p->n_in;
+    if (ln.func_w != nullptr) kp.use_tma = encode_out_maps(kp, out, bytes) ? 1 : 0;
+    if (ln.n_lwork > 0) encode_chunk_maps(kp, out, bytes, ln.l_chunks);
+  }
   bool forked = false;
   const bool lane_items = ln.n_lwork > 0;
   if ((two && s_beg > c_end) || lane_items) {

@@ -3,8 +3,9 @@
 // segment of a row and walks it alone, 32 lanes x ITEMS consecutive positions at a time:
 //   loads -> pass 1 (recursion from zero) -> warp-shuffle scan -> start state = rho^{ITEMS lane} C + exclusive
 //   -> pass 2 (outputs) -> carry C <- rho^{32 ITEMS} C + warp total.
-// There is no barrier and no shared memory on the data path, so a stalled warp never holds up the
-// others of its CTA. The segment starts from a zero state 2L samples before its first output
+// There is no CTA barrier: a warp's only shared memory is its own 4 KB output staging tile (whole
+// warp-tiles leave it by one TMA tensor store), so a stalled warp never holds up the others of its
+// CTA. The segment starts from a zero state 2L samples before its first output
 // (samples before t_dom count as zero), which keeps the FP32 residue history short; start-state
 // items (long windows, compensated FP32) instead begin from the exact state given by the row's
 // prefix sums (psum_kernel.cuh). The carry step uses rho^{32 ITEMS} split into two floats so that
