@@ -256,11 +256,11 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const __grid_co
 
     for (int k = 0; k < wi.n_sub; ++k) {
       const int64_t tf = wi.t_a + (int64_t)k * WT + (int64_t)lane * ITEMS;
-      if constexpr (V8 && GF) {
-        // SFT, FP32 input: an L2 prefetch of the input run two warp-tiles ahead (one bulk prefetch
+      if constexpr (PKM) {
+        // SFT Morlet, FP32 input: an L2 prefetch of the input run two warp-tiles ahead (one bulk prefetch
         // of 2 KB, issued by lane 0 through a predicate inside the asm, which keeps a divergent
         // branch out of the loop). Measured on the full scalogram: one tile ahead -1.1 %, two
-        // ahead +0.6 %; for the damped recursions -3 %, so they have none.
+        // ahead +0.6 %; for the damped recursions -3 % and for real output -4 %, so they have none.
         const int64_t a = wi.x_off + wi.t_a + (int64_t)(k + 2) * WT;
         const bool ok = k + 2 < wi.n_sub && a >= 4 && a + WT <= P.n_x;  // (rounded down: stays inside)
         const uintptr_t pa = reinterpret_cast<uintptr_t>(reinterpret_cast<const float*>(P.x) + a) & ~uintptr_t(15);
@@ -503,8 +503,8 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const __grid_co
       constexpr bool STAGE_R = (C::OUT == OUT_REAL && sizeof(R) == 4 && ITEMS == 16);
       const int64_t tw = wi.t_a + (int64_t)k * WT;  // first position of the warp-tile
       if (tw >= t_end || tw + WT <= t_out) continue;  // no output in this warp-tile (warp-uniform)
-      if constexpr (STAGE && C::ASFT) {
-        // Damped recursions (ASFT, multiplication method): whole 32-byte aligned tiles as four
+      if constexpr (STAGE && C::ASFT && C::OUT == OUT_MORLET) {
+        // ASFT Morlet (damped recursion): whole 32-byte aligned tiles as four
         // 256-bit stores per lane, the others through padded shared rows. (TMA stores measured
         // slower for these kernels: 4.45 against 4.17 ms on the full scalogram by the ASFT.)
         {
