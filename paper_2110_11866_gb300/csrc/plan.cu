@@ -129,6 +129,7 @@ struct morlet_plan_s {
   std::vector<double> sigmas;
   std::vector<int64_t> x_off;
   long long n_in = 0;  // input samples of the batch (sum of lengths)
+  long long n_pl = 0;  // adjoint: elements per plane (n_in rounded up to a multiple of 4: 16-byte plane starts)
   // MORLET_FLAG_EDGE: every signal copied into a buffer with `pad` replicated edge samples on each
   // side; the rows run on that buffer and store only their centre
   long long pad = 0;
@@ -283,7 +284,7 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
                 long long& slots, Launch& ln, std::vector<WorkItem>& pwork, std::vector<WorkItem>& lwork,
                 long long warp_slots) {
   // Forward: the S scales. Adjoint: 2S virtual scales q, the real (q = 2s) and imaginary (q = 2s + 1)
-  // plane of gW at scale s, each row reading and writing plane q (planes of n_in samples).
+  // plane of gW at scale s, each row reading and writing plane q (planes of n_pl elements).
   const int S = adjoint ? 2 * (int)p->sigmas.size() : (int)p->sigmas.size();
   const std::vector<ScaleTab>& tabs = adjoint ? p->h_tabs_adj : p->h_tabs;
   const long long nsig = (long long)p->lengths.size();
@@ -309,11 +310,11 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
   const long long E = adjoint ? 0 : p->pad;
   // the row (signal i, scale s): first input element, first output element
   auto row_in = [&](long long i, int s) -> long long {
-    if (adjoint) return (long long)s * p->n_in + p->x_off[i];
+    if (adjoint) return (long long)s * p->n_pl + p->x_off[i];
     return E ? p->xp_off[i] : p->x_off[i];
   };
   auto row_out = [&](long long i, int s) -> long long {
-    if (adjoint) return (long long)s * p->n_in + p->x_off[i];
+    if (adjoint) return (long long)s * p->n_pl + p->x_off[i];
     return (long long)S * p->x_off[i] + (long long)s * p->lengths[i] - E;  // scalogram row (minus the pad)
   };
   // start-state items: n_ss tiles each, as many tiles as leaves about four items per warp slot
@@ -477,7 +478,7 @@ int setup_launch(morlet_plan_s* p, bool adjoint, Launch& ln, long long& slots) {
   ln.func = kernel_for(variant_of(p, adjoint), p->K_kernel, false);
   if (!ln.func) return MORLET_ERR_UNSUPPORTED;
   ln.tabs = adjoint ? p->d_tabs_adj : p->d_tabs;
-  ln.n_x = adjoint ? 2 * (long long)p->sigmas.size() * p->n_in : (p->pad > 0 ? p->n_xpad : p->n_in);
+  ln.n_x = adjoint ? 2 * (long long)p->sigmas.size() * p->n_pl : (p->pad > 0 ? p->n_xpad : p->n_in);
   if (adjoint || p->form != 1) {
     ln.func_w = kernel_for(variant_of(p, adjoint), p->K_kernel, true);
     if (!ln.func_w) return MORLET_ERR_UNSUPPORTED;
@@ -804,31 +805,94 @@ fail:
 }
 
 // The adjoint's input: gW [signal][scale][n] (complex) split into its real and imaginary planes,
-// plane 2s (real) and 2s + 1 (imaginary) of n_in samples each, signal i at x_off_i in every plane.
+// plane 2s (real) and 2s + 1 (imaginary) of n_pl elements each, signal i at x_off_i in every plane.
+// Each thread moves 4 consecutive samples: 4 independent loads in flight, and for FP32 one 16-byte
+// store per plane (samples grouped so that each group starts on a 16-byte plane boundary; the first
+// samples of a row, before its first boundary, one by one).
 template <typename T>
 __global__ void split_planes_kernel(const T* __restrict__ g, T* __restrict__ planes, const int64_t* __restrict__ desc,
-                                    int64_t nsig, int32_t S, int64_t n_in) {
+                                    int64_t nsig, int32_t S, int64_t n_pl) {
+  using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
   for (int64_t r = blockIdx.y; r < nsig * S; r += gridDim.y) {
     const int64_t i = r / S, s = r % S;
     const int64_t xo = desc[2 * i], n = desc[2 * i + 1];
-    const T* gr = g + 2 * (S * xo + s * n);
-    T* pa = planes + (2 * s) * n_in + xo;
-    T* pb = pa + n_in;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-      pa[j] = gr[2 * j];
-      pb[j] = gr[2 * j + 1];
+    const T2* gr = reinterpret_cast<const T2*>(g) + (S * xo + s * n);
+    T* pa = planes + (2 * s) * n_pl + xo;
+    T* pb = pa + n_pl;
+    const int64_t h = sizeof(T) == 4 ? (4 - (xo & 3)) & 3 : 0;  // samples before the first boundary
+    if (blockIdx.x == 0 && threadIdx.x < h && threadIdx.x < n) {
+      const T2 v = __ldcs(gr + threadIdx.x);
+      pa[threadIdx.x] = v.x;
+      pb[threadIdx.x] = v.y;
+    }
+    for (int64_t j = h + 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x); j < n;
+         j += 4 * (int64_t)gridDim.x * blockDim.x) {
+      T2 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (j + u < n) v[u] = __ldcs(gr + j + u);
+      bool done = false;
+      if constexpr (sizeof(T) == 4) {
+        if (j + 4 <= n) {
+          *reinterpret_cast<float4*>(pa + j) = make_float4(v[0].x, v[1].x, v[2].x, v[3].x);
+          *reinterpret_cast<float4*>(pb + j) = make_float4(v[0].y, v[1].y, v[2].y, v[3].y);
+          done = true;
+        }
+      }
+      if (!done) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (j + u < n) {
+            pa[j + u] = v[u].x;
+            pb[j + u] = v[u].y;
+          }
+      }
     }
   }
 }
 
-// gx[t] = sum over the 2S planes in order (q = 0, 1, ..., 2S - 1), so the sum over scales has a fixed
-// order (deterministic, no atomics).
+// gx[t] = sum over the nq planes in order (q = 0, 1, ..., nq - 1), so the sum over scales has a fixed
+// order (deterministic, no atomics). FP32: 4 consecutive t per thread as 16-byte loads (planes start
+// on 16-byte boundaries), 4 planes' loads in flight.
 template <typename T>
-__global__ void sum_planes_kernel(const T* __restrict__ planes, T* __restrict__ gx, int32_t nq, int64_t n_in) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_in; t += (int64_t)gridDim.x * blockDim.x) {
-    T acc = planes[t];
-    for (int32_t q = 1; q < nq; ++q) acc += planes[q * n_in + t];
-    gx[t] = acc;
+__global__ void sum_planes_kernel(const T* __restrict__ planes, T* __restrict__ gx, int32_t nq, int64_t n_in,
+                                  int64_t n_pl) {
+  if constexpr (sizeof(T) == 4) {
+    const float4* p4 = reinterpret_cast<const float4*>(planes);
+    const int64_t q4 = n_pl / 4;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; 4 * g < n_in; g += (int64_t)gridDim.x * blockDim.x) {
+      float4 acc = __ldcs(p4 + g);
+      int32_t q = 1;
+      for (; q + 4 <= nq; q += 4) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = __ldcs(p4 + (q + u) * q4 + g);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          acc.x += v[u].x;
+          acc.y += v[u].y;
+          acc.z += v[u].z;
+          acc.w += v[u].w;
+        }
+      }
+      for (; q < nq; ++q) {
+        const float4 v = __ldcs(p4 + q * q4 + g);
+        acc.x += v.x;
+        acc.y += v.y;
+        acc.z += v.z;
+        acc.w += v.w;
+      }
+      const float a[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (4 * g + u < n_in) gx[4 * g + u] = a[u];
+    }
+  } else {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_in; t += (int64_t)gridDim.x * blockDim.x) {
+      T acc = planes[t];
+      for (int32_t q = 1; q < nq; ++q) acc += planes[q * n_pl + t];
+      gx[t] = acc;
+    }
   }
 }
 
@@ -848,23 +912,24 @@ cudaError_t backward_enqueue(morlet_plan_s* p, const void* gW, void* gx, cudaStr
   const int S = (int)p->sigmas.size();
   long long longest = 0;
   for (auto n : p->lengths) longest = std::max<long long>(longest, n);
-  const dim3 gs((unsigned)std::min<long long>(256, (longest + 255) / 256), (unsigned)std::min<long long>(65535, nsig * S));
-  const unsigned gr = (unsigned)std::min<long long>(4LL * p->sms * 8, (p->n_in + 255) / 256);
+  const dim3 gs((unsigned)std::min<long long>(256, (longest + 1023) / 1024), (unsigned)std::min<long long>(65535, nsig * S));
+  const long long groups = p->elem == 4 ? (p->n_in + 3) / 4 : p->n_in;
+  const unsigned gr = (unsigned)std::min<long long>(4LL * p->sms * 8, (groups + 255) / 256);
   if (p->elem == 8)
     split_planes_kernel<double><<<gs, 256, 0, st>>>(static_cast<const double*>(gW), static_cast<double*>(p->d_gplanes),
-                                                    p->d_sig_desc, nsig, S, p->n_in);
+                                                    p->d_sig_desc, nsig, S, p->n_pl);
   else
     split_planes_kernel<float><<<gs, 256, 0, st>>>(static_cast<const float*>(gW), static_cast<float*>(p->d_gplanes),
-                                                   p->d_sig_desc, nsig, S, p->n_in);
+                                                   p->d_sig_desc, nsig, S, p->n_pl);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = enqueue(p, p->adj, p->d_gplanes, p->d_wplanes, p->d_ticket + TICKETS, st);
   if (e != cudaSuccess) return e;
   if (p->elem == 8)
     sum_planes_kernel<double><<<gr, 256, 0, st>>>(static_cast<const double*>(p->d_wplanes), static_cast<double*>(gx),
-                                                  2 * S, p->n_in);
+                                                  2 * S, p->n_in, p->n_pl);
   else
     sum_planes_kernel<float><<<gr, 256, 0, st>>>(static_cast<const float*>(p->d_wplanes), static_cast<float*>(gx),
-                                                 2 * S, p->n_in);
+                                                 2 * S, p->n_in, p->n_pl);
   return cudaGetLastError();
 }
 
@@ -1273,6 +1338,7 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
       acc += p->lengths[i];
     }
     p->n_in = acc;
+    p->n_pl = (acc + 3) / 4 * 4;
     CK(cudaGetDevice(&p->device));
     CK(cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device));
 
@@ -1373,7 +1439,7 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
         p->h_tabs_adj[2 * s + 1] = b;
       }
       CK(cudaMemcpyAsync(p->d_tabs_adj, p->h_tabs_adj.data(), sizeof(ScaleTab) * 2 * S, cudaMemcpyHostToDevice, st));
-      const size_t planes = p->elem * 2 * (size_t)S * (size_t)p->n_in;
+      const size_t planes = p->elem * 2 * (size_t)S * (size_t)p->n_pl;
       CK(cudaMalloc(&p->d_gplanes, planes));
       CK(cudaMalloc(&p->d_wplanes, planes));
       std::vector<int64_t> sd(2 * p->lengths.size());
