@@ -161,6 +161,11 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const __grid_co
   constexpr bool APK = C::ASFT && std::is_same<R, float>::value && CH == 1 &&
                        (C::OUT == OUT_MORLET || C::OUT == OUT_REAL || C::OUT == OUT_CPLX);
   constexpr bool APC = APK && C::OUT == OUT_CPLX;
+  // The ASFT (real kappa = rho^{2L}, shared by every term) runs on U = V - kappa x[t - 2L], which
+  // obeys U <- rho U + (x[t] - kappa x[t - 2L]): the window of the last 2L samples, with a real
+  // driving term shared by every term (the SFT's form with a damped rho), so that a term pair takes
+  // four packed operations per position instead of five. Re V = Re U + kappa x[t - 2L] in the combine.
+  constexpr bool AU = APK && !APC;
   constexpr bool V8 = PK || APK;  // 256-bit loads of the FP32 input runs
   constexpr int H = Pairs<K>::H;
   using EIn = R;
@@ -187,7 +192,7 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const __grid_co
 
     const ScaleTab* tb = P.tabs + wi.scale;
     const int64_t L = tb->L, D = tb->D;
-    const int64_t Wl = GF ? 2 * L : 2 * L + 1;  // lag of the second input stream
+    const int64_t Wl = (GF || AU) ? 2 * L : 2 * L + 1;  // lag of the second input stream
     const R kap = TabR<R>::kappa(tb);
     V kapc[C::OUT == OUT_CPLX ? K : 1];  // multiplication method: complex lag factor per term
 #pragma unroll
@@ -236,6 +241,7 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const __grid_co
       }
     }
     const V E = TabR<R>::E(tb);
+    const R cxk = cx * kap;  // U form: the kappa x[t - 2L] part of Re V, summed over the terms
     const EIn* __restrict__ xs = reinterpret_cast<const EIn*>(P.x) + wi.x_off;
     const int64_t N = wi.n;
     const int64_t lo = wi.t_dom;
@@ -252,6 +258,14 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const __grid_co
       }
     } else if constexpr (C::START_H) {
       if (wi.p_row >= 0) start_state_window<K, ITEMS, true>(P, wi, tb, rho, lane, Cw);
+    }
+    if constexpr (AU) {
+      // V(b - 1) -> U(b - 1) = V(b - 1) - kappa x[b - 1 - 2L], b = the item's first position (zero
+      // for a window segment: its state and the samples before its restart are zero)
+      const int64_t u = wi.t_a - 1 - 2 * L;
+      const R xu = (u >= lo && u < N) ? xs[u] : R(0);
+#pragma unroll
+      for (int v = 0; v < NT; ++v) Cw[v].x = fma(-kap, xu, Cw[v].x);
     }
 
     for (int k = 0; k < wi.n_sub; ++k) {
@@ -328,6 +342,24 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const __grid_co
             if constexpr (PKO) B[v].y = ((v & 1) ? ry2[v >> 1].y : ry2[v >> 1].x) * s14;
             else B[v].y = rho[v % K].y * s14;
           }
+        } else if constexpr (AU) {
+          // U <- rho U + d from zero, d = x[t] - kappa x[t - 2L], two terms per instruction
+          float2 X2[H], Y2[H];
+#pragma unroll
+          for (int h = 0; h < H; ++h) X2[h] = Y2[h] = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int i = 0; i < ITEMS; ++i) {
+            const float2 d2 = pk_dup(fmaf(-kap, xl[i], xa[i]));
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+              const float2 vr = pk_fma(rx2[h], X2[h], pk_fma(nry2[h], Y2[h], d2));
+              Y2[h] = pk_fma(ry2[h], X2[h], pk_mul(rx2[h], Y2[h]));
+              X2[h] = vr;
+            }
+          }
+#pragma unroll
+          for (int v = 0; v < NT; ++v)
+            B[v] = (v & 1) ? cmake<R>(X2[v >> 1].y, Y2[v >> 1].y) : cmake<R>(X2[v >> 1].x, Y2[v >> 1].x);
         } else if constexpr (APK) {
           // the damped recursion from zero, two terms per instruction (the scalar step's operations
           // in the same order)
@@ -453,6 +485,25 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const __grid_co
             ox = pk_fma(cl2[h], vi, pk_fma(cm2[h], vr, ox));
           }
           return cmake<R>(fma(cx, xl[i], ox.x + ox.y), R(0));
+        } else if constexpr (AU) {
+          // U <- rho U + d and the combine (Re V = Re U + kappa x[t - 2L]), two terms per
+          // instruction, then the ASFT factor E
+          const float2 dd = pk_dup(fmaf(-kap, xl[i], xa[i]));
+          float2 ox = make_float2(0.f, 0.f), oy = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int h = 0; h < H; ++h) {
+            const float2 vr = pk_fma(rx2[h], X2[h], pk_fma(nry2[h], Y2[h], dd));
+            const float2 vi = pk_fma(ry2[h], X2[h], pk_mul(rx2[h], Y2[h]));
+            X2[h] = vr;
+            Y2[h] = vi;
+            if constexpr (C::OUT == OUT_MORLET) {
+              ox = pk_fma(cm2[h], vr, ox);
+              oy = pk_fma(cl2[h], vi, oy);
+            } else {
+              ox = pk_fma(cl2[h], vi, pk_fma(cm2[h], vr, ox));
+            }
+          }
+          return cmul(cmake<R>(fma(cxk, xl[i], ox.x + ox.y), oy.x + oy.y), E);
         } else if constexpr (APK) {
           // damped recursion and combine, two terms per instruction, then the ASFT factor E
           const float2 xv2 = pk_dup(xa[i]), xl2 = pk_dup(xl[i]), nk2 = pk_dup(-kap);
