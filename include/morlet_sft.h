@@ -242,8 +242,9 @@ int morlet_plan_set_row_thresholds(morlet_plan_t plan, int64_t lane_chunk_max_L,
  *   seg_mult (8, 12 or 16): window segments run about seg_mult * L positions after their 2L-position
  *     restart (a longer segment spends a smaller share on the restart);
  *   ss_tiles_max (4..64): start-state work items hold at most this many 512-position tiles;
- *   order (0 or 1): inside each block of signals the rows go scale by scale in index order (0) or
- *     in decreasing window length (1, so that the last work items claimed are the short ones);
+ *   order (0, 1 or 2): inside each block of signals the rows go scale by scale in index order (0)
+ *     or in decreasing window length (1); 2 takes order 0 and then sorts the work items of each
+ *     launch longest first, so that a launch ends on short items;
  *   asft_chains (0 or 1): ASFT plans put every row on one look-back chain (1) instead of cutting
  *     rows with 2L <= 8192 into window segments (0).
  * MORLET_FLAG_AUTOTUNE picks them (and the row thresholds) by timing. Rebuilds the forward's work

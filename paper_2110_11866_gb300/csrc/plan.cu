@@ -167,7 +167,8 @@ struct morlet_plan_s {
   // schedule knobs (MORLET_FLAG_AUTOTUNE or morlet_plan_set_schedule); none changes the transform
   int seg_mult = 16;             // window segments of about seg_mult * L positions
   long long ss_tiles_max = 32;   // start-state items of at most this many 512-position tiles
-  int order = 0;                 // 0: scales in index order inside a signal block; 1: decreasing L
+  int order = 0;                 // 0: scales in index order inside a signal block; 1: decreasing L;
+                                 // 2: order 0, then the items of each launch longest first
   int asft_chains = 0;           // ASFT: 1 = one look-back chain per row, 0 = window segments (L <= 4096)
   int tuned = 0;                 // 1: the autotuner ran; -1: it was skipped (no scratch memory)
   long long tune_outputs = 0;    // outputs of the rows the autotuner timed
@@ -469,6 +470,15 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
   ln.chain_end = (long long)(mid - work.begin());
   auto ss = std::stable_partition(mid, work.end(), [](const WorkItem& w) { return w.p_row < 0; });
   ln.ss_begin = (long long)(ss - work.begin());
+  if (p->order == 2) {
+    // longest items first inside each launch, so that the last items claimed are short ones and the
+    // launch ends with few warps idle (independent items only; look-back items keep their order)
+    auto longer = [](const WorkItem& a, const WorkItem& b) { return a.n_sub > b.n_sub; };
+    std::stable_sort(mid, ss, longer);
+    std::stable_sort(ss, work.end(), longer);
+    std::stable_sort(lwork.begin(), lwork.end(),
+                     [](const WorkItem& a, const WorkItem& b) { return a.n_sub + a.t_dom > b.n_sub + b.t_dom; });
+  }
 }
 
 int setup_launch(morlet_plan_s* p, bool adjoint, Launch& ln, long long& slots) {
@@ -1049,11 +1059,12 @@ constexpr long long TUNE_OUTPUTS = 1LL << 28;  // outputs of the subset the auto
 // (the fastest schedule depends on the batch's parallelism: a subset of the signals leaves some
 // kernels too few work items), otherwise every k-th signal up to TUNE_OUTPUTS outputs. Each
 // candidate is timed as replays of its captured forward graph, the way morlet_forward runs it.
-// Knobs are tried one at a time, each with the best values of the knobs before it:
+// Knobs are tried set by set, each with the best values of the sets before it:
 //  - compensated FP32 SFT Morlet: the row thresholds (8 pairs within the precision limits), the
-//    window-segment length (8, 12, 16 L), the scale order inside a signal block, the start-state
-//    item size (16, 32, 64 tiles);
-//  - the ASFT: one look-back chain per row against window segments, then the segment length.
+//    window-segment length (8, 12, 16 L), then the item order (index order, decreasing L, longest
+//    items first) together with the start-state item size (16, 32, 64 tiles);
+//  - the ASFT: one look-back chain per row against window segments, then the segment length,
+//    then the item order together with the start-state item size.
 // Each candidate is timed twice (interleaved passes, the faster kept), and a knob keeps its current
 // value unless another is at least 1 % faster. Every schedule computes the same transform. If the
 // sub-plan or its scratch buffers cannot be allocated the plan keeps its defaults and reports the
@@ -1179,19 +1190,15 @@ int autotune(morlet_plan_s* p, cudaStream_t st) {
     rc = try_set(c);
     if (rc) goto fail;
     c.clear();
-    for (int o : {0, 1}) {
-      Sched v = best;
-      v.order = o;
-      c.push_back(v);
-    }
-    rc = try_set(c);
-    if (rc) goto fail;
-    c.clear();
-    for (long long t : {32LL, 16LL, 64LL}) {
-      Sched v = best;
-      v.ss_tiles = t;
-      c.push_back(v);
-    }
+    // the item order and the start-state item size together: longest-first order pays off with
+    // larger items, and neither alone may clear the 1 % margin
+    for (int o : {0, 1, 2})
+      for (long long t : {32LL, 16LL, 64LL}) {
+        Sched v = best;
+        v.order = o;
+        v.ss_tiles = t;
+        c.push_back(v);
+      }
     rc = try_set(c);
     if (rc) goto fail;
   } else {
@@ -1214,11 +1221,13 @@ int autotune(morlet_plan_s* p, cudaStream_t st) {
       if (rc) goto fail;
       c.clear();
     }
-    for (int o : {0, 1}) {
-      Sched v = best;
-      v.order = o;
-      c.push_back(v);
-    }
+    for (int o : {0, 1, 2})
+      for (long long t : {32LL, 16LL, 64LL}) {
+        Sched v = best;
+        v.order = o;
+        v.ss_tiles = t;
+        c.push_back(v);
+      }
     rc = try_set(c);
     if (rc) goto fail;
   }
@@ -1628,7 +1637,7 @@ int morlet_plan_set_row_thresholds(morlet_plan_t p, int64_t lane_chunk_max_L, in
 int morlet_plan_set_schedule(morlet_plan_t p, int32_t seg_mult, int32_t ss_tiles_max, int32_t order,
                              int32_t asft_chains) {
   if (!p || (seg_mult != 8 && seg_mult != 12 && seg_mult != 16) || ss_tiles_max < 4 || ss_tiles_max > 64 ||
-      order < 0 || order > 1 || asft_chains < 0 || asft_chains > 1)
+      order < 0 || order > 2 || asft_chains < 0 || asft_chains > 1)
     return MORLET_ERR_ARG;
   if (p->h_err && *(volatile int*)p->h_err) return MORLET_ERR_TIMEOUT;
   const Sched old = get_sched(p);

@@ -214,7 +214,7 @@ def test_autotune_keeps_results():
     assert st["lane_chunk_max_L"] in (0, 64, 128, 256) and st["start_state_min_L"] in (1024, 2048)
     sc = m.morlet_plan_schedule(plan)
     assert sc["autotuned"] == 1 and sc["autotune_outputs"] == sum(lens) * len(sigmas), sc
-    assert sc["seg_mult"] in (8, 12, 16) and sc["ss_tiles_max"] in (16, 32, 64) and sc["order"] in (0, 1)
+    assert sc["seg_mult"] in (8, 12, 16) and sc["ss_tiles_max"] in (16, 32, 64) and sc["order"] in (0, 1, 2)
     for i, x in enumerate(sigs):
         for s, sg in enumerate(sigmas):
             assert rel_err(out[i][s], oracle_forward(x.astype(np.float64), sg, 4)) < 1e-5
@@ -341,7 +341,7 @@ def test_chirp_seeds_default_schedule(seed):
     assert not bad, bad
 
 
-SCHEDULES = [(16, 32, 0), (12, 32, 0), (8, 32, 0), (16, 16, 1), (16, 64, 1), (8, 64, 1)]
+SCHEDULES = [(16, 32, 0), (12, 32, 0), (8, 32, 0), (16, 16, 1), (16, 64, 1), (8, 64, 1), (16, 32, 2), (8, 16, 2)]
 
 
 @pytest.mark.parametrize("sched", SCHEDULES)
