@@ -430,7 +430,9 @@ def secondary(m, torch, dev, st, only=None):
     - the multiplication method, the ASFT and the direct method on the scalogram's scales with
       L <= 4096, and the full scalogram by the ASFT and with edge extension;
     - separable 2-D Gaussian filtering of a 4096 x 4096 image.
-    Errors are max|got - oracle| / max|oracle| over whole rows (or the stated part of them)."""
+    Errors are max|got - oracle| / max|oracle| over whole rows (or the stated part of them). The
+    batched forms are planned with MORLET_FLAG_AUTOTUNE, like the headline; their keys carry the
+    schedule the tuner chose."""
     from oracle import morlet as om
     from oracle import sft_dd
     out = {}
@@ -548,7 +550,9 @@ def secondary(m, torch, dev, st, only=None):
         x = torch.from_numpy(np.concatenate(w4.signals)).to(dev)
         n4 = B4 * N4 * S4
         y = torch.empty(n4, dtype=torch.float32, device=dev)
-        p = m.morlet_plan(lens4, w4.sigmas, K=7, method=m.MORLET_GAUSS, transform=tr, deriv=dv, precision=prec)
+        p = m.morlet_plan(lens4, w4.sigmas, K=7, method=m.MORLET_GAUSS, transform=tr, deriv=dv, precision=prec,
+                          flags=m.MORLET_FLAG_AUTOTUNE)
+        sched = m.morlet_plan_schedule(p)
         t = _timed(torch, lambda: m.morlet_forward(p, x, y, st), st)
         err = 0.0
         for b in (0, B4 - 1):
@@ -561,7 +565,7 @@ def secondary(m, torch, dev, st, only=None):
                     ref = sft_dd.asft_gauss(xb, om.fit_gauss_asft(sg, 6, dv, om.default_n0(sg)))
                 err = max(err, _row_err(got[s], ref))
         del y, x, p
-        return {"workload": "c4 batch 64 x 65536 float32, 16 scales, P = 6 (7 terms)", "ms": t,
+        return {"workload": "c4 batch 64 x 65536 float32, 16 scales, P = 6 (7 terms)", "ms": t, "schedule": sched,
                 "value": n4 / (t * 1e-3), "unit": "output samples/s",
                 "hbm_frac_at_8B_per_output": 8.0 * n4 / (t * 1e-3) / 1e9 / peak,
                 "max_rel_err_vs_oracle": err, "error_on": "signals 0 and 63 x 16 scales, every output"}
@@ -578,7 +582,9 @@ def secondary(m, torch, dev, st, only=None):
         n3 = sum(lens3) * S
         x = torch.from_numpy(w3.concat()).to(dev)
         Wt = torch.empty(n3, dtype=torch.complex64, device=dev)
-        p = m.morlet_plan(lens3, sig22, K=4, method=meth, precision=prec, transform=tr, flags=fl)
+        p = m.morlet_plan(lens3, sig22, K=4, method=meth, precision=prec, transform=tr,
+                          flags=fl | m.MORLET_FLAG_AUTOTUNE)
+        sched = m.morlet_plan_schedule(p)
         t = _timed(torch, lambda: m.morlet_forward(p, x, Wt, st), st)
         err = 0.0
         picks = (short_i, mid_i) if meth == m.MORLET_MULTIPLY else (long_i, mid_i)
@@ -594,7 +600,7 @@ def secondary(m, torch, dev, st, only=None):
                     ref = sft_dd.sft_direct_method(xd, om.fit_direct(sg, 6.0, 4))
                 err = max(err, _row_err(got[s], ref))
         del Wt, x, p
-        return {"workload": f"c3 signals, the {S} scales with L <= 4096, K = 4", "ms": t,
+        return {"workload": f"c3 signals, the {S} scales with L <= 4096, K = 4", "ms": t, "schedule": sched,
                 "value": n3 / (t * 1e-3), "unit": "output samples/s",
                 "hbm_frac_at_12B_per_output": 12.0 * n3 / (t * 1e-3) / 1e9 / peak,
                 "max_rel_err_vs_oracle": err,
@@ -611,7 +617,10 @@ def secondary(m, torch, dev, st, only=None):
         S = len(w3.sigmas)
         x = torch.from_numpy(w3.concat()).to(dev)
         Wt = torch.empty(w3.n_outputs, dtype=torch.complex64, device=dev)
+        kw = dict(kw)
+        kw["flags"] = kw.get("flags", 0) | m.MORLET_FLAG_AUTOTUNE
         p = m.morlet_plan(lens3, w3.sigmas, K=4, **kw)
+        sched = m.morlet_plan_schedule(p)
         t = _timed(torch, lambda: m.morlet_forward(p, x, Wt, st), st)
         err = 0.0
         for i in (long_i, mid_i):
@@ -628,6 +637,7 @@ def secondary(m, torch, dev, st, only=None):
         del Wt, x, p
         v = w3.n_outputs / (t * 1e-3)
         return {"workload": f"c3 scalogram (256 signals x 32 scales, K = 4) {what}", "ms": t, "value": v,
+                "schedule": sched,
                 "unit": "output samples/s", "hbm_frac_at_12B_per_output": 12.0 * v / 1e9 / peak,
                 "max_rel_err_vs_oracle": err,
                 "error_on": f"signals {long_i}, {mid_i} (lengths {lens3[long_i]}, {lens3[mid_i]}) x 32 scales, every output"}
