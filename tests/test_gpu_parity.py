@@ -240,7 +240,8 @@ def test_every_autotune_choice_passes(K):
         with pytest.raises(m.MorletError) as err:
             m.morlet_plan_set_row_thresholds(plan, *bad)
         assert err.value.code == m.MORLET_ERR_ARG
-    pairs = [(128, 2048), (256, 2048), (64, 2048), (0, 2048), (128, 1024), (256, 1024), (64, 1024), (0, 1024)]
+    pairs = [(128, 2048), (256, 2048), (64, 2048), (0, 2048), (128, 1024), (256, 1024), (64, 1024), (0, 1024),
+             (128, 512), (256, 512)]
     for ls, ss in pairs:
         m.morlet_plan_set_row_thresholds(plan, ls, ss)
         st = m.morlet_plan_stats(plan)
