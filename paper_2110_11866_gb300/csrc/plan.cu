@@ -1060,7 +1060,7 @@ constexpr long long TUNE_OUTPUTS = 1LL << 28;  // outputs of the subset the auto
 // kernels too few work items), otherwise every k-th signal up to TUNE_OUTPUTS outputs. Each
 // candidate is timed as replays of its captured forward graph, the way morlet_forward runs it.
 // Knobs are tried set by set, each with the best values of the sets before it:
-//  - compensated FP32 SFT Morlet: the row thresholds (10 pairs within the precision limits), the
+//  - compensated FP32 SFT Morlet: the row thresholds (13 pairs within the precision limits), the
 //    window-segment length (8, 12, 16 L), then the item order (index order, decreasing L, longest
 //    items first) together with the start-state item size (16, 32, 64 tiles);
 //  - the ASFT: one look-back chain per row against window segments, then the segment length,
@@ -1172,7 +1172,8 @@ int autotune(morlet_plan_s* p, cudaStream_t st) {
   if (sft) {
     const long long pairs[][2] = {{LS_MAX_L, SS_MIN_L}, {256, SS_MIN_L}, {64, SS_MIN_L}, {0, SS_MIN_L},
                                   {LS_MAX_L, 1024},     {256, 1024},     {64, 1024},       {0, 1024},
-                                  {LS_MAX_L, 512},      {256, 512}};
+                                  {LS_MAX_L, 512},      {256, 512},      {LS_MAX_L, LS_MAX_L}, {64, 64},
+                                  {0, 1}};
     std::vector<Sched> c;
     for (auto& pr : pairs) {
       Sched v = best;

@@ -211,7 +211,9 @@ def test_autotune_keeps_results():
     sigmas = [8.0, 40.0, 300.0, 1500.0]
     plan, out = gpu_forward(sigs, sigmas, K=4, flags=m.MORLET_FLAG_AUTOTUNE)
     st = m.morlet_plan_stats(plan)
-    assert st["lane_chunk_max_L"] in (0, 64, 128, 256) and st["start_state_min_L"] in (1024, 2048)
+    pairs = [(128, 2048), (256, 2048), (64, 2048), (0, 2048), (128, 1024), (256, 1024), (64, 1024), (0, 1024),
+             (128, 512), (256, 512), (128, 128), (64, 64), (0, 1)]
+    assert (st["lane_chunk_max_L"], st["start_state_min_L"]) in pairs, st
     sc = m.morlet_plan_schedule(plan)
     assert sc["autotuned"] == 1 and sc["autotune_outputs"] == sum(lens) * len(sigmas), sc
     assert sc["seg_mult"] in (8, 12, 16) and sc["ss_tiles_max"] in (16, 32, 64) and sc["order"] in (0, 1, 2)
@@ -241,7 +243,7 @@ def test_every_autotune_choice_passes(K):
             m.morlet_plan_set_row_thresholds(plan, *bad)
         assert err.value.code == m.MORLET_ERR_ARG
     pairs = [(128, 2048), (256, 2048), (64, 2048), (0, 2048), (128, 1024), (256, 1024), (64, 1024), (0, 1024),
-             (128, 512), (256, 512)]
+             (128, 512), (256, 512), (128, 128), (64, 64), (0, 1)]
     for ls, ss in pairs:
         m.morlet_plan_set_row_thresholds(plan, ls, ss)
         st = m.morlet_plan_stats(plan)
@@ -276,6 +278,34 @@ def test_chirp_sigma_sweep(K):
         for s, sg in enumerate(sigmas):
             e = rel_err(out[0][s], oracle_forward(x.astype(np.float64), sg, K))
             assert e < 1e-5, (sg, K, e)
+
+
+@pytest.mark.parametrize("K", [3, 4, 6])
+@pytest.mark.parametrize("ls,ss", [(0, 1), (64, 64), (128, 128)])
+def test_chirp_sigma_sweep_start_state_everywhere(K, ls, ss):
+    """The chirp through the kernels' bands with start-state items for every row above the
+    lane-chunk limit (no window segments), items of the longest accepted length (64 tiles), in
+    both item orders: start states from window sums of tile sums at every window length."""
+    x = WL.c2_chirps().astype(np.float32)
+    sigmas = [8.0, 11.0, 16.0, 32.0, 64.0, 128.0, 362.0, 1024.0, 2896.0]
+    refs = [oracle_forward(x.astype(np.float64), sg, K) for sg in sigmas]
+    import torch
+    plan = m.morlet_plan([len(x)], sigmas, K=K, precision=m.MORLET_FP32_COMP)
+    xt = torch.from_numpy(x).cuda()
+    for order in (0, 2):
+        m.morlet_plan_set_row_thresholds(plan, ls, ss)
+        m.morlet_plan_set_schedule(plan, 16, 64, order, 0)
+        st = m.morlet_plan_stats(plan)
+        n_lane = sum(int(np.ceil(4 * sg)) <= ls for sg in sigmas)
+        assert st["rows_lane_chunk"] == n_lane and st["rows_start_state"] == len(sigmas) - n_lane, st
+        W = torch.full((len(x) * len(sigmas),), float("nan"), dtype=torch.complex64, device="cuda")
+        m.morlet_forward(plan, xt, W)
+        torch.cuda.synchronize()
+        assert m.morlet_last_device_error(plan) == 0
+        Wh = W.cpu().numpy().reshape(len(sigmas), len(x))
+        for s, sg in enumerate(sigmas):
+            e = rel_err(Wh[s], refs[s])
+            assert e < 1e-5, (ls, ss, order, sg, K, e)
 
 
 @pytest.mark.parametrize("K", [4, 6])
