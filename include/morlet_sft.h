@@ -223,11 +223,14 @@ int morlet_plan_set_spin_limit(morlet_plan_t plan, int64_t polls);
 /*
  * morlet_plan_set_row_thresholds - choose which rows of a compensated-FP32 rotating-form SFT
  * forward take the lane-chunk scan (L <= lane_chunk_max_L; 0: none) and which take start-state
- * work items (L > start_state_min_L), the two choices MORLET_FLAG_AUTOTUNE makes by timing; other
- * plans keep their single schedule and ignore the values. Only choices that keep every row within
- * the compensated-FP32 gate (1e-5 of max|W|) are accepted: 0 <= lane_chunk_max_L <= 256 and
- * 1 <= start_state_min_L <= 2048 (window segments of longer windows drift past the gate on
- * resonant inputs). The transform is the same for every accepted choice; only the schedule
+ * work items (L > start_state_min_L), the two choices MORLET_FLAG_AUTOTUNE makes by timing. For an
+ * FP32 rotating-form ASFT plan start_state_min_L instead sets which rows start from Horner tile-sum
+ * states (L > start_state_min_L, at most 4096, the default; the other rows are window segments) and
+ * lane_chunk_max_L is ignored; other plans keep their single schedule and ignore both. Only choices
+ * that keep every row within the compensated-FP32 gate (1e-5 of max|W|) are accepted:
+ * 0 <= lane_chunk_max_L <= 256 and 1 <= start_state_min_L <= 2048 (window segments of longer
+ * windows drift past the gate on resonant inputs; start-state items hold at any window length).
+ * The transform is the same for every accepted choice; only the schedule
  * changes. Rebuilds the forward's work tables synchronously (device memory is freed and
  * allocated, so no forward of this plan may be in flight). Errors: MORLET_ERR_ARG for a value out
  * of those ranges; MORLET_ERR_NOMEM or MORLET_ERR_CUDA if the rebuild fails (the plan keeps its

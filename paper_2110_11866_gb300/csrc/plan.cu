@@ -164,6 +164,8 @@ struct morlet_plan_s {
   void* gb_out = nullptr;
   long long ss_min_L = 0;        // rows with L above this use start states (0: none)
   long long ls_max_L = 0;        // rows with L up to this use the lane-chunk scan (0: none)
+  long long h_ss_min_L = 4096;   // Horner plans (ASFT, multiplication method): rows with L above this
+                                 // start from Horner tile-sum states (the rest: window segments)
   // schedule knobs (MORLET_FLAG_AUTOTUNE or morlet_plan_set_schedule); none changes the transform
   int seg_mult = 16;             // window segments of about seg_mult * L positions
   long long ss_tiles_max = 32;   // start-state items of at most this many 512-position tiles
@@ -243,6 +245,13 @@ int seg_policy(const morlet_plan_s* p) {
 
 // Plans whose long-window rows start from window sums of Horner tile sums: the ASFT (damped rho)
 // unless the schedule puts its rows on chains, and the multiplication method (non-harmonic rho).
+// Plans whose long rows can start from Horner tile-sum states (ASFT, multiplication method; FP32,
+// rotating form, no forced chains), whatever the ASFT's chain policy.
+bool horner_capable(const morlet_plan_s* p) {
+  if (p->form != 2 || p->desc.precision == MORLET_FP64 || (p->desc.flags & MORLET_FLAG_NO_HALO)) return false;
+  return p->desc.method == MORLET_MULTIPLY || p->desc.transform == MORLET_ASFT;
+}
+
 bool horner_plan(const morlet_plan_s* p) {
   if (p->form != 2 || p->desc.precision == MORLET_FP64 || (p->desc.flags & MORLET_FLAG_NO_HALO)) return false;
   return p->desc.method == MORLET_MULTIPLY || (p->desc.transform == MORLET_ASFT && !p->asft_chains);
@@ -258,7 +267,7 @@ bool ss_row(const morlet_plan_s* p, bool adjoint, const ScaleTab& tb) {
   if (adjoint)
     return p->ss_min_L > 0 && p->desc.precision == MORLET_FP32_COMP && !(p->desc.flags & MORLET_FLAG_NO_HALO) &&
            tb.L > p->ss_min_L;
-  if (horner_plan(p)) return tb.L > TILE;
+  if (horner_plan(p)) return tb.L > p->h_ss_min_L;
   return p->ss_min_L > 0 && p->form == 2 && p->desc.precision == MORLET_FP32_COMP &&
          p->desc.transform == MORLET_SFT && p->desc.method != MORLET_MULTIPLY &&
          !(p->desc.flags & MORLET_FLAG_NO_HALO) && tb.L > p->ss_min_L;
@@ -1030,10 +1039,11 @@ struct Sched {
   int order;          // scale order inside a signal block
   long long ss_tiles; // start-state item size limit (tiles)
   int asft_chains;    // ASFT rows on one look-back chain each
+  long long h_ss;     // Horner plans: start-state rows L > h_ss
 };
 
 Sched get_sched(const morlet_plan_s* p) {
-  return Sched{p->ls_max_L, p->ss_min_L, p->seg_mult, p->order, p->ss_tiles_max, p->asft_chains};
+  return Sched{p->ls_max_L, p->ss_min_L, p->seg_mult, p->order, p->ss_tiles_max, p->asft_chains, p->h_ss_min_L};
 }
 
 void put_sched(morlet_plan_s* p, const Sched& c) {
@@ -1043,6 +1053,7 @@ void put_sched(morlet_plan_s* p, const Sched& c) {
   p->order = c.order;
   p->ss_tiles_max = c.ss_tiles;
   p->asft_chains = c.asft_chains;
+  p->h_ss_min_L = c.h_ss;
 }
 
 // Compensated FP32 SFT Morlet plans in the rotating form: the plans with row-kind choices.
@@ -1217,6 +1228,15 @@ int autotune(morlet_plan_s* p, cudaStream_t st) {
       for (int m : {16, 12, 8}) {
         Sched v = best;
         v.seg_mult = m;
+        c.push_back(v);
+      }
+      rc = try_set(c);
+      if (rc) goto fail;
+      c.clear();
+      // Horner start states from shorter windows on (1: every row)
+      for (long long h : {(long long)TILE, 512LL, 1LL}) {
+        Sched v = best;
+        v.h_ss = h;
         c.push_back(v);
       }
       rc = try_set(c);
@@ -1614,10 +1634,24 @@ int morlet_plan_set_spin_limit(morlet_plan_t p, int64_t polls) {
 }
 
 int morlet_plan_set_row_thresholds(morlet_plan_t p, int64_t lane_chunk_max_L, int64_t start_state_min_L) {
-  if (!p || lane_chunk_max_L < 0 || lane_chunk_max_L > LS_MAX_L_MAX || start_state_min_L < 1 ||
-      start_state_min_L > SS_MIN_L_MAX)
-    return MORLET_ERR_ARG;
+  if (!p || lane_chunk_max_L < 0 || lane_chunk_max_L > LS_MAX_L_MAX || start_state_min_L < 1) return MORLET_ERR_ARG;
   if (p->h_err && *(volatile int*)p->h_err) return MORLET_ERR_TIMEOUT;
+  // the ASFT: Horner start states for the rows with L above the limit (<= 4096)
+  if (horner_capable(p) && p->desc.transform == MORLET_ASFT) {
+    if (start_state_min_L > TILE) return MORLET_ERR_ARG;
+    const long long old_h = p->h_ss_min_L;
+    p->h_ss_min_L = start_state_min_L;
+    long long slots = 0;
+    int rc = build_forward(p, slots);
+    if (rc != MORLET_OK) {
+      p->h_ss_min_L = old_h;
+      long long s2 = 0;
+      const int rc2 = build_forward(p, s2);
+      return rc2 != MORLET_OK ? rc2 : rc;
+    }
+    return MORLET_OK;
+  }
+  if (start_state_min_L > SS_MIN_L_MAX) return MORLET_ERR_ARG;
   const morlet_plan_desc& d = p->desc;
   if (!(p->form == 2 && d.precision == MORLET_FP32_COMP && d.transform == MORLET_SFT && d.method == MORLET_DIRECT))
     return MORLET_OK;  // a single schedule
@@ -1663,7 +1697,7 @@ int morlet_plan_set_schedule(morlet_plan_t p, int32_t seg_mult, int32_t ss_tiles
 int morlet_plan_schedule(morlet_plan_t p, int64_t o[8]) {
   if (!p || !o) return MORLET_ERR_ARG;
   o[0] = p->ls_max_L;
-  o[1] = p->ss_min_L;
+  o[1] = (horner_capable(p) && p->desc.transform == MORLET_ASFT) ? p->h_ss_min_L : p->ss_min_L;
   o[2] = p->seg_mult;
   o[3] = p->ss_tiles_max;
   o[4] = p->order;

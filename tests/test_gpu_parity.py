@@ -126,6 +126,31 @@ def test_asft_start_state_rows(K):
             worst = max(worst, e)
             assert e < 1e-4, (i, sg, e)
     print(f"ASFT start-state rows K={K}: worst {worst:.2e}")
+    # Horner start states from shorter windows on, down to every row, in both item orders
+    import torch
+    refs = [[oracle_forward(x.astype(np.float64), sg, K, transform=m.MORLET_ASFT) for sg in sigmas] for x in sigs]
+    xt = torch.from_numpy(np.concatenate(sigs)).cuda()
+    S, n_in = len(sigmas), sum(lens)
+    for h in (512, 1):
+        for order in (0, 2):
+            m.morlet_plan_set_row_thresholds(plan, 0, h)
+            m.morlet_plan_set_schedule(plan, 16, 64, order, 0)
+            st = m.morlet_plan_stats(plan)
+            assert st["rows_start_state"] == sum(4 * sg > h for sg in sigmas) * len(lens), (h, st)
+            assert m.morlet_plan_schedule(plan)["start_state_min_L"] == h
+            W = torch.full((n_in * S,), float("nan"), dtype=torch.complex64, device="cuda")
+            m.morlet_forward(plan, xt, W)
+            torch.cuda.synchronize()
+            assert m.morlet_last_device_error(plan) == 0
+            Wh = W.cpu().numpy()
+            off = 0
+            for i, n in enumerate(lens):
+                for s, sg in enumerate(sigmas):
+                    e = rel_err(Wh[S * off + s * n: S * off + (s + 1) * n], refs[i][s])
+                    assert e < 1e-4, (h, order, i, sg, e)
+                off += n
+    with pytest.raises(m.MorletError):
+        m.morlet_plan_set_row_thresholds(plan, 0, 4097)
     import torch
     P = K + 3
     gplan = m.morlet_plan(lens, sigmas, K=P + 1, method=m.MORLET_GAUSS, transform=m.MORLET_ASFT, deriv=1,
