@@ -63,7 +63,7 @@ enum {
 /* flags */
 enum {
   MORLET_FLAG_NO_GRAPH = 1,   /* launch kernels directly instead of replaying a CUDA graph */
-  MORLET_FLAG_AUTOTUNE = 2,   /* compensated FP32 SFT Morlet and ASFT plans: at plan time, time the
+  MORLET_FLAG_AUTOTUNE = 2,   /* compensated FP32 SFT Morlet, ASFT and multiplication-method plans: at plan time, time the
                                  forward (a sub-plan with a zero input and a scratch output: the whole
                                  batch if that scratch takes at most a quarter of the free device
                                  memory, else every k-th signal up to 2^28 outputs) under a few
@@ -224,7 +224,8 @@ int morlet_plan_set_spin_limit(morlet_plan_t plan, int64_t polls);
  * morlet_plan_set_row_thresholds - choose which rows of a compensated-FP32 rotating-form SFT
  * forward take the lane-chunk scan (L <= lane_chunk_max_L; 0: none) and which take start-state
  * work items (L > start_state_min_L), the two choices MORLET_FLAG_AUTOTUNE makes by timing. For an
- * FP32 rotating-form ASFT plan start_state_min_L instead sets which rows start from Horner tile-sum
+ * FP32 rotating-form ASFT or multiplication-method plan start_state_min_L instead sets which rows
+ * start from Horner tile-sum
  * states (L > start_state_min_L, at most 4096, the default; the other rows are window segments) and
  * lane_chunk_max_L is ignored; other plans keep their single schedule and ignore both. Only choices
  * that keep every row within the compensated-FP32 gate (1e-5 of max|W|) are accepted:

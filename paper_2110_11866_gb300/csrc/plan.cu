@@ -1075,7 +1075,8 @@ constexpr long long TUNE_OUTPUTS = 1LL << 28;  // outputs of the subset the auto
 //    window-segment length (8, 12, 16 L), then the item order (index order, decreasing L, longest
 //    items first) together with the start-state item size (16, 32, 64 tiles);
 //  - the ASFT: one look-back chain per row against window segments, then the segment length,
-//    then the item order together with the start-state item size.
+//    the window length beyond which rows start from Horner states, and the item order together
+//    with the start-state item size; the multiplication method the same without the chains.
 // Each candidate is timed twice (interleaved passes, the faster kept), and a knob keeps its current
 // value unless another is at least 1 % faster. Every schedule computes the same transform. If the
 // sub-plan or its scratch buffers cannot be allocated the plan keeps its defaults and reports the
@@ -1084,7 +1085,8 @@ int autotune(morlet_plan_s* p, cudaStream_t st) {
   const morlet_plan_desc& d = p->desc;
   const bool sft = sft_schedulable(p);
   const bool asft = d.transform == MORLET_ASFT && !(d.flags & MORLET_FLAG_NO_HALO);
-  if (!sft && !asft) return MORLET_OK;
+  const bool mult = d.method == MORLET_MULTIPLY && horner_capable(p);
+  if (!sft && !asft && !mult) return MORLET_OK;
   const long long S = (long long)p->sigmas.size();
   const long long nsig = (long long)p->lengths.size();
   const long long total = p->n_in * S;
@@ -1216,14 +1218,16 @@ int autotune(morlet_plan_s* p, cudaStream_t st) {
     if (rc) goto fail;
   } else {
     std::vector<Sched> c;
-    for (int a : {0, 1}) {
-      Sched v = best;
-      v.asft_chains = a;
-      c.push_back(v);
+    if (asft) {  // the multiplication method has no look-back chains
+      for (int a : {0, 1}) {
+        Sched v = best;
+        v.asft_chains = a;
+        c.push_back(v);
+      }
+      rc = try_set(c);
+      if (rc) goto fail;
+      c.clear();
     }
-    rc = try_set(c);
-    if (rc) goto fail;
-    c.clear();
     if (!best.asft_chains) {
       for (int m : {16, 12, 8}) {
         Sched v = best;
@@ -1636,8 +1640,9 @@ int morlet_plan_set_spin_limit(morlet_plan_t p, int64_t polls) {
 int morlet_plan_set_row_thresholds(morlet_plan_t p, int64_t lane_chunk_max_L, int64_t start_state_min_L) {
   if (!p || lane_chunk_max_L < 0 || lane_chunk_max_L > LS_MAX_L_MAX || start_state_min_L < 1) return MORLET_ERR_ARG;
   if (p->h_err && *(volatile int*)p->h_err) return MORLET_ERR_TIMEOUT;
-  // the ASFT: Horner start states for the rows with L above the limit (<= 4096)
-  if (horner_capable(p) && p->desc.transform == MORLET_ASFT) {
+  // the ASFT and the multiplication method: Horner start states for the rows with L above the
+  // limit (<= 4096)
+  if (horner_capable(p)) {
     if (start_state_min_L > TILE) return MORLET_ERR_ARG;
     const long long old_h = p->h_ss_min_L;
     p->h_ss_min_L = start_state_min_L;
@@ -1697,7 +1702,7 @@ int morlet_plan_set_schedule(morlet_plan_t p, int32_t seg_mult, int32_t ss_tiles
 int morlet_plan_schedule(morlet_plan_t p, int64_t o[8]) {
   if (!p || !o) return MORLET_ERR_ARG;
   o[0] = p->ls_max_L;
-  o[1] = (horner_capable(p) && p->desc.transform == MORLET_ASFT) ? p->h_ss_min_L : p->ss_min_L;
+  o[1] = horner_capable(p) ? p->h_ss_min_L : p->ss_min_L;
   o[2] = p->seg_mult;
   o[3] = p->ss_tiles_max;
   o[4] = p->order;

@@ -328,15 +328,33 @@ def test_multiply_method(K, norm):
     torch.cuda.synchronize()
     assert m.morlet_last_device_error(plan) == 0
     Wh = W.cpu().numpy()
+    refs = [[om.morlet_multiply_direct(x.astype(np.float64), om.fit_multiply(sigma, xi, K, norm=norm))
+             for sigma in sigmas] for x in sigs]
     off = 0
-    for x, n in zip(sigs, lens):
+    for i, n in enumerate(lens):
         for s, sigma in enumerate(sigmas):
-            ref = om.morlet_multiply_direct(x.astype(np.float64), om.fit_multiply(sigma, xi, K, norm=norm))
             got = Wh[S * off + s * n: S * off + (s + 1) * n]
-            e = rel_err(got, ref)
+            e = rel_err(got, refs[i][s])
             print(f"multiply K={K} norm={norm} n={n} sigma={sigma}: {e:.2e}")
             assert e < 1e-4, (n, sigma, e)
         off += n
+    # Horner start states from shorter windows on (every row at 1), longest items first
+    for h in (512, 1):
+        m.morlet_plan_set_row_thresholds(plan, 0, h)
+        m.morlet_plan_set_schedule(plan, 16, 64, 2, 0)
+        st = m.morlet_plan_stats(plan)
+        assert st["rows_start_state"] == sum(4 * sg > h for sg in sigmas) * len(lens), (h, st)
+        W = torch.full((n_in * S,), float("nan"), dtype=torch.complex64, device="cuda")
+        m.morlet_forward(plan, xt, W)
+        torch.cuda.synchronize()
+        assert m.morlet_last_device_error(plan) == 0
+        Wh = W.cpu().numpy()
+        off = 0
+        for i, n in enumerate(lens):
+            for s, sigma in enumerate(sigmas):
+                e = rel_err(Wh[S * off + s * n: S * off + (s + 1) * n], refs[i][s])
+                assert e < 1e-4, (h, n, sigma, e)
+            off += n
 
 
 @pytest.mark.parametrize("sigma", [300.0, 2000.0])
