@@ -3,7 +3,8 @@
 Workload (default): the batched scalogram -- 256 float32 signals with lengths log-uniform in
 [1024, 1048576] (seed 2), 32 scales sigma = 2^(3 + j/3), omega0 = 6/sigma, K = 4, compensated FP32
 (FP32 scan, two-float carries and prefix sums), complex64 outputs, one graph-captured forward per
-step (lane-chunk kernel, two warp-scan launches, tile-sum kernel). A step is one whole transform of the batch (all
+step on the schedule MORLET_FLAG_AUTOTUNE picks (on this batch: the tile sums, then start-state
+work items of the warp scan for every row). A step is one whole transform of the batch (all
 hot-path steps: load, rotation, scan, start states, combine, store). Metric: complex output samples per second; the roofline counts the algorithmic
 12 bytes per output (4-byte input read + 8-byte output write) against the measured copy bandwidth.
 
@@ -346,7 +347,11 @@ def main():
                                           "start_state_min_L": pst["start_state_min_L"]}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "forward step (lane-chunk, warp-scan and tile-sum kernels, one graph)",
+                         "kernel": "forward step, whole graph (" + ", ".join(
+                             k for k, on in (("lane-chunk scan", stats.get("rows_lane_chunk", 0) > 0),
+                                             ("warp scan", stats.get("rows_window", 0) + stats.get("rows_start_state", 0) > 0),
+                                             ("tile sums", stats.get("prefix_items", 0) > 0),
+                                             ("look-back scan", stats.get("rows_lookback", 0) > 0)) if on) + ")",
                          "algorithmic_bytes_per_output": BYTES_PER_OUTPUT,
                          "strict_floor_bytes_per_output": 8 + 4 / S,
                          "strict_floor_frac": achieved * (8 + 4 / S) / BYTES_PER_OUTPUT / peak},
