@@ -1516,7 +1516,19 @@ int morlet_plan(morlet_plan_t* out, const morlet_plan_desc* d, void* stream) {
     if (rc) goto fail;
     long long slots_adj = 0;
     if (has_adj) {
+      // The adjoint's rows (compensated FP32) as start-state items for every row, 64 tiles each,
+      // longest first: the schedule the autotuner picks for the forward of a large batch
+      const long long ss0 = p->ss_min_L, t0 = p->ss_tiles_max;
+      const int o0 = p->order;
+      if (p->desc.precision == MORLET_FP32_COMP) {
+        p->ss_min_L = 1;
+        p->ss_tiles_max = 64;
+        p->order = 2;
+      }
       rc = setup_launch(p, true, p->adj, slots_adj);
+      p->ss_min_L = ss0;
+      p->ss_tiles_max = t0;
+      p->order = o0;
       if (rc) goto fail;
     }
     p->nt_slot = p->K_kernel;
