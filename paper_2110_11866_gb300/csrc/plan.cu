@@ -66,10 +66,12 @@ constexpr int TICKETS = 5;
 constexpr long long PS_TILE_H = 512, PS_CHUNK_H = 8;  // prefix-sum tile and chunk (psum_kernel.cuh)
 constexpr long long TS_CHUNK_H = 8;                    // tiles per tile-sum work item
 // Rows whose half window exceeds this start their work items from exact states (window sums of
-// tile sums, or prefix sums). A window segment restarts 2L positions before its first output and
-// runs about 16 L positions, so its FP32 residue history grows with L; for L > 2048 a resonant
-// input (a chirp through the kernel's band) takes it past 1e-5 of max|W| (1.4e-5 measured at
-// L = 4096), while start-state items (at most 32 warp-tiles from an exact state) stay below 9e-6.
+// tile sums, or prefix sums); the default, without autotuning. A window segment restarts 2L
+// positions before its first output and runs about 16 L positions, so its FP32 residue history
+// grows with L; for L > 2048 a resonant input (a chirp through the kernel's band) takes it past
+// 1e-5 of max|W| (1.4e-5 measured at L = 4096), while start-state items (up to 64 warp-tiles from
+// an exact state, two-float carries between warp-tiles) stay within the gate at any L. Lower
+// thresholds, down to 1 (start-state items for every row), are the autotuner's to choose.
 constexpr long long SS_MIN_L = 2048;
 // Largest start-state threshold and lane-chunk threshold that keep every row within the
 // compensated-FP32 gate (measured on chirps and white noise, K = 3..6).
