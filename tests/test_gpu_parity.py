@@ -306,12 +306,13 @@ def test_chirp_sigma_sweep(K):
 
 
 @pytest.mark.parametrize("K", [3, 4, 6])
-@pytest.mark.parametrize("ls,ss", [(0, 1), (64, 64), (128, 128)])
-def test_chirp_sigma_sweep_start_state_everywhere(K, ls, ss):
-    """The chirp through the kernels' bands with start-state items for every row above the
-    lane-chunk limit (no window segments), items of the longest accepted length (64 tiles), in
-    both item orders: start states from window sums of tile sums at every window length."""
-    x = WL.c2_chirps().astype(np.float32)
+@pytest.mark.parametrize("ls,ss,seed", [(0, 1, 1), (64, 64, 1), (128, 128, 1), (0, 1, 11), (0, 1, 13)])
+def test_chirp_sigma_sweep_start_state_everywhere(K, ls, ss, seed):
+    """The chirp through the kernels' bands (several seeds of the recipe) with start-state items for
+    every row above the lane-chunk limit (no window segments), items of the longest accepted length
+    (64 tiles), in both item orders: start states from window sums of tile sums at every window
+    length."""
+    x = WL.c2_chirps(seed).astype(np.float32)
     sigmas = [8.0, 11.0, 16.0, 32.0, 64.0, 128.0, 362.0, 1024.0, 2896.0]
     refs = [oracle_forward(x.astype(np.float64), sg, K) for sg in sigmas]
     import torch
