@@ -173,8 +173,9 @@ int gauss_smooth(const void* x, int64_t N, double sigma, int32_t P, int32_t deri
  * overlap. deriv_x, deriv_y in 0..2 (G, G_D, G_DD along that axis); harmonics p = 0..P; L =
  * ceil(4 sigma); zero extension outside the image.
  * Builds (first call) and caches, per (device, ny, nx, sigma, P, deriv_y, deriv_x, precision), the
- * two 1-D plans and a workspace of 2 ny nx elements; later calls with the same key allocate nothing
- * and are asynchronous on `stream`.
+ * two 1-D plans (with MORLET_FLAG_AUTOTUNE: the first call also times their schedules) and a
+ * workspace of 2 ny nx elements; later calls with the same key allocate nothing and are
+ * asynchronous on `stream`.
  * Errors: MORLET_ERR_ARG (sizes, derivatives, precision; ny or nx above 2^21), MORLET_ERR_NOMEM,
  * MORLET_ERR_CUDA, and those of morlet_plan / morlet_forward.
  */

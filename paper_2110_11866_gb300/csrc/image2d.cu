@@ -64,6 +64,7 @@ int make_plan(int64_t n_signals, int64_t len, double sigma, int32_t P, int32_t d
   d.transform = MORLET_SFT;
   d.precision = precision;
   d.deriv = deriv;
+  d.flags = MORLET_FLAG_AUTOTUNE;  // the schedule timed once per image shape, when the plans are made
   return morlet_plan(out, &d, stream);
 }
 

@@ -1058,10 +1058,12 @@ void put_sched(morlet_plan_s* p, const Sched& c) {
   p->h_ss_min_L = c.h_ss;
 }
 
-// Compensated FP32 SFT Morlet plans in the rotating form: the plans with row-kind choices.
+// Compensated FP32 SFT plans in the rotating form (Morlet, Gaussian): the plans with row-kind choices
+// (the Gaussian rows have no lane-chunk scan; their limit there has no effect).
 bool sft_schedulable(const morlet_plan_s* p) {
   const morlet_plan_desc& d = p->desc;
-  return p->form == 2 && d.precision == MORLET_FP32_COMP && d.transform == MORLET_SFT && d.method == MORLET_DIRECT;
+  return p->form == 2 && d.precision == MORLET_FP32_COMP && d.transform == MORLET_SFT &&
+         (d.method == MORLET_DIRECT || d.method == MORLET_GAUSS);
 }
 
 constexpr long long TUNE_OUTPUTS = 1LL << 28;  // outputs of the subset the autotuner times when the batch is too big
@@ -1672,8 +1674,7 @@ int morlet_plan_set_row_thresholds(morlet_plan_t p, int64_t lane_chunk_max_L, in
   }
   if (start_state_min_L > SS_MIN_L_MAX) return MORLET_ERR_ARG;
   const morlet_plan_desc& d = p->desc;
-  if (!(p->form == 2 && d.precision == MORLET_FP32_COMP && d.transform == MORLET_SFT && d.method == MORLET_DIRECT))
-    return MORLET_OK;  // a single schedule
+  if (!sft_schedulable(p)) return MORLET_OK;  // a single schedule
   const long long old_ls = p->ls_max_L, old_ss = p->ss_min_L;
   p->ls_max_L = lane_chunk_max_L;
   p->ss_min_L = start_state_min_L;

@@ -269,6 +269,41 @@ def test_gauss_smooth(deriv, precision):
 
 
 @pytest.mark.parametrize("deriv", [0, 1, 2])
+def test_gauss_smooth_start_state_everywhere(deriv):
+    """Gaussian smoothing by the SFT (compensated FP32, a ragged batch at several scales) with every
+    row on start-state items (thresholds 0:1, 64-tile items longest first, the schedule the
+    autotuner may pick for these plans) against the oracle's kernel integral, gate 1e-5."""
+    import torch
+    rng = np.random.default_rng(60 + deriv)
+    lens = [70000, 5, 4097, 30000]
+    sigs = [rng.standard_normal(n).astype(np.float32) for n in lens]
+    sigmas, P = [5.0, 40.0, 700.0], 6
+    plan = m.morlet_plan(lens, sigmas, K=P + 1, method=m.MORLET_GAUSS, deriv=deriv, precision=m.MORLET_FP32_COMP)
+    m.morlet_plan_set_row_thresholds(plan, 0, 1)
+    m.morlet_plan_set_schedule(plan, 16, 64, 2, 0)
+    st = m.morlet_plan_stats(plan)
+    assert st["rows_start_state"] == len(lens) * len(sigmas), st
+    S, n_in = len(sigmas), sum(lens)
+    y = torch.full((n_in * S,), float("nan"), dtype=torch.float32, device="cuda")
+    m.morlet_forward(plan, torch.from_numpy(np.concatenate(sigs)).cuda(), y)
+    torch.cuda.synchronize()
+    assert m.morlet_last_device_error(plan) == 0
+    yh = y.cpu().numpy()
+    off = 0
+    for x, n in zip(sigs, lens):
+        for s, sg in enumerate(sigmas):
+            gf = om.fit_gauss(sg, P, deriv)
+            ref = sft_dd.sft_gauss(x.astype(np.float64), gf)
+            got = yh[S * off + s * n: S * off + (s + 1) * n]
+            scale = np.abs(ref).max()
+            if n < 2 * gf["L"]:  # a row shorter than the window: the rounding scale of its arithmetic
+                scale = max(scale, np.abs(om.kernel_gauss(gf)).sum() * np.abs(x).max())
+            e = float(np.abs(got - ref).max() / scale)
+            assert e < 1e-5, (deriv, n, sg, e)
+        off += n
+
+
+@pytest.mark.parametrize("deriv", [0, 1, 2])
 def test_gauss_smooth_asft(deriv):
     """Gaussian smoothing and its derivatives by the ASFT (eqs. GsASFT, gddAsft, FP32 attenuated
     recursion): a batch of ragged signals at several scales against the oracle's double-double
