@@ -292,6 +292,22 @@ void ss_tiles(long long x_off, long long o_lo, long long o_hi, long long& t_grid
   kE = (o_hi - 1 - t_grid) / PS_TILE_H;
 }
 
+// The tiles whose sums a start-state item starting on tile kb of its row reads (start_state_window):
+// its window begins at u0 = t_a - 2L (t_a - 2L - 1 for the Horner form's 2L + 1 samples); the tile
+// holding u0 is summed by the item itself when u0 lies inside it (a masked sum), so the item reads
+// the sums of tiles [a, b) = [k0 (+ 1 if u0 is inside tile k0), kb).
+void window_tiles(long long t_grid, long long kb, long long L, bool horner, long long& a, long long& b) {
+  const long long u0 = t_grid + PS_TILE_H * kb - 2 * L - (horner ? 1 : 0);
+  long long k0 = 0;
+  bool partial = false;
+  if (u0 > t_grid) {
+    k0 = (u0 - t_grid) / PS_TILE_H;
+    partial = u0 > t_grid + PS_TILE_H * k0;
+  }
+  a = k0 + (partial ? 1 : 0);
+  b = kb;
+}
+
 void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& work, std::vector<ChainDesc>& chains,
                 long long& slots, Launch& ln, std::vector<WorkItem>& pwork, std::vector<WorkItem>& lwork,
                 long long warp_slots) {
@@ -345,6 +361,7 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
   for (auto& rs : order)
     if (ss_row(p, adjoint, tabs[rs.second])) max_win = std::max<long long>(max_win, 2 * tabs[rs.second].L / PS_TILE_H + 2);
   ln.ss_window = ((!adjoint && horner_plan(p)) || max_win <= 16 * n_ss) ? 1 : 0;  // Horner rows: window sums only
+  const bool horner_rows = !adjoint && horner_plan(p);
   for (auto& rs : order) {
     const long long i = rs.first;
     const int s = rs.second;
@@ -422,16 +439,15 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
         k_last = k;
       }
       // Prefix sums at the ends of tiles 0 .. k_last - 1 (prefix mode: every tile); or tile sums
-      // (window mode) of the tiles inside the windows of the item starts kb, [kb - wt, kb - 1] with
-      // wt = ceil((2L + 1) / 512) + 1 (a window spans at most that many tiles), in chunks.
+      // (window mode) of the tiles the item starts kb read (window_tiles), in chunks.
       const long long n_t = k_last;
       const long long first = ln.n_pslots;
       const long long chunk = ln.ss_window ? TS_CHUNK_H : PS_CHUNK_H;
       std::vector<std::pair<long long, long long>> need;  // tile ranges [a, b)
       if (ln.ss_window) {
-        const long long wt = (2 * tb.L + 1 + PS_TILE_H - 1) / PS_TILE_H + 1;
         for (long long kb = kD; kb <= k_last; kb += n_ss) {
-          const long long a = std::max(0LL, kb - wt), b = kb;
+          long long a, b;
+          window_tiles(tg, kb, tb.L, horner_rows, a, b);
           if (a >= b) continue;
           if (!need.empty() && a <= need.back().second) need.back().second = std::max(need.back().second, b);
           else need.push_back({a, b});
@@ -1078,9 +1094,10 @@ constexpr long long TUNE_OUTPUTS = 1LL << 28;  // outputs of the subset the auto
 //  - compensated FP32 SFT Morlet: the row thresholds (13 pairs within the precision limits), the
 //    window-segment length (8, 12, 16 L), then the item order (index order, decreasing L, longest
 //    items first) together with the start-state item size (16, 32, 64 tiles);
-//  - the ASFT: one look-back chain per row against window segments, then the segment length,
-//    the window length beyond which rows start from Horner states, and the item order together
-//    with the start-state item size; the multiplication method the same without the chains.
+//  - the ASFT: one look-back chain per row against window segments with Horner start states for
+//    the rows beyond each window length (4096, 512, 1: every row), then the segment length, that
+//    window length again, and the item order together with the start-state item size; the
+//    multiplication method the same without the chains.
 // Each candidate is timed twice (interleaved passes, the faster kept), and a knob keeps its current
 // value unless another is at least 1 % faster. Every schedule computes the same transform. If the
 // sub-plan or its scratch buffers cannot be allocated the plan keeps its defaults and reports the
@@ -1223,11 +1240,17 @@ int autotune(morlet_plan_s* p, cudaStream_t st) {
   } else {
     std::vector<Sched> c;
     if (asft) {  // the multiplication method has no look-back chains
-      for (int a : {0, 1}) {
-        Sched v = best;
-        v.asft_chains = a;
-        c.push_back(v);
-      }
+      // one chain per row against window segments with Horner start states from each limit on: the
+      // limit decides whether segments win (the c4 Gaussian ASFT batch: chains 79 G outputs/s,
+      // segments with the default limit 74, with start states for every row 110)
+      for (int a : {0, 1})
+        for (long long h : {(long long)TILE, 512LL, 1LL}) {
+          if (a == 1 && h != (long long)TILE) continue;
+          Sched v = best;
+          v.asft_chains = a;
+          v.h_ss = a == 1 ? best.h_ss : h;
+          c.push_back(v);
+        }
       rc = try_set(c);
       if (rc) goto fail;
       c.clear();
