@@ -647,6 +647,38 @@ def secondary(m, torch, dev, st, only=None):
                 "max_rel_err_vs_oracle": err,
                 "error_on": f"signals {long_i}, {mid_i} (lengths {lens3[long_i]}, {lens3[mid_i]}) x 32 scales, every output"}
 
+    # ---- the full scalogram by the multiplication method (windows up to L = 41286) ----
+    def multiply_full():
+        S = len(w3.sigmas)
+        x = torch.from_numpy(w3.concat()).to(dev)
+        Wt = torch.empty(w3.n_outputs, dtype=torch.complex64, device=dev)
+        p = m.morlet_plan(lens3, w3.sigmas, K=4, method=m.MORLET_MULTIPLY, precision=m.MORLET_FP32_PLAIN,
+                          flags=m.MORLET_FLAG_AUTOTUNE)
+        sched = m.morlet_plan_schedule(p)
+        t = _timed(torch, lambda: m.morlet_forward(p, x, Wt, st), st)
+        err = 0.0
+        rng = np.random.default_rng(7)
+        for i in (short_i, mid_i, long_i):
+            xd = w3.signals[i].astype(np.float64)
+            got = rows_of(Wt, i, S)
+            n = lens3[i]
+            # the shortest signal whole; the others at 512 positions (both ends, the middle, random)
+            idx = None if n <= 4096 else np.unique(np.concatenate([[0, 1, n // 2, n - 2, n - 1],
+                                                                   rng.integers(0, n, 507)]))
+            for s, sg in enumerate(w3.sigmas):
+                ref = om.morlet_multiply_direct(xd, om.fit_multiply(sg, 6.0, 4), idx)
+                err = max(err, _row_err(got[s] if idx is None else got[s][idx], ref))
+        del Wt, x, p
+        v = w3.n_outputs / (t * 1e-3)
+        return {"workload": "c3 scalogram (256 signals x 32 scales) by the multiplication method, K = 4 "
+                            "(7 non-harmonic terms, FP32)", "ms": t, "value": v, "schedule": sched,
+                "unit": "output samples/s", "hbm_frac_at_12B_per_output": 12.0 * v / 1e9 / peak,
+                "max_rel_err_vs_oracle": err,
+                "error_on": f"signal {short_i} (length {lens3[short_i]}) x 32 scales, every output; signals "
+                            f"{mid_i}, {long_i} x 32 scales at 512 positions each (denominator: the oracle's "
+                            f"maximum over those positions)"}
+
+    guard("multiply_K4_c3", multiply_full)
     guard("edge_extension_c3", lambda: full("with edge extension",
                                             dict(precision=m.MORLET_FP32_COMP, flags=m.MORLET_FLAG_EDGE), True))
     guard("asft_K4_c3", lambda: full("by the ASFT (FP32)",

@@ -392,12 +392,13 @@ def test_multiply_method(K, norm):
             off += n
 
 
-@pytest.mark.parametrize("sigma", [300.0, 2000.0])
-def test_multiply_method_long_signal(sigma):
+@pytest.mark.parametrize("sigma,tail", [(300.0, 1 << 17), (2000.0, 1 << 17), (10321.27, 1 << 15)])
+def test_multiply_method_long_signal(sigma, tail):
     """The multiplication method's non-harmonic powers e^{i omega0 n} are formed from an FP64 angle
     (reduced mod 2 pi) times an exact harmonic: on a 2^24-sample signal (window segments at sigma 300,
-    start-state items at 2000) outputs up to n = 2^24 - 1 agree with the direct sum of the oracle's
-    kernel, at sampled n everywhere in the row and on a full 2^17-sample stretch at its end."""
+    start-state items at 2000 and at the c3 scalogram's largest scale, L = 41286) outputs up to
+    n = 2^24 - 1 agree with the direct sum of the oracle's kernel, at sampled n everywhere in the row
+    and on a full stretch at its end."""
     import torch
     N, K = 1 << 24, 4
     x = WL.c5_pink()
@@ -410,7 +411,6 @@ def test_multiply_method_long_signal(sigma):
     rng = np.random.default_rng(int(sigma))
     idx = np.unique(np.concatenate([[0, 1, N // 2, N - 2, N - 1], rng.integers(0, N, 64)]))
     ref = om.morlet_multiply_direct(x.astype(np.float64), mf, idx)
-    tail = 1 << 17
     M = tail + 2 * mf["L"]
     ref_tail = om.morlet_multiply_direct(x[N - M:].astype(np.float64), mf)[M - tail:]
     Wh = W.cpu().numpy()
