@@ -292,22 +292,6 @@ void ss_tiles(long long x_off, long long o_lo, long long o_hi, long long& t_grid
   kE = (o_hi - 1 - t_grid) / PS_TILE_H;
 }
 
-// The tiles whose sums a start-state item starting on tile kb of its row reads (start_state_window):
-// its window begins at u0 = t_a - 2L (t_a - 2L - 1 for the Horner form's 2L + 1 samples); the tile
-// holding u0 is summed by the item itself when u0 lies inside it (a masked sum), so the item reads
-// the sums of tiles [a, b) = [k0 (+ 1 if u0 is inside tile k0), kb).
-void window_tiles(long long t_grid, long long kb, long long L, bool horner, long long& a, long long& b) {
-  const long long u0 = t_grid + PS_TILE_H * kb - 2 * L - (horner ? 1 : 0);
-  long long k0 = 0;
-  bool partial = false;
-  if (u0 > t_grid) {
-    k0 = (u0 - t_grid) / PS_TILE_H;
-    partial = u0 > t_grid + PS_TILE_H * k0;
-  }
-  a = k0 + (partial ? 1 : 0);
-  b = kb;
-}
-
 void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& work, std::vector<ChainDesc>& chains,
                 long long& slots, Launch& ln, std::vector<WorkItem>& pwork, std::vector<WorkItem>& lwork,
                 long long warp_slots) {
@@ -439,7 +423,7 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
         k_last = k;
       }
       // Prefix sums at the ends of tiles 0 .. k_last - 1 (prefix mode: every tile); or tile sums
-      // (window mode) of the tiles the item starts kb read (window_tiles), in chunks.
+      // (window mode) of the tiles the item starts kb read (ss_window_tiles), in chunks.
       const long long n_t = k_last;
       const long long first = ln.n_pslots;
       const long long chunk = ln.ss_window ? TS_CHUNK_H : PS_CHUNK_H;
@@ -447,7 +431,7 @@ void build_work(const morlet_plan_s* p, bool adjoint, std::vector<WorkItem>& wor
       if (ln.ss_window) {
         for (long long kb = kD; kb <= k_last; kb += n_ss) {
           long long a, b;
-          window_tiles(tg, kb, tb.L, horner_rows, a, b);
+          ss_window_tiles(tg, kb, tb.L, horner_rows, PS_TILE_H, &a, &b);
           if (a >= b) continue;
           if (!need.empty() && a <= need.back().second) need.back().second = std::max(need.back().second, b);
           else need.push_back({a, b});

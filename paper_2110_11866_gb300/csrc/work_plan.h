@@ -55,6 +55,25 @@ __host__ __device__ inline long long ws_floordiv(long long a, long long b) {
   return (a >= 0) ? a / b : -((-a + b - 1) / b);
 }
 
+// Start-state items of a row whose tile k covers positions [t_grid + tile k, t_grid + tile (k + 1)):
+// the tiles whose sums an item starting on tile kb reads (start_state_window). Its window begins at
+// u0 = t_a - 2L (t_a - 2L - 1 for the Horner form's 2L + 1 samples), t_a = t_grid + tile kb; the
+// tile holding u0 is summed by the item itself when u0 lies inside it (a masked sum), and positions
+// before t_grid are zero, so the item reads the sums of the tiles [a, b) = [k0 (+ 1 if u0 is inside
+// tile k0), kb), k0 = the tile of u0 (0 when u0 <= t_grid).
+__host__ __device__ inline void ss_window_tiles(long long t_grid, long long kb, long long L, bool horner,
+                                                long long tile, long long* a, long long* b) {
+  const long long u0 = t_grid + tile * kb - 2 * L - (horner ? 1 : 0);
+  long long k0 = 0;
+  bool partial = false;
+  if (u0 > t_grid) {
+    k0 = (u0 - t_grid) / tile;
+    partial = u0 > t_grid + tile * k0;
+  }
+  *a = k0 + (partial ? 1 : 0);
+  *b = kb;
+}
+
 // Appends the row's work items to out (if not null) and returns their number; *slots is advanced by
 // the number of look-back slots the row uses, *subtiles by the sub-tiles it processes.
 __host__ __device__ inline long long row_work(const RowSpec& r, long long T, WorkItem* out, long long* slots,

@@ -343,23 +343,37 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const __grid_co
             else B[v].y = rho[v % K].y * s14;
           }
         } else if constexpr (AU) {
-          // U <- rho U + d from zero, d = x[t] - kappa x[t - 2L], two terms per instruction
-          float2 X2[H], Y2[H];
+          // U <- rho U + d from zero, d = x[t] - kappa x[t - 2L], two terms per instruction, as the
+          // real second-order recurrence in Reinsch's form for a damped rotation (rho = r e^{-i theta},
+          // r = |rho| = e^{-alpha} for every term, lam = 4 sin^2(theta / 2)):
+          //     e_i = r e_{i-1} + d_i - r lam s_{i-1},  s_i = r s_{i-1} + e_i,
+          // then U = (e_15 + (r lam / 2) s_14) + i Im(rho) s_14: three operations per position and
+          // term pair instead of four.
+          const float r = sqrtf(fmaf(rho[0].x, rho[0].x, rho[0].y * rho[0].y));
+          const float2 r2 = pk_dup(r);
+          float2 nl2[H], e2[H], s2[H];
 #pragma unroll
-          for (int h = 0; h < H; ++h) X2[h] = Y2[h] = make_float2(0.f, 0.f);
+          for (int h = 0; h < H; ++h) {
+            const float l0 = __ldg(&tb->f_lam[2 * h]), l1 = 2 * h + 1 < K ? __ldg(&tb->f_lam[2 * h + 1]) : 0.f;
+            nl2[h] = make_float2(-r * l0, -r * l1);
+            e2[h] = s2[h] = make_float2(0.f, 0.f);
+          }
 #pragma unroll
           for (int i = 0; i < ITEMS; ++i) {
             const float2 d2 = pk_dup(fmaf(-kap, xl[i], xa[i]));
 #pragma unroll
             for (int h = 0; h < H; ++h) {
-              const float2 vr = pk_fma(rx2[h], X2[h], pk_fma(nry2[h], Y2[h], d2));
-              Y2[h] = pk_fma(ry2[h], X2[h], pk_mul(rx2[h], Y2[h]));
-              X2[h] = vr;
+              e2[h] = pk_fma(nl2[h], s2[h], pk_fma(r2, e2[h], d2));
+              if (i + 1 < ITEMS) s2[h] = pk_fma(r2, s2[h], e2[h]);  // the last step keeps s_14
             }
           }
 #pragma unroll
-          for (int v = 0; v < NT; ++v)
-            B[v] = (v & 1) ? cmake<R>(X2[v >> 1].y, Y2[v >> 1].y) : cmake<R>(X2[v >> 1].x, Y2[v >> 1].x);
+          for (int v = 0; v < NT; ++v) {
+            const int h = v >> 1;
+            const float e = (v & 1) ? e2[h].y : e2[h].x, s14 = (v & 1) ? s2[h].y : s2[h].x;
+            const float nl = (v & 1) ? nl2[h].y : nl2[h].x, ry = (v & 1) ? ry2[h].y : ry2[h].x;
+            B[v] = cmake<R>(fmaf(-0.5f * nl, s14, e), ry * s14);
+          }
         } else if constexpr (APK) {
           // the damped recursion from zero, two terms per instruction (the scalar step's operations
           // in the same order)

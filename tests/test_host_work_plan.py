@@ -60,6 +60,10 @@ extern "C" long long row_work_c(long long N, long long L, long long D, long long
   *chained = ch ? 1 : 0;
   return m;
 }
+extern "C" void ss_window_tiles_c(long long t_grid, long long kb, long long L, int horner, long long tile,
+                                  long long* a, long long* b) {
+  ss_window_tiles(t_grid, kb, L, horner != 0, tile, a, b);
+}
 """
 
 
@@ -80,6 +84,10 @@ def harness(tmp_path_factory):
     ll, i32, pll, pi = ctypes.c_longlong, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int)
     f.restype = ll
     f.argtypes = [ll, ll, ll, ll, ll, i32, i32, i32, ll, i32, ll, ll, ll, pll, ll, pll, pll, pi]
+    g = lib.ss_window_tiles_c
+    g.restype = None
+    g.argtypes = [ll, ll, ll, i32, ll, pll, pll]
+    f.window_tiles = g
     return f
 
 
@@ -193,3 +201,29 @@ def test_row_work_edges(harness):
             for N in (1, 3, T, 10 * T + 3):
                 check_row(harness, N, L, L, 3, 8, policy, 1)
                 check_row(harness, N, L, L, 0, 4, policy, 0)
+
+
+def test_start_state_window_tiles(harness):
+    """The tiles whose sums a start-state item reads (ss_window_tiles, the rule the plan uses to
+    choose which tile sums to compute) are exactly the tiles that lie wholly inside the item's
+    window [u0, t_a) and at or after the row's tile 0; with the masked sum of the part of the window
+    in front of them (from max(u0, t_grid) to their start, inside one tile) they cover the window's
+    positions from t_grid on exactly once. Brute force over seeded random rows, both window forms."""
+    rng = np.random.default_rng(31)
+    tile = 512
+    a, b = ctypes.c_longlong(0), ctypes.c_longlong(0)
+    for _ in range(3000):
+        t_grid = -512 + int(rng.integers(0, 8))
+        kb = int(rng.integers(1, 400))
+        L = int(rng.choice([int(rng.integers(1, 300)), int(rng.integers(256, 50000))]))
+        horner = int(rng.integers(0, 2))
+        harness.window_tiles(t_grid, kb, L, horner, tile, ctypes.byref(a), ctypes.byref(b))
+        t_a = t_grid + tile * kb
+        u0 = t_a - 2 * L - horner
+        full = [k for k in range(kb) if t_grid + tile * k >= u0 and t_grid + tile * (k + 1) <= t_a]
+        assert b.value == kb and list(range(a.value, b.value)) == full, (t_grid, kb, L, horner)
+        # the masked part [max(u0, t_grid), first full tile) lies inside one tile (the whole window
+        # when no tile is full)
+        lo = max(u0, t_grid)
+        head_end = t_grid + tile * full[0] if full else t_a
+        assert 0 <= head_end - lo < tile or (not full and head_end - lo == tile), (t_grid, kb, L, horner)
