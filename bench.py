@@ -297,7 +297,7 @@ def main():
     # finished). CUDA events split each step into its copy-in, compute and copy-out phases.
     sc = m.morlet_plan_schedule(plan)
     plan2 = m.morlet_plan(lens, sigmas, xi=w.xi, K=w.K, precision=m.MORLET_FP32_COMP, form=args.form)
-    if args.form == 2:
+    if args.form != 1:  # the rotating form (the default): the schedule of the timed plan
         m.morlet_plan_set_row_thresholds(plan2, sc["lane_chunk_max_L"], sc["start_state_min_L"])
         m.morlet_plan_set_schedule(plan2, sc["seg_mult"], sc["ss_tiles_max"], sc["order"], sc["asft_chains"])
     x2, W2 = torch.empty_like(x), torch.empty_like(W)
