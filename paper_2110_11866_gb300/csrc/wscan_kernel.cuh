@@ -568,68 +568,7 @@ __global__ void __launch_bounds__(THREADS, C::MINB) wscan_kernel(const __grid_co
       constexpr bool STAGE_R = (C::OUT == OUT_REAL && sizeof(R) == 4 && ITEMS == 16);
       const int64_t tw = wi.t_a + (int64_t)k * WT;  // first position of the warp-tile
       if (tw >= t_end || tw + WT <= t_out) continue;  // no output in this warp-tile (warp-uniform)
-      if constexpr (STAGE && C::ASFT && C::OUT == OUT_MORLET) {
-        // ASFT Morlet (damped recursion): whole 32-byte aligned tiles as four
-        // 256-bit stores per lane, the others through padded shared rows. (TMA stores measured
-        // slower for these kernels: 4.45 against 4.17 ms on the full scalogram by the ASFT.)
-        {
-          V* obd = reinterpret_cast<V*>(P.out) + (wi.out_off - D + tw);
-          if (tw >= t_out && tw + WT <= t_end && (reinterpret_cast<uintptr_t>(obd) & 31) == 0) {
-            // every output of the tile, 32-byte aligned: each lane writes its 128 bytes as four
-            // whole-sector 256-bit stores
-            float* op = reinterpret_cast<float*>(obd + lane * ITEMS);
-#pragma unroll
-            for (int i = 0; i < ITEMS; i += 4) {
-              const V o0 = one(i), o1 = one(i + 1), o2 = one(i + 2), o3 = one(i + 3);
-              asm volatile("st.global.cs.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(op + 2 * i),
-                           "f"(o0.x), "f"(o0.y), "f"(o1.x), "f"(o1.y), "f"(o2.x), "f"(o2.y), "f"(o3.x), "f"(o3.y)
-                           : "memory");
-            }
-            continue;
-          }
-        }
-        // Otherwise the warp-tile's 512 outputs go through this warp's shared rows (one padded
-        // 144-byte row per lane, conflict-free both ways) so that every store instruction writes
-        // 512 (or 256) contiguous bytes instead of 32 scattered half-sectors; positions outside
-        // [t_out, t_end) are masked.
-        __shared__ float4 s_out[WARPS * 32 * 9];
-        float4* rows = s_out + (threadIdx.x >> 5) * (32 * 9);
-#pragma unroll
-        for (int i = 0; i < ITEMS; i += 2) {
-          const V o0 = one(i);
-          const V o1 = one(i + 1);
-          rows[lane * 9 + i / 2] = make_float4(o0.x, o0.y, o1.x, o1.y);
-        }
-        __syncwarp();
-        V* ob = reinterpret_cast<V*>(P.out) + (wi.out_off - D + tw);
-        const int lo_o = (int)(t_out > tw ? t_out - tw : 0);         // stored outputs [lo_o, hi_o)
-        const int hi_o = (int)(t_end < tw + WT ? t_end - tw : WT);
-        const bool aligned = (reinterpret_cast<uintptr_t>(ob) & 15) == 0;
-        if (aligned && lo_o == 0 && hi_o == WT) {  // the common case: every output of the tile
-#pragma unroll
-          for (int r = 0; r < 8; ++r) {
-            const int c = 32 * r + lane;
-            __stcs(reinterpret_cast<float4*>(ob) + c, rows[(c >> 3) * 9 + (c & 7)]);
-          }
-        } else if (aligned) {
-#pragma unroll
-          for (int r = 0; r < 8; ++r) {
-            const int c = 32 * r + lane;  // 16-byte chunk: outputs 2c, 2c + 1
-            const float4 v = rows[(c >> 3) * 9 + (c & 7)];
-            const bool in0 = 2 * c >= lo_o && 2 * c < hi_o, in1 = 2 * c + 1 >= lo_o && 2 * c + 1 < hi_o;
-            if (in0 && in1) __stcs(reinterpret_cast<float4*>(ob) + c, v);
-            else if (in0) __stcs(ob + 2 * c, make_float2(v.x, v.y));
-            else if (in1) __stcs(ob + 2 * c + 1, make_float2(v.z, v.w));
-          }
-        } else {
-#pragma unroll
-          for (int r = 0; r < 16; ++r) {
-            const int o = 32 * r + lane;
-            if (o >= lo_o && o < hi_o) __stcs(ob + o, reinterpret_cast<const float2*>(rows + (o >> 4) * 9)[o & 15]);
-          }
-        }
-        __syncwarp();
-      } else if constexpr (STAGE) {
+      if constexpr (STAGE) {
         V* ob = reinterpret_cast<V*>(P.out) + (wi.out_off - D + tw);
         const bool full = tw >= t_out && tw + WT <= t_end;
         // The warp's 512 outputs are staged in its 4 KB tile of shared memory: lane l's 128 bytes
