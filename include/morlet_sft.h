@@ -63,13 +63,16 @@ enum {
 /* flags */
 enum {
   MORLET_FLAG_NO_GRAPH = 1,   /* launch kernels directly instead of replaying a CUDA graph */
-  MORLET_FLAG_AUTOTUNE = 2,   /* compensated FP32 SFT Morlet, ASFT and multiplication-method plans: at plan time, time the
-                                 forward (a sub-plan with a zero input and a scratch output: the whole
-                                 batch if that scratch takes at most a quarter of the free device
-                                 memory, else every k-th signal up to 2^28 outputs) under a few
-                                 schedules -- row thresholds, segment and item lengths, row order,
-                                 ASFT chains (morlet_plan_set_schedule) -- and keep the fastest (each
-                                 knob keeps its default unless another value is at least 1 % faster) */
+  MORLET_FLAG_AUTOTUNE = 2,   /* compensated FP32 SFT plans (Morlet and Gaussian), FP32 ASFT and
+                                 multiplication-method plans: at plan time, time the forward (a
+                                 sub-plan with a zero input and a scratch output: the whole batch if
+                                 that scratch takes at most a quarter of the free device memory, else
+                                 every k-th signal up to 2^28 outputs) under a few schedules -- row
+                                 thresholds (morlet_plan_set_row_thresholds; for the ASFT and the
+                                 multiplication method the Horner start-state limit, timed together
+                                 with the ASFT's chains), segment and item lengths, item order, ASFT
+                                 chains (morlet_plan_set_schedule) -- and keep the fastest (each
+                                 knob keeps its value unless another is at least 1 % faster) */
   MORLET_FLAG_NO_HALO = 4,    /* force one look-back chain per row (no per-tile window recompute) */
   MORLET_FLAG_EDGE = 8,       /* forward: extend each signal with its edge values instead of zeros
                                  (Sec. II: "zero or the values on the edges"); the plan holds a padded
