@@ -12,6 +12,12 @@ of s) fails here with a readable message.
 - The ASFT's U form: with kappa = rho^{2L} real, V <- rho (V - kappa x[t - 2L - 1]) + x[t] (the
   window of the last 2L + 1 samples) and U = V - kappa x[t - 2L] obey
   U <- rho U + (x[t] - kappa x[t - 2L]).
+- The SFT warp scan in the frame of the tile start: with lane aggregates B_l, B'_l =
+  rho^{-16 (l + 1)} B_l, the state before lane l is rho^{16 l} (C + sum_{l' < l} B'_{l'}).
+- Start states from tile sums: the window sum ending at t_a - 1 is sum_k rho^{512 (kb - 1 - k)} G_k
+  over the tiles inside the window, plus the masked part of the tile holding its first sample.
+- The three-shear rotation x += t y, y -= s x, x += t y with t = tan(theta / 2), s = sin(theta)
+  multiplies x + i y by e^{-i theta}.
 """
 import numpy as np
 
@@ -95,3 +101,60 @@ def test_asft_u_form_tracks_the_v_recursion():
         t = len(x) - 1
         win = sum(rho ** (t - u) * xa(u) for u in range(t - 2 * L, t + 1))
         assert abs(V - win) < 1e-10
+
+
+def test_frame_of_tile_scan_gives_each_lanes_start_state():
+    rng = np.random.default_rng(8)
+    for theta in (1e-4, 0.37, 2.9):
+        rho = np.exp(-1j * theta)
+        C = complex(rng.standard_normal(), rng.standard_normal())
+        d = rng.standard_normal(512)
+        B = np.array([complex_pass(rho, d[16 * l:16 * l + 16]) for l in range(32)])
+        Bp = rho ** (-16.0 * (np.arange(32) + 1)) * B
+        excl = np.concatenate([[0j], np.cumsum(Bp)[:-1]])
+        S = rho ** (16.0 * np.arange(32)) * (C + excl)
+        g = C
+        for l in range(32):
+            assert abs(S[l] - g) < 1e-10 * max(1.0, abs(g)), (theta, l)
+            for v in d[16 * l:16 * l + 16]:
+                g = rho * g + v
+        assert abs(rho ** 512 * (C + Bp.sum()) - g) < 1e-9 * max(1.0, abs(g))
+
+
+def test_start_state_from_tile_sums_is_the_window_sum():
+    rng = np.random.default_rng(9)
+    T = 512
+    for _ in range(20):
+        L = int(rng.integers(1, 2000))
+        theta = np.pi * int(rng.integers(1, 6)) / L
+        rho = np.exp(-1j * theta)
+        t_grid = -512 + int(rng.integers(0, 8))
+        kb = int(rng.integers(1, 12))
+        n = T * (kb + 2)
+        x = rng.standard_normal(n)
+        xa = lambda u: x[u] if 0 <= u < n else 0.0
+        t_a = t_grid + T * kb
+        u0 = t_a - 2 * L
+        want = sum(rho ** (t_a - 1 - u) * xa(u) for u in range(max(u0, t_grid), t_a))
+        # tile sums G_k = sum_{u in tile k} rho^{e_k - u} x[u], e_k the tile's last position
+        def tile_sum(k, lo):
+            a0 = t_grid + T * k
+            return sum(rho ** (a0 + T - 1 - u) * xa(u) for u in range(max(a0, lo), a0 + T))
+        k0 = (u0 - t_grid) // T if u0 > t_grid else 0
+        got = 0j
+        for k in range(k0, kb):
+            got += rho ** (T * (kb - 1 - k)) * tile_sum(k, u0 if k == k0 else t_grid)
+        assert abs(got - want) < 1e-9 * max(1.0, abs(want)), (L, kb, t_grid)
+
+
+def test_three_shears_rotate_by_minus_theta():
+    rng = np.random.default_rng(10)
+    for theta in (1e-6, 0.01, 1.0, 3.0):
+        t, s = np.tan(theta / 2), np.sin(theta)
+        x0, y0 = rng.standard_normal(2)
+        x, y = x0, y0
+        x = x + t * y
+        y = y - s * x
+        x = x + t * y
+        want = complex(x0, y0) * np.exp(-1j * theta)
+        assert abs(complex(x, y) - want) < 1e-12, theta
