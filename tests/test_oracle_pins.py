@@ -132,6 +132,34 @@ def test_table1_sft_soft_pin():
         assert best < math.log(1.25), (P, best)
 
 
+def test_table1_asft_soft_pin():
+    """Table I, ASFT rows (soft pin, n0 = 10, L = 256; sigma is not printed): the oracle's own ASFT
+    Gaussian fits (fit_gauss_asft: the damped window, the shift identity and its derivative reading,
+    beta = pi / L) give effective kernels whose relative RMSE against G, G_D, G_DD over [-3L, 3L]
+    (zero outside the window) reproduces all three printed errors of the rows P = 3, 4 and 6 to
+    within 10 % at some sigma in [L/6, L/3]. A dropped alpha term in the derivative brackets, a wrong
+    sign of the damping or a shift by the wrong n0 moves e(G_D) or e(G_DD) far off. The P = 5 row is
+    left out: its e(G) is three times the SFT row's while its e(G_D) and e(G_DD) are below the SFT
+    row's, unlike every other row, and no sigma reproduces it."""
+    g = _gold("table1_relative_rmse.json")
+    L = g["L"]
+    kk = np.arange(-3 * L, 3 * L + 1)
+    targets = (M.gaussian, M.gaussian_d, M.gaussian_dd)
+
+    def rmse(P, d, sig):
+        kp, ker = M.kernel_gauss_asft(M.fit_gauss_asft(sig, P, d, 10, L))
+        full = np.zeros(kk.shape)
+        full[kp - kk[0]] = ker
+        tgt = targets[d](kk.astype(np.float64), sig)
+        return 100.0 * math.sqrt(np.sum((full - tgt) ** 2) / np.sum(tgt ** 2))
+
+    for P in (3, 4, 6):
+        want = np.array(g["ASFT"][str(P)])
+        best = min(np.abs(np.log(np.array([rmse(P, d, L / r) for d in range(3)]) / want)).max()
+                   for r in np.linspace(3.0, 6.0, 31))
+        assert best < math.log(1.10), (P, best)
+
+
 # ------------------------------------------------------------------------------------------------
 # Kernel integral (O-SFT) against brute force, Algorithm 1 and the definition
 # ------------------------------------------------------------------------------------------------
